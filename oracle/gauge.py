@@ -1,0 +1,94 @@
+"""Wilson gauge action, staple force and kinetic term (oracle; test infrastructure only).
+
+The paper writes the Hamiltonian as H(q, p) = S(q) + T(p) (section 2) and
+calls the S-hat vector field the force (section 3).  It does not state the
+gauge action; the oracle uses the unimproved Wilson plaquette action
+
+    S_G = beta * sum_x sum_{mu<nu} (1 - Re Tr U_{mu nu}(x) / 3),
+    U_{mu nu}(x) = U_mu(x) U_nu(x+mu) U_mu(x+nu)^dagger U_nu(x)^dagger,
+
+periodic in all four directions.  The force is the left derivative
+F^a_mu(x) = dS/d eps^a along U_mu(x) -> exp(i eps T^a) U_mu(x), and the
+kinetic term is T = (1/2) sum (p^a)^2 over all links and colours.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+from .su3 import dag, trace, im_tr_gellmann
+
+
+def shift(f: np.ndarray, mu: int, step: int) -> np.ndarray:
+    """f(x + step * mu-hat) with periodic wrap; site axes are (t, z, y, x)."""
+    return np.roll(f, -step, axis=3 - mu)
+
+
+def plaquette_field(u: np.ndarray, mu: int, nu: int) -> np.ndarray:
+    """U_{mu nu}(x) on every site."""
+    return (u[..., mu, :, :] @ shift(u[..., nu, :, :], mu, 1)
+            @ dag(shift(u[..., mu, :, :], nu, 1)) @ dag(u[..., nu, :, :]))
+
+
+def wilson_action(u: np.ndarray, beta: float) -> float:
+    s = 0.0
+    for mu in range(4):
+        for nu in range(mu + 1, 4):
+            s += np.sum(1.0 - np.real(trace(plaquette_field(u, mu, nu))) / 3.0)
+    return float(beta * s)
+
+
+def mean_plaquette(u: np.ndarray) -> float:
+    """<Re Tr U_p / 3> over the 6V plaquettes."""
+    acc = 0.0
+    for mu in range(4):
+        for nu in range(mu + 1, 4):
+            acc += np.mean(np.real(trace(plaquette_field(u, mu, nu)))) / 3.0
+    return float(acc / 6.0)
+
+
+def staple_sum(u: np.ndarray, mu: int) -> np.ndarray:
+    """A_mu(x): the six staples closing a plaquette with U_mu(x).
+
+    Upper staple U_nu(x+mu) U_mu(x+nu)^dagger U_nu(x)^dagger and lower staple
+    U_nu(x+mu-nu)^dagger U_mu(x-nu)^dagger U_nu(x-nu), for every nu != mu, so
+    that Re Tr(U_mu(x) A_mu(x)) is the sum over the plaquettes holding U_mu(x).
+    """
+    a = np.zeros(u.shape[:4] + (3, 3), dtype=np.complex128)
+    for nu in range(4):
+        if nu == mu:
+            continue
+        u_mu = u[..., mu, :, :]
+        u_nu = u[..., nu, :, :]
+        a += shift(u_nu, mu, 1) @ dag(shift(u_mu, nu, 1)) @ dag(u_nu)
+        u_nu_m = shift(u_nu, nu, -1)                 # U_nu(x - nu)
+        a += (dag(shift(u_nu_m, mu, 1))              # U_nu(x + mu - nu)^dagger
+              @ dag(shift(u_mu, nu, -1))             # U_mu(x - nu)^dagger
+              @ u_nu_m)
+    return a
+
+
+def gauge_force(u: np.ndarray, beta: float) -> np.ndarray:
+    """F^a_mu(x) = dS_G/d eps^a = (beta/6) Im Tr(lambda^a U_mu(x) A_mu(x)).
+
+    From d/d eps [-(beta/3) Re Tr(exp(i eps T^a) U A)] at eps = 0
+    = (beta/3) Im Tr(T^a U A).  Shape ``[Lt, Lz, Ly, Lx, 4, 8]``.
+    """
+    f = np.empty(u.shape[:5] + (8,))
+    for mu in range(4):
+        omega = u[..., mu, :, :] @ staple_sum(u, mu)
+        f[..., mu, :] = (beta / 6.0) * im_tr_gellmann(omega)
+    return f
+
+
+def kinetic(p: np.ndarray) -> float:
+    """T = (1/2) sum_links sum_a (p^a)^2 = sum_links Tr P^2."""
+    return float(0.5 * np.sum(p * p))
+
+
+def gauge_transform_links(u: np.ndarray, g: np.ndarray) -> np.ndarray:
+    """U_mu(x) -> g(x) U_mu(x) g(x+mu)^dagger."""
+    out = np.empty_like(u)
+    for mu in range(4):
+        out[..., mu, :, :] = g @ u[..., mu, :, :] @ dag(shift(g, mu, 1))
+    return out
