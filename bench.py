@@ -1,0 +1,355 @@
+"""Benchmark: force-gradient HMC trajectories per second on one GB300 per rank.
+
+Workload (one "step" = one HMC trajectory): pure-gauge SU(3) Wilson action on
+a 32^4 lattice at beta = 6.0, force-gradient PQPQP integrator of Table 1 with
+dt = 0.25 and tau = 1 (4 MD steps, 13 force evaluations, 8 link drifts),
+FP32 links, momenta and forces with FP64 dH sums, 18-real links.  The chain
+starts from a seeded hot start thermalised by 10 force-gradient trajectories
+(dt = 1/8, always accepted); W warm-up trajectories with Metropolis follow,
+then K timed trajectories.
+
+Output: one JSON line (rank 0).  `value` is trajectories per second over all
+ranks with the fields resident in HBM; `e2e` is the same metric through the
+C ABI with host buffers (gauge field and momenta uploaded, gauge field read
+back every trajectory); `roofline` reports the gauge-force kernel against
+the FP32 FMA peak; `cpu_baseline` times the FP64 CPU oracle on a 16^4 sample.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_0910_2950_gb300 import inputs  # noqa: E402
+
+BETA = 6.0
+DT = 0.25
+TAU = 1.0
+L_BENCH = 32
+THERM_TRAJ = 10
+METRIC = "FG-HMC trajectories/s at fixed acceptance"
+UNIT = "trajectories/s"
+# FP32 peak of the FMA pipes: 152 SMs x 128 lanes x 2 flop x 2070 MHz (maximum SM clock).
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12
+# FP64 is nominal (1.25 TFLOP/s for the whole GPU).
+FP64_PEAK_TFLOPS = 1.25
+
+# Algorithmic work per link of the fused gauge-force kernel, by mode:
+# staple sum 6 x (2 products of 198 flop + 18 to accumulate) = 2484, U*A 198,
+# projection and scale 24, kick 16; exp(i c P) (Cayley-Hamilton) 420 and U <- E U 198;
+# FP32 re-unitarisation 100.
+FLOP_FORCE = 2484 + 198 + 24
+FLOP_KICK = 16
+FLOP_EXP_MUL = 420 + 198
+FLOP_REUNIT = 100
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--lattice", type=int, default=L_BENCH)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--integrator", default="fg")
+    ap.add_argument("--dt", type=float, default=DT)
+    ap.add_argument("--link-reals", type=int, default=18)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ----------------------------------------------------------------------------- oracle legs
+def oracle_trajectory_rate(sample_l: int, target_l: int, integrator: str, dt: float, seed: int):
+    """Time the FP64 CPU oracle on one trajectory of a sample_l^4 lattice and
+    scale it to target_l^4 by the volume ratio (work per trajectory is linear
+    in V).  Returns (trajectories/s at target volume, seconds, description)."""
+    from oracle import integrators as it
+    dims = (sample_l,) * 4
+    u = inputs.hot_start(dims, seed)
+    p = inputs.gaussian_momenta(dims, seed)
+    t0 = time.perf_counter()
+    it.trajectory(it.GaugeSystem(BETA), it.Integrator(integrator), u, p, dt, TAU)
+    secs = time.perf_counter() - t0
+    scale = (sample_l / target_l) ** 4
+    return scale / secs, secs, (f"one {integrator} trajectory (tau={TAU}, dt={dt}) on {sample_l}^4 in "
+                                f"FP64 numpy, {secs:.2f} s, scaled by V ratio ({sample_l}/{target_l})^4")
+
+
+def cpu_cores_used():
+    return 1  # numpy batched 3x3 products and eigh run on one thread
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return 0
+    sample_l = 12
+    rates, secs = [], []
+    for k in range(args.warmup + args.steps):
+        r, s, desc = oracle_trajectory_rate(sample_l, args.lattice, args.integrator, args.dt, 100 + k)
+        if k >= args.warmup:
+            rates.append(r)
+            secs.append(s)
+    value = len(rates) / sum(1.0 / r for r in rates)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
+                         "sample": f"each step: {desc}"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(args):
+    L = args.lattice
+    return {
+        "workload": f"pure-gauge SU(3) Wilson {L}^4, beta={BETA}, {args.integrator} integrator "
+                    f"tau={TAU} dt={args.dt}, {args.precision} links/forces, FP64 dH sums, "
+                    f"{args.link_reals}-real links, hot start + {THERM_TRAJ} thermalising trajectories",
+        "lattice": [L] * 4, "beta": BETA, "integrator": args.integrator, "dt": args.dt, "tau": TAU,
+        "precision": args.precision, "link_reals": args.link_reals,
+        "l2": f"inputs larger than L2: gauge field "
+              f"{4 * L**4 * args.link_reals * (4 if args.precision == 'fp32' else 8) / 1e6:.0f} MB",
+        "parallelism": "replicas (one independent chain per GPU)",
+    }
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args):
+    rank, world, local = dist_info()
+    import torch
+    import torch.distributed as dist
+
+    cpu = None
+    if rank == 0 and world >= 1 and not args.no_cpu_baseline:
+        # oracle first, before this process touches the GPU
+        r, s, desc = oracle_trajectory_rate(16, args.lattice, args.integrator, args.dt, 7)
+        cpu = {"value": r, "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle", "sample": desc}
+
+    if world > 1:
+        dist.init_process_group("nccl", rank=rank, world_size=world)
+    torch.cuda.set_device(local)
+    from paper_0910_2950_gb300 import build, fg
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    fg.load()
+
+    L = args.lattice
+    dims = (L,) * 4
+    stream = torch.cuda.Stream()
+    lat = fg.Lattice(dims, BETA, precision=args.precision, link_reals=args.link_reals,
+                     seed=1000 + rank, stream=stream.cuda_stream)
+    u0 = inputs.hot_start(dims, 1 + rank)
+    lat.set_gauge(u0)
+    del u0
+    for _ in range(THERM_TRAJ):
+        lat.trajectory("fg", 0.125, TAU, refresh=True, u_accept=0.0)
+    for _ in range(args.warmup):
+        lat.trajectory(args.integrator, args.dt, TAU, refresh=True, u_accept=-1.0)
+
+    clocks = ClockSampler(local)
+    lat.timing(True)
+    lat.timing_reset()
+    lat.timing(True)
+    n_launch0 = lat.launch_count()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    results = []
+    for _ in range(args.steps):
+        results.append(lat.trajectory(args.integrator, args.dt, TAU, refresh=True, u_accept=-1.0))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    launches = lat.launch_count() - n_launch0
+    force_ms, force_n = lat.kernel_time("gauge_force")
+    lat.timing(False)
+
+    t = torch.tensor([elapsed_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    max_ms = float(t.item())
+    value = world * args.steps / (max_ms / 1000.0)
+
+    acc = float(np.mean([r["accepted"] for r in results]))
+    emdh = float(np.mean([np.exp(-r["dH"]) for r in results]))
+    n_force = results[0]["n_force"]
+    nsteps = results[0]["n_steps"]
+
+    # ---------------------------------------------------------------- roofline (gauge force)
+    links = 4 * lat.V
+    reunit = 1 if args.precision == "fp32" else 0
+    # per FG trajectory: n (kick+drift) + n displacements + n (FG kick + drift) + 1 final kick
+    if args.integrator in ("fg", "force_gradient"):
+        per_traj = nsteps * (FLOP_FORCE + FLOP_KICK + FLOP_EXP_MUL + reunit * FLOP_REUNIT)   # P Q
+        per_traj += nsteps * (FLOP_FORCE + FLOP_EXP_MUL + reunit * FLOP_REUNIT)             # G displace
+        per_traj += nsteps * (FLOP_FORCE + FLOP_KICK + FLOP_EXP_MUL + reunit * FLOP_REUNIT)  # G kick + Q
+        per_traj += FLOP_FORCE + FLOP_KICK                                                  # final P
+    else:
+        per_traj = n_force * (FLOP_FORCE + FLOP_KICK + FLOP_EXP_MUL)
+    flops_per_launch = per_traj * links / n_force
+    avg_launch_s = force_ms / 1000.0 / max(force_n, 1)
+    achieved = flops_per_launch / avg_launch_s / 1e12
+    esize = 4 if args.precision == "fp32" else 8
+    bytes_per_launch = links * (args.link_reals * esize + 2 * 8 * esize)
+    peak = FP32_PEAK_TFLOPS if args.precision == "fp32" else FP64_PEAK_TFLOPS
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None,
+            "kernel": "gauge_force (fused staple force + kick/drift/displace)",
+            "launches": force_n, "avg_launch_us": avg_launch_s * 1e6,
+            "algorithmic_gbs": bytes_per_launch / avg_launch_s / 1e9,
+            "share_of_step": force_ms / elapsed_ms}
+
+    # ---------------------------------------------------------------- e2e through host buffers
+    e2e = None
+    if not args.no_e2e:
+        ncanon_u = lat.V * 4 * 18
+        ncanon_p = lat.V * 4 * 8
+        hu = torch.empty(ncanon_u, dtype=torch.float64, pin_memory=True).numpy()
+        hp = torch.empty(ncanon_p, dtype=torch.float64, pin_memory=True).numpy()
+        hu[:] = lat.get_gauge().view(np.float64).ravel()
+        rng = inputs.make_rng(77 + rank)
+        hp[:] = rng.standard_normal(ncanon_p)
+        lat.set_gauge(hu)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            lat.set_gauge(hu)
+            lat.set_momenta(hp)
+            r = lat.trajectory(args.integrator, args.dt, TAU, refresh=False, u_accept=-1.0)
+            out = lat.get_gauge()
+            hu[:] = out.view(np.float64).ravel()
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * args.steps / float(te.item()), "unit": UNIT,
+               "h2d_bytes_per_step": (ncanon_u + ncanon_p) * 8,
+               "d2h_bytes_per_step": ncanon_u * 8 + 14 * 8,
+               "note": "per trajectory: gauge field and momenta uploaded from pinned host memory "
+                       "(canonical FP64), trajectory run, gauge field and result read back"}
+
+    if rank == 0:
+        cfg = workload_config(args)
+        cfg.update({"acceptance": acc, "mean_exp_minus_dH": emdh,
+                    "dH": [round(r["dH"], 6) for r in results[:8]],
+                    "forces_per_trajectory": n_force, "md_steps": nsteps,
+                    "plaquette": lat.plaquette()})
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+                "config": cfg, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    lat.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

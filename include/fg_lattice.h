@@ -1,0 +1,227 @@
+/*
+ * fg_lattice.h -- C ABI of the GB300 force-gradient Hybrid Monte Carlo library.
+ *
+ * The library runs the molecular-dynamics (MD) step of Hybrid Monte Carlo for
+ * 4D SU(3) lattice gauge theory with the integrators of Kennedy, Clark and
+ * Silva, "Force Gradient Integrators" (LAT2009):
+ *
+ *   - the Wilson gauge staple force and the momentum kick exp(c dt S-hat)
+ *     (section 3; S-hat is "the force");
+ *   - the exact link drift exp(c dt T-hat), U <- exp(i c dt P) U (section 2);
+ *   - the force-gradient kick exp((48 dt S-hat - dt^3 {S,{S,T}}-hat)/72) of
+ *     Table 1, evaluated as the force at links displaced along the force by
+ *     dt^2/24 (section 4 gives {S,{S,T}} = e^i(S) e_i(S));
+ *   - the kinetic term and the action sums behind dH (section 5, Fig. 1);
+ *   - for Nf = 2 Wilson fermions: the even-odd preconditioned Wilson-Dirac
+ *     operator, CG on Mhat^dagger Mhat and the pseudofermion force
+ *     e_i(S) = -X^dagger e_i(M) X, X = M^{-1} phi (section 4, section 5).
+ *
+ * Conventions (the paper leaves them open; these are fixed here):
+ *   - lattice dims {Lx, Ly, Lz, Lt}, each even and >= 2; V = Lx Ly Lz Lt;
+ *     lexicographic site index i = x + Lx (y + Ly (z + Lz t)); links periodic,
+ *     fermions antiperiodic in t;
+ *   - Wilson gauge action S_G = beta sum_{x, mu<nu} (1 - Re Tr U_{mu nu}(x) / 3);
+ *   - momenta P = sum_a p^a lambda^a / 2 (Gell-Mann), T = (1/2) sum (p^a)^2;
+ *   - the force on a link is F^a = dS / d eps^a along U -> exp(i eps lambda^a/2) U;
+ *     a kick is p^a <- p^a - c dt F^a, a drift is U <- exp(i c dt P) U;
+ *   - Wilson-Dirac M = 1 - kappa D, D = sum_mu [(1 - gamma_mu) U_mu(x) d_{x+mu}
+ *     + (1 + gamma_mu) U_mu(x-mu)^dagger d_{x-mu}], DeGrand-Rossi gammas;
+ *     Mhat = 1 - kappa^2 D_eo D_oe on even sites; S_F = phi^dagger
+ *     (Mhat^dagger Mhat)^{-1} phi with phi = Mhat^dagger chi.
+ *
+ * Host array layouts (all FP64, owned by the caller, copied by the library):
+ *   gauge    double[V][4][3][3][2]  site (lexicographic), mu, row, col, re/im
+ *   momenta  double[V][4][8]        Gell-Mann coefficients p^a per link
+ *   force    double[V][4][8]        F^a per link
+ *   spinor   double[V/2][4][3][2]   even sites in increasing lexicographic
+ *                                   order (row = lexicographic index / 2),
+ *                                   spin, colour, re/im
+ *
+ * Ownership and threading: a handle owns all of its device memory and one
+ * CUDA stream (or uses the caller's stream given in fg_params.cuda_stream).
+ * A handle is used by one host thread at a time; different handles are
+ * independent.  Every call is stream-ordered on the handle's stream and
+ * returns after the results it reports are on the host.
+ *
+ * Errors: every entry point returns an fg_status; nothing aborts.  On an
+ * error fg_last_error() holds a one-line description.  FG_ECUDA reports a
+ * CUDA runtime error (the handle should then be destroyed).
+ */
+#ifndef FG_LATTICE_H
+#define FG_LATTICE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FG_ABI_VERSION 1
+
+typedef struct fg_lattice fg_lattice;   /* opaque handle */
+
+typedef enum {
+  FG_OK = 0,
+  FG_EINVAL = 1,     /* bad argument (null pointer, odd dims, bad enum, ...) */
+  FG_ENOMEM = 2,     /* device or pinned-host allocation failed */
+  FG_ECUDA = 3,      /* CUDA runtime error */
+  FG_ENOCONV = 4,    /* CG reached cg_maxiter without converging */
+  FG_ETIMEOUT = 5,   /* a host wait exceeded its limit */
+  FG_ESTATE = 6      /* call not valid in the handle's state (e.g. no pseudofermion) */
+} fg_status;
+
+/* Integrators of Table 1 / section 3.  One MD step of each, in order:
+ *   FG_LEAPFROG        PQP:   kick 1/2, drift 1, kick 1/2
+ *   FG_OMELYAN         PQPQP: kick a, drift 1/2, kick 1-2a, drift 1/2, kick a
+ *   FG_FORCE_GRADIENT  kick 1/6, drift 1/2, force-gradient kick 2/3, drift 1/2, kick 1/6
+ *   FG_CAMPOSTRINI     drift w1/2, kick w1, drift (w1+w0)/2, kick w0, drift
+ *                      (w1+w0)/2, kick w1, drift w1/2; w1 = 1/(2-2^(1/3)), w0 = 1-2 w1
+ *   FG_QPQ             drift 1/2, kick 1, drift 1/2
+ * (kick c means exp(c dt S-hat), drift c means exp(c dt T-hat)). */
+typedef enum {
+  FG_LEAPFROG = 0,
+  FG_OMELYAN = 1,
+  FG_FORCE_GRADIENT = 2,
+  FG_CAMPOSTRINI = 3,
+  FG_QPQ = 4
+} fg_integrator;
+
+/* Arithmetic of the bulk fields (links, momenta, forces, CG inner vectors).
+ * Action, kinetic and dH sums and the CG outer residual are FP64 always. */
+typedef enum {
+  FG_FP64 = 0,
+  FG_FP32 = 1
+} fg_precision;
+
+typedef struct {
+  int dims[4];             /* Lx, Ly, Lz, Lt; each even, >= 2 */
+  double beta;             /* gauge coupling */
+  double kappa;            /* hopping parameter; 0 => pure gauge (no fermions) */
+  double alpha;            /* PQPQP parameter for FG_OMELYAN (default 0.1932) */
+  int precision;           /* fg_precision (default FG_FP64) */
+  int link_reals;          /* 18 (full) or 12 (two rows + reconstruction); default 18 */
+  int reunitarize;         /* 1: re-project links onto SU(3) after every drift;
+                              default 0 for FG_FP64, 1 for FG_FP32 */
+  double cg_tol;           /* relative residual |phi - M x| / |phi| for force solves (1e-10) */
+  double cg_tol_action;    /* the same for the action solve at trajectory end (1e-12) */
+  int cg_maxiter;          /* CG iteration cap (default 20000) */
+  double cg_delta;         /* FP32 inner CG: reliable update when the iterated residual
+                              falls by this factor (default 0.1) */
+  unsigned long long seed; /* device momentum / pseudofermion RNG and host accept RNG */
+  void *cuda_stream;       /* cudaStream_t to run on; NULL => the handle creates one */
+} fg_params;
+
+/* Result of one HMC trajectory (section 5, Fig. 1: dH over a whole trajectory). */
+typedef struct {
+  double dH;               /* H_end - H_start, summed site by site in FP64 */
+  double H0, H1;           /* total H at start and end */
+  double S_gauge0, S_gauge1;
+  double S_ferm0, S_ferm1; /* pseudofermion action (0 for pure gauge) */
+  double T0, T1;           /* kinetic term */
+  int accepted;            /* Metropolis outcome; on rejection the links are restored */
+  int n_steps;             /* MD steps (tau / dt) */
+  int n_force;             /* force evaluations (adjacent outer kicks merged) */
+  int n_solves;            /* CG solves, including the action solve */
+  long long cg_iters;      /* CG iterations summed over all solves */
+} fg_traj_result;
+
+typedef struct {
+  int iterations;          /* inner iterations */
+  int reliable_updates;    /* FP64 residual recomputations (mixed precision) */
+  double true_residual;    /* |b - M x| / |b| recomputed in FP64 at exit */
+} fg_cg_result;
+
+/* Fill *p with defaults (dims 4^4, beta 6.0, pure gauge, FP64, 18 reals). */
+fg_status fg_params_default(fg_params *p);
+
+/* Create a handle: validates *p, allocates the device fields (cold start links,
+ * zero momenta).  *out is NULL on failure. */
+fg_status fg_lattice_create(const fg_params *p, fg_lattice **out);
+void fg_lattice_destroy(fg_lattice *h);
+
+/* One-line description of the last error on this handle ("" if none). */
+const char *fg_last_error(const fg_lattice *h);
+
+/* Gauge field in and out (host layout above).  fg_set_gauge does not check
+ * unitarity; links are stored in the handle's precision. */
+fg_status fg_set_gauge(fg_lattice *h, const double *host_links);
+fg_status fg_get_gauge(fg_lattice *h, double *host_links);
+
+/* Momenta in and out (host layout above). */
+fg_status fg_set_momenta(fg_lattice *h, const double *host_p8);
+fg_status fg_get_momenta(fg_lattice *h, double *host_p8);
+
+/* Draw unit-Gaussian momenta on the device (Philox-4x32-10 counter RNG keyed
+ * by fg_params.seed; every call advances the counter). */
+fg_status fg_refresh_momenta(fg_lattice *h);
+
+/* Pseudofermion heat bath from a given complex Gaussian chi on even sites:
+ * phi = Mhat^dagger chi (section 4's S = phi^dagger M^{-1} phi with
+ * M = Mhat^dagger Mhat), and S_F = chi^dagger chi at this gauge field.
+ * FG_ESTATE if the handle is pure gauge (kappa == 0). */
+fg_status fg_set_pseudofermion(fg_lattice *h, const double *host_chi_even);
+/* The same with chi drawn on the device (density exp(-|chi|^2)). */
+fg_status fg_refresh_pseudofermion(fg_lattice *h);
+
+/* Total force F^a = dS/d eps^a (gauge + pseudofermion) on every link, into
+ * host_f8 (layout above). */
+fg_status fg_force(fg_lattice *h, double *host_f8);
+
+/* Actions at the current fields: S_G, S_F (one CG solve to cg_tol_action;
+ * 0 for pure gauge) and T.  Any output pointer may be NULL. */
+fg_status fg_action(fg_lattice *h, double *S_gauge, double *S_ferm, double *T_kin);
+
+/* Mean plaquette <Re Tr U_p / 3>. */
+fg_status fg_plaquette(fg_lattice *h, double *plaq);
+
+/* One MD step of the given integrator with step dt, in place on links and
+ * momenta (no kick merging across steps). */
+fg_status fg_md_step(fg_lattice *h, fg_integrator integ, double dt);
+
+/* One force-gradient PQPQP step (Table 1, last row): fg_md_step(FG_FORCE_GRADIENT). */
+fg_status fg_fg_step(fg_lattice *h, double dt);
+
+/* One HMC trajectory of length tau = n dt (section 3: (step)^(tau/dt)):
+ *   refresh != 0: draw momenta (and chi, with fermions) on the device first;
+ *   refresh == 0: use the momenta (and pseudofermion) already set.
+ *   u_accept in [0,1): Metropolis with this uniform (accept iff u < exp(-dH));
+ *   u_accept < 0: draw the uniform from the handle's host RNG.
+ * Adjacent outer kicks of neighbouring steps are merged.  On rejection the
+ * links are restored; momenta are left at their end-of-trajectory values.
+ * *out may be NULL. */
+fg_status fg_trajectory(fg_lattice *h, fg_integrator integ, double dt, double tau,
+                        int refresh, double u_accept, fg_traj_result *out);
+
+/* Building blocks for callers and tests (even-site spinors, host layout above). */
+/* out = Mhat in (dagger = 0) or Mhat^dagger in (dagger = 1). */
+fg_status fg_apply_mhat(fg_lattice *h, const double *host_in_even, double *host_out_even,
+                        int dagger);
+/* Solve Mhat^dagger Mhat x = b to cg_tol with x0 = 0. */
+fg_status fg_cg_solve(fg_lattice *h, const double *host_b_even, double *host_x_even,
+                      fg_cg_result *res);
+
+/* Re-project every link onto SU(3) (Gram-Schmidt of rows 1-2, row 3 = (row1 x row2)^*). */
+fg_status fg_reunitarize(fg_lattice *h);
+
+/* Per-kernel timing with CUDA events on the handle's stream.  While enabled,
+ * every launch of the named kernel class is bracketed by events;
+ * fg_kernel_time synchronises and returns the summed device time and the
+ * number of launches since the last reset.  Classes: "gauge_force",
+ * "drift", "energy", "reduce", "momenta", "dslash", "cg_blas",
+ * "fermion_force", "convert". */
+fg_status fg_timing_enable(fg_lattice *h, int on);
+fg_status fg_timing_reset(fg_lattice *h);
+fg_status fg_kernel_time(fg_lattice *h, const char *kernel_class, double *total_ms,
+                         long long *launches);
+
+/* Number of kernels this handle has launched since creation. */
+long long fg_launch_count(const fg_lattice *h);
+
+/* Block until all work queued on the handle's stream has finished. */
+fg_status fg_sync(fg_lattice *h);
+
+/* Device bytes held by the handle. */
+unsigned long long fg_device_bytes(const fg_lattice *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FG_LATTICE_H */

@@ -1,0 +1,320 @@
+// Host runtime behind the C ABI of include/fg_lattice.h.
+//
+// A handle owns the device fields of one lattice in checkerboard SoA order
+// (see fg_common.cuh), one CUDA stream, and a small pinned host buffer for
+// the scalars that cross back to the host (dH and the action sums).  The
+// integrator sequencer turns one MD step of Table 1 / section 3 into a list
+// of kicks (P), drifts (Q) and force-gradient kicks (G), merges adjacent
+// kicks and adjacent drifts of neighbouring steps, and launches it as fused
+// kernels: a kick followed by a drift is one launch (force, kick, drift of
+// the same link, written to a second link buffer); a force-gradient kick is
+// one launch that displaces the links along the force and one that kicks
+// with the force at the displaced links (then drifts, if a drift follows).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <new>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/fg_lattice.h"
+#include "fg_kernels.h"
+#include "fg_runtime.h"
+
+namespace fg {
+
+const char* kKernelClasses[] = {"gauge_force", "drift", "energy", "reduce", "momenta",
+                                "dslash", "cg_blas", "fermion_force", "convert"};
+
+// ---------------------------------------------------------------------------
+// Integrator sequences (Table 1 and section 3).
+std::vector<Op> step_ops(int integ, double alpha) {
+  std::vector<Op> v;
+  switch (integ) {
+    case FG_LEAPFROG:
+      v = {{'P', 0.5, 0}, {'Q', 1.0, 0}, {'P', 0.5, 0}};
+      break;
+    case FG_QPQ:
+      v = {{'Q', 0.5, 0}, {'P', 1.0, 0}, {'Q', 0.5, 0}};
+      break;
+    case FG_OMELYAN:
+      v = {{'P', alpha, 0}, {'Q', 0.5, 0}, {'P', 1.0 - 2.0 * alpha, 0}, {'Q', 0.5, 0}, {'P', alpha, 0}};
+      break;
+    case FG_FORCE_GRADIENT:
+      // middle: exp((48 dt S-hat - dt^3 {S,{S,T}}-hat)/72) -> kick 2/3 with the force
+      // evaluated at links displaced by 2 (1/72) / (2/3) dt^2 = dt^2/24 along the force
+      v = {{'P', 1.0 / 6.0, 0}, {'Q', 0.5, 0}, {'G', 2.0 / 3.0, 1.0 / 24.0}, {'Q', 0.5, 0},
+           {'P', 1.0 / 6.0, 0}};
+      break;
+    case FG_CAMPOSTRINI: {
+      const double w1 = 1.0 / (2.0 - std::cbrt(2.0));
+      const double w0 = 1.0 - 2.0 * w1;
+      v = {{'Q', w1 / 2, 0}, {'P', w1, 0}, {'Q', (w1 + w0) / 2, 0}, {'P', w0, 0},
+           {'Q', (w1 + w0) / 2, 0}, {'P', w1, 0}, {'Q', w1 / 2, 0}};
+      break;
+    }
+    default:
+      break;
+  }
+  return v;
+}
+
+std::vector<Op> trajectory_ops(int integ, double alpha, int nsteps, bool merge) {
+  std::vector<Op> out;
+  const std::vector<Op> one = step_ops(integ, alpha);
+  for (int n = 0; n < nsteps; ++n) {
+    for (const Op& o : one) {
+      if (merge && !out.empty() && out.back().kind == o.kind && o.kind != 'G') {
+        out.back().c += o.c;
+      } else {
+        out.push_back(o);
+      }
+    }
+  }
+  return out;
+}
+
+int count_forces(const std::vector<Op>& ops) {
+  int n = 0;
+  for (const Op& o : ops) n += (o.kind == 'P') ? 1 : (o.kind == 'G' ? 2 : 0);
+  return n;
+}
+
+// ---------------------------------------------------------------------------
+// Kernel timing with CUDA events.
+void Timer::begin(int cls, cudaStream_t st) {
+  if (!on) return;
+  Rec r;
+  r.cls = cls;
+  cudaEventCreate(&r.a);
+  cudaEventCreate(&r.b);
+  cudaEventRecord(r.a, st);
+  recs.push_back(r);
+}
+void Timer::end(cudaStream_t st) {
+  if (!on || recs.empty()) return;
+  cudaEventRecord(recs.back().b, st);
+}
+void Timer::reset() {
+  for (Rec& r : recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  recs.clear();
+}
+bool Timer::total(int cls, double* ms, long long* n) {
+  double t = 0;
+  long long c = 0;
+  for (Rec& r : recs) {
+    if (r.cls != cls) continue;
+    float x = 0;
+    if (cudaEventElapsedTime(&x, r.a, r.b) != cudaSuccess) return false;
+    t += x;
+    ++c;
+  }
+  *ms = t;
+  *n = c;
+  return true;
+}
+
+}  // namespace fg
+
+using namespace fg;
+
+// ---------------------------------------------------------------------------
+// C ABI.
+#define FG_CHECK_HANDLE(h) \
+  do {                     \
+    if (!(h)) return FG_EINVAL; \
+  } while (0)
+
+extern "C" {
+
+fg_status fg_params_default(fg_params* p) {
+  if (!p) return FG_EINVAL;
+  std::memset(p, 0, sizeof(*p));
+  p->dims[0] = p->dims[1] = p->dims[2] = p->dims[3] = 4;
+  p->beta = 6.0;
+  p->kappa = 0.0;
+  p->alpha = 0.1932;
+  p->precision = FG_FP64;
+  p->link_reals = 18;
+  p->reunitarize = -1;
+  p->cg_tol = 1e-10;
+  p->cg_tol_action = 1e-12;
+  p->cg_maxiter = 20000;
+  p->cg_delta = 0.1;
+  p->seed = 1;
+  p->cuda_stream = nullptr;
+  return FG_OK;
+}
+
+fg_status fg_lattice_create(const fg_params* p, fg_lattice** out) {
+  if (!out) return FG_EINVAL;
+  *out = nullptr;
+  if (!p) return FG_EINVAL;
+  for (int i = 0; i < 4; ++i)
+    if (p->dims[i] < 2 || (p->dims[i] & 1)) return FG_EINVAL;
+  const long long V = (long long)p->dims[0] * p->dims[1] * p->dims[2] * p->dims[3];
+  if (V > (1LL << 28)) return FG_EINVAL;  // 32-bit link indices: 4V < 2^31
+  if (p->precision != FG_FP64 && p->precision != FG_FP32) return FG_EINVAL;
+  if (p->link_reals != 18 && p->link_reals != 12) return FG_EINVAL;
+  if (!(p->beta >= 0.0) || !(p->kappa >= 0.0) || !(p->cg_tol > 0.0) || !(p->cg_tol_action > 0.0) ||
+      p->cg_maxiter < 1 || !(p->cg_delta > 0.0 && p->cg_delta < 1.0))
+    return FG_EINVAL;
+  fg_lattice* h = new (std::nothrow) fg_lattice();
+  if (!h) return FG_ENOMEM;
+  h->prm = *p;
+  if (h->prm.reunitarize < 0) h->prm.reunitarize = (p->precision == FG_FP32) ? 1 : 0;
+  if (!(h->prm.alpha > 0.0)) h->prm.alpha = 0.1932;
+  fg_status s = lattice_init(h);
+  if (s != FG_OK) {
+    delete h;
+    return s;
+  }
+  *out = h;
+  return FG_OK;
+}
+
+void fg_lattice_destroy(fg_lattice* h) {
+  if (!h) return;
+  delete h;
+}
+
+const char* fg_last_error(const fg_lattice* h) { return h ? h->err.c_str() : "null handle"; }
+
+fg_status fg_set_gauge(fg_lattice* h, const double* x) {
+  FG_CHECK_HANDLE(h);
+  if (!x) return h->fail(FG_EINVAL, "null gauge pointer");
+  return h->be->set_gauge(x);
+}
+fg_status fg_get_gauge(fg_lattice* h, double* x) {
+  FG_CHECK_HANDLE(h);
+  if (!x) return h->fail(FG_EINVAL, "null gauge pointer");
+  return h->be->get_gauge(x);
+}
+fg_status fg_set_momenta(fg_lattice* h, const double* x) {
+  FG_CHECK_HANDLE(h);
+  if (!x) return h->fail(FG_EINVAL, "null momenta pointer");
+  return h->be->set_momenta(x);
+}
+fg_status fg_get_momenta(fg_lattice* h, double* x) {
+  FG_CHECK_HANDLE(h);
+  if (!x) return h->fail(FG_EINVAL, "null momenta pointer");
+  return h->be->get_momenta(x);
+}
+fg_status fg_refresh_momenta(fg_lattice* h) {
+  FG_CHECK_HANDLE(h);
+  return h->be->refresh_momenta();
+}
+fg_status fg_set_pseudofermion(fg_lattice* h, const double* chi) {
+  FG_CHECK_HANDLE(h);
+  if (!chi) return h->fail(FG_EINVAL, "null chi pointer");
+  if (h->prm.kappa == 0.0) return h->fail(FG_ESTATE, "pure-gauge handle has no pseudofermion");
+  return h->be->set_pseudofermion(chi);
+}
+fg_status fg_refresh_pseudofermion(fg_lattice* h) {
+  FG_CHECK_HANDLE(h);
+  if (h->prm.kappa == 0.0) return h->fail(FG_ESTATE, "pure-gauge handle has no pseudofermion");
+  return h->be->refresh_pseudofermion();
+}
+fg_status fg_force(fg_lattice* h, double* f) {
+  FG_CHECK_HANDLE(h);
+  if (!f) return h->fail(FG_EINVAL, "null force pointer");
+  return h->be->force(f);
+}
+fg_status fg_action(fg_lattice* h, double* sg, double* sf, double* t) {
+  FG_CHECK_HANDLE(h);
+  return h->be->action(sg, sf, t);
+}
+fg_status fg_plaquette(fg_lattice* h, double* plaq) {
+  FG_CHECK_HANDLE(h);
+  if (!plaq) return h->fail(FG_EINVAL, "null pointer");
+  double sg = 0;
+  fg_status s = h->be->gauge_action(&sg);
+  if (s != FG_OK) return s;
+  const double nplaq = 6.0 * h->g.V;
+  *plaq = (h->prm.beta > 0) ? 1.0 - sg / (h->prm.beta * nplaq) : 0.0;
+  if (h->prm.beta == 0) return h->fail(FG_EINVAL, "plaquette needs beta > 0");
+  return FG_OK;
+}
+fg_status fg_md_step(fg_lattice* h, fg_integrator integ, double dt) {
+  FG_CHECK_HANDLE(h);
+  if ((int)integ < 0 || (int)integ > 4 || !std::isfinite(dt)) return h->fail(FG_EINVAL, "bad integrator or dt");
+  return h->be->md_step((int)integ, dt);
+}
+fg_status fg_fg_step(fg_lattice* h, double dt) { return fg_md_step(h, FG_FORCE_GRADIENT, dt); }
+
+fg_status fg_trajectory(fg_lattice* h, fg_integrator integ, double dt, double tau, int refresh,
+                        double u_accept, fg_traj_result* out) {
+  FG_CHECK_HANDLE(h);
+  if ((int)integ < 0 || (int)integ > 4) return h->fail(FG_EINVAL, "bad integrator");
+  if (!(dt > 0.0) || !(tau > 0.0)) return h->fail(FG_EINVAL, "dt and tau must be positive");
+  const double ns = tau / dt;
+  const int n = (int)std::llround(ns);
+  if (n < 1 || std::fabs(n * dt - tau) > 1e-9 * tau) return h->fail(FG_EINVAL, "tau must be a multiple of dt");
+  if (u_accept >= 1.0) return h->fail(FG_EINVAL, "u_accept must be < 1");
+  fg_traj_result r;
+  std::memset(&r, 0, sizeof(r));
+  fg_status s = h->be->trajectory((int)integ, dt, n, refresh, u_accept, &r);
+  if (out) *out = r;
+  return s;
+}
+fg_status fg_apply_mhat(fg_lattice* h, const double* in, double* out, int dagger) {
+  FG_CHECK_HANDLE(h);
+  if (!in || !out) return h->fail(FG_EINVAL, "null spinor pointer");
+  if (h->prm.kappa == 0.0) return h->fail(FG_ESTATE, "pure-gauge handle has no fermions");
+  return h->be->apply_mhat(in, out, dagger);
+}
+fg_status fg_cg_solve(fg_lattice* h, const double* b, double* x, fg_cg_result* res) {
+  FG_CHECK_HANDLE(h);
+  if (!b || !x) return h->fail(FG_EINVAL, "null spinor pointer");
+  if (h->prm.kappa == 0.0) return h->fail(FG_ESTATE, "pure-gauge handle has no fermions");
+  fg_cg_result r;
+  std::memset(&r, 0, sizeof(r));
+  fg_status s = h->be->cg_solve(b, x, &r);
+  if (res) *res = r;
+  return s;
+}
+fg_status fg_reunitarize(fg_lattice* h) {
+  FG_CHECK_HANDLE(h);
+  return h->be->reunitarize_all();
+}
+fg_status fg_timing_enable(fg_lattice* h, int on) {
+  FG_CHECK_HANDLE(h);
+  h->timer.on = on != 0;
+  return FG_OK;
+}
+fg_status fg_timing_reset(fg_lattice* h) {
+  FG_CHECK_HANDLE(h);
+  if (cudaStreamSynchronize(h->st) != cudaSuccess) return h->fail(FG_ECUDA, "sync failed");
+  h->timer.reset();
+  return FG_OK;
+}
+fg_status fg_kernel_time(fg_lattice* h, const char* cls, double* ms, long long* n) {
+  FG_CHECK_HANDLE(h);
+  if (!cls || !ms || !n) return h->fail(FG_EINVAL, "null argument");
+  int id = -1;
+  for (int i = 0; i < kNumKernelClasses; ++i)
+    if (std::strcmp(cls, kKernelClasses[i]) == 0) id = i;
+  if (id < 0) return h->fail(FG_EINVAL, "unknown kernel class");
+  cudaError_t e = cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) return h->fail(FG_ECUDA, cudaGetErrorString(e));
+  if (!h->timer.total(id, ms, n)) return h->fail(FG_ECUDA, "event timing failed");
+  return FG_OK;
+}
+long long fg_launch_count(const fg_lattice* h) { return h ? h->launches : -1; }
+fg_status fg_sync(fg_lattice* h) {
+  FG_CHECK_HANDLE(h);
+  cudaError_t e = cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) return h->fail(FG_ECUDA, cudaGetErrorString(e));
+  return FG_OK;
+}
+unsigned long long fg_device_bytes(const fg_lattice* h) { return h ? h->dev_bytes : 0ULL; }
+
+}  // extern "C"

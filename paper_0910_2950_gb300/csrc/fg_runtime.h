@@ -1,0 +1,92 @@
+// Host runtime types shared by the C ABI (fg_lattice.cu) and the backends.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/fg_lattice.h"
+#include "fg_kernels.h"
+
+namespace fg {
+
+// One sub-step of an integrator: 'P' kick exp(c dt S-hat), 'Q' drift
+// exp(c dt T-hat), 'G' force-gradient kick with coefficient c and the force
+// taken at links displaced by d dt^2 along the force.
+struct Op {
+  char kind;
+  double c;
+  double d;
+};
+
+std::vector<Op> step_ops(int integ, double alpha);
+std::vector<Op> trajectory_ops(int integ, double alpha, int nsteps, bool merge);
+int count_forces(const std::vector<Op>& ops);
+
+enum KernelClass {
+  KC_GAUGE_FORCE = 0, KC_DRIFT, KC_ENERGY, KC_REDUCE, KC_MOMENTA,
+  KC_DSLASH, KC_CG_BLAS, KC_FERMION_FORCE, KC_CONVERT
+};
+constexpr int kNumKernelClasses = 9;
+extern const char* kKernelClasses[];
+
+struct Timer {
+  struct Rec {
+    int cls;
+    cudaEvent_t a, b;
+  };
+  bool on = false;
+  std::vector<Rec> recs;
+  void begin(int cls, cudaStream_t st);
+  void end(cudaStream_t st);
+  void reset();
+  bool total(int cls, double* ms, long long* n);
+  ~Timer() { reset(); }
+};
+
+struct IBackend {
+  virtual ~IBackend() {}
+  virtual fg_status set_gauge(const double* host) = 0;
+  virtual fg_status get_gauge(double* host) = 0;
+  virtual fg_status set_momenta(const double* host) = 0;
+  virtual fg_status get_momenta(double* host) = 0;
+  virtual fg_status refresh_momenta() = 0;
+  virtual fg_status set_pseudofermion(const double* chi) = 0;
+  virtual fg_status refresh_pseudofermion() = 0;
+  virtual fg_status force(double* host_f8) = 0;
+  virtual fg_status gauge_action(double* sg) = 0;
+  virtual fg_status action(double* sg, double* sf, double* t) = 0;
+  virtual fg_status md_step(int integ, double dt) = 0;
+  virtual fg_status trajectory(int integ, double dt, int nsteps, int refresh, double u_accept,
+                               fg_traj_result* r) = 0;
+  virtual fg_status apply_mhat(const double* in, double* out, int dagger) = 0;
+  virtual fg_status cg_solve(const double* b, double* x, fg_cg_result* r) = 0;
+  virtual fg_status reunitarize_all() = 0;
+};
+
+}  // namespace fg
+
+struct fg_lattice {
+  fg_params prm;
+  fg::GeomH g;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  std::string err;
+  std::unique_ptr<fg::IBackend> be;
+  fg::Timer timer;
+  long long launches = 0;
+  unsigned long long dev_bytes = 0;
+  unsigned long long accept_draws = 0;
+  fg_status fail(fg_status s, const std::string& m) {
+    err = m;
+    return s;
+  }
+  ~fg_lattice();
+};
+
+namespace fg {
+// Creates the stream and the backend for h->prm (defined in backend.cu).
+fg_status lattice_init(fg_lattice* h);
+}  // namespace fg

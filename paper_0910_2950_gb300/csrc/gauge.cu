@@ -1,0 +1,453 @@
+// Pure-gauge kernels of the force-gradient HMC step (sm_103a).
+//
+//  * gauge_force_kernel: Wilson staple force F^a = (beta/6) Im Tr(lambda^a U A)
+//    (the S-hat vector field of section 3), fused with what the integrator does
+//    next on the same link: store it, kick the momentum, kick then drift the
+//    link, or displace the link along the force for the force-gradient step
+//    of Table 1 (U' = exp(-i dt^2/24 F) U).
+//  * drift_kernel: the exact T-hat flow U <- exp(i c P) U (section 2).
+//  * energy_kernel: per-site T(x) + S_G(x) in FP64, block partial sums for the
+//    dH of section 5 (summed as site-by-site differences).
+//  * refresh_momenta_kernel: unit-Gaussian momenta from a counter-based RNG.
+//
+// One thread per link; a block is 64 consecutive checkerboard sites x 4
+// directions, so the four links of a site and their staples share L1/L2 lines.
+#include "fg_common.cuh"
+#include "fg_kernels.h"
+
+namespace fg {
+
+static inline Geom to_dev(const GeomH& h) {
+  Geom g;
+  for (int i = 0; i < 4; ++i) g.L[i] = h.L[i];
+  g.Lxh = h.Lxh; g.Vh = h.Vh; g.V = h.V;
+  return g;
+}
+
+constexpr int kSitesPerBlock = 64;
+
+template <typename R, int NC>
+__device__ __forceinline__ M3<R> staple_sum(const Gauge<R, NC>& U, const Geom& g, const int c[4],
+                                            int s, int mu) {
+  M3<R> a;
+  zero(a);
+#pragma unroll 1
+  for (int k = 1; k < 4; ++k) {
+    const int nu = (mu + k) & 3;
+    const int s_pmu = cb_neighbor(g, c, mu, +1);
+    const int s_pnu = cb_neighbor(g, c, nu, +1);
+    const int s_mnu = cb_neighbor(g, c, nu, -1);
+    const int s_pmu_mnu = cb_neighbor2(g, c, mu, +1, nu, -1);
+    {
+      // upper: U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag
+      const M3<R> t = mul_nd(U.load(nu, s_pmu), U.load(mu, s_pnu));
+      mac_nd(a, t, U.load(nu, s));
+    }
+    {
+      // lower: U_nu(x+mu-nu)^dag U_mu(x-nu)^dag U_nu(x-nu) = (U_mu(x-nu) U_nu(x+mu-nu))^dag U_nu(x-nu)
+      const M3<R> t = mul(U.load(mu, s_mnu), U.load(nu, s_pmu_mnu));
+      mac_dn(a, t, U.load(nu, s_mnu));
+    }
+  }
+  return a;
+}
+
+template <typename R, int NC, int MODE>
+__global__ void __launch_bounds__(256) gauge_force_kernel(Gauge<R, NC> U, Mom<R> P, Mom<R> F,
+                                                          Mom<R> FF, Gauge<R, NC> Ubase,
+                                                          Gauge<R, NC> Uout, Geom g, R beta6,
+                                                          R ckick, R cdrift, R cdisp, int reunit) {
+  const int s = blockIdx.x * kSitesPerBlock + threadIdx.x;
+  const int mu = threadIdx.y;
+  if (s >= g.V) return;
+  int c[4], par;
+  cb_coords(g, s, c, par);
+  const M3<R> a = staple_sum(U, g, c, s, mu);
+  const M3<R> ul = U.load(mu, s);
+  const M3<R> omega = mul(ul, a);
+  R f[8];
+  im_tr_gellmann(omega, f);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) f[k] *= beta6;
+  if (FF.p != nullptr) {
+    R ff[8];
+    FF.load(mu, s, ff);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) f[k] += ff[k];
+  }
+  if (MODE == FM_STORE) {
+    F.store(mu, s, f);
+  } else if (MODE == FM_KICK || MODE == FM_KICK_DRIFT) {
+    R p[8];
+    P.load(mu, s, p);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) p[k] = fma(-ckick, f[k], p[k]);
+    P.store(mu, s, p);
+    if (MODE == FM_KICK_DRIFT) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) p[k] *= cdrift;
+      const M3<R> e = expi_herm(alg_to_mat(p));
+      const M3<R> ub = (Ubase.p == U.p) ? ul : Ubase.load(mu, s);
+      M3<R> un = mul(e, ub);
+      if (reunit) reunitarize(un);
+      Uout.store(mu, s, un);
+    }
+  } else {  // FM_DISPLACE
+#pragma unroll
+    for (int k = 0; k < 8; ++k) f[k] *= -cdisp;
+    const M3<R> e = expi_herm(alg_to_mat(f));
+    M3<R> un = mul(e, ul);
+    if (reunit) reunitarize(un);
+    Uout.store(mu, s, un);
+  }
+}
+
+template <typename R, int NC>
+__global__ void __launch_bounds__(256) drift_kernel(Gauge<R, NC> Uin, Mom<R> P, Gauge<R, NC> Uout,
+                                                    int V, R c, int reunit) {
+  const int s = blockIdx.x * kSitesPerBlock + threadIdx.x;
+  const int mu = threadIdx.y;
+  if (s >= V) return;
+  R p[8];
+  P.load(mu, s, p);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) p[k] *= c;
+  const M3<R> e = expi_herm(alg_to_mat(p));
+  M3<R> un = mul(e, Uin.load(mu, s));
+  if (reunit) reunitarize(un);
+  Uout.store(mu, s, un);
+}
+
+template <typename R, int NC>
+__global__ void __launch_bounds__(256) unit_links_kernel(Gauge<R, NC> U, int V) {
+  const int s = blockIdx.x * kSitesPerBlock + threadIdx.x;
+  const int mu = threadIdx.y;
+  if (s >= V) return;
+  M3<R> u;
+  identity(u);
+  U.store(mu, s, u);
+}
+
+template <typename R, int NC>
+__global__ void __launch_bounds__(256) reunitarize_kernel(Gauge<R, NC> U, int V) {
+  const int s = blockIdx.x * kSitesPerBlock + threadIdx.x;
+  const int mu = threadIdx.y;
+  if (s >= V) return;
+  M3<R> u = U.load(mu, s);
+  reunitarize(u);
+  U.store(mu, s, u);
+}
+
+constexpr int kEnergyThreads = 256;
+
+template <typename R, int NC>
+__global__ void __launch_bounds__(kEnergyThreads) energy_kernel(Gauge<R, NC> U, Mom<R> P, Geom g,
+                                                                double beta, int mode,
+                                                                double* __restrict__ h0,
+                                                                double* __restrict__ partial) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  double v[3] = {0.0, 0.0, 0.0};  // S_G, T, dh
+  if (s < g.V) {
+    int c[4], par;
+    cb_coords(g, s, c, par);
+    double t = 0.0;
+    if (P.p != nullptr) {
+#pragma unroll 1
+      for (int mu = 0; mu < 4; ++mu) {
+        R p[8];
+        P.load(mu, s, p);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) t += double(p[k]) * double(p[k]);
+      }
+      t *= 0.5;
+    }
+    double sg = 0.0;
+#pragma unroll 1
+    for (int mu = 0; mu < 4; ++mu) {
+      const M3<R> umu = U.load(mu, s);
+#pragma unroll 1
+      for (int nu = mu + 1; nu < 4; ++nu) {
+        const M3<R> a = mul(umu, U.load(nu, cb_neighbor(g, c, mu, +1)));
+        const M3<R> b = mul(U.load(nu, s), U.load(mu, cb_neighbor(g, c, nu, +1)));
+        sg += 1.0 - double(re_tr_mul_nd(a, b)) * (1.0 / 3.0);
+      }
+    }
+    sg *= beta;
+    v[0] = sg;
+    v[1] = t;
+    const double h = sg + t;
+    if (mode == 0) h0[s] = h;
+    else if (mode == 1) v[2] = h - h0[s];
+  }
+  block_reduce_store<3>(v, partial, gridDim.x);
+}
+
+__global__ void __launch_bounds__(1024) reduce_kernel(const double* __restrict__ partial, int nblocks,
+                                                      int nv, double* __restrict__ out,
+                                                      int accumulate) {
+  __shared__ double sh[32];
+  for (int k = 0; k < nv; ++k) {
+    double x = 0.0;
+    for (int i = threadIdx.x; i < nblocks; i += blockDim.x) x += partial[(size_t)k * nblocks + i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sh[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      x = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      if (lane == 0) out[k] = accumulate ? out[k] + x : x;
+    }
+    __syncthreads();
+  }
+}
+
+// Box-Muller on two 32-bit uniforms: u1 in (0, 1], u2 in [0, 1).
+template <typename R>
+__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, R& z0, R& z1) {
+  const double u1 = ((double)a + 1.0) * 2.3283064365386963e-10;
+  const double u2 = (double)b * 2.3283064365386963e-10;
+  const double r = sqrt(-2.0 * log(u1));
+  double sn, cs;
+  sincospi(2.0 * u2, &sn, &cs);
+  z0 = R(r * cs);
+  z1 = R(r * sn);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) refresh_momenta_kernel(Mom<R> P, Geom g, uint32_t k0,
+                                                              uint32_t k1, uint32_t draw) {
+  const int s = blockIdx.x * kSitesPerBlock + threadIdx.x;
+  const int mu = threadIdx.y;
+  if (s >= g.V) return;
+  int c[4], par;
+  cb_coords(g, s, c, par);
+  const uint32_t lex = (uint32_t)(c[0] + g.L[0] * (c[1] + g.L[1] * (c[2] + g.L[2] * c[3])));
+  R p[8];
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    uint32_t ctr[4] = {lex * 4u + (uint32_t)mu, draw, 0u /* stream: momenta */, (uint32_t)half};
+    Philox::rounds(ctr, k0, k1);
+    box_muller<R>(ctr[0], ctr[1], p[4 * half + 0], p[4 * half + 1]);
+    box_muller<R>(ctr[2], ctr[3], p[4 * half + 2], p[4 * half + 3]);
+  }
+  P.store(mu, s, p);
+}
+
+template <typename R, int NC>
+__global__ void gauge_to_device_kernel(const double* __restrict__ canon, Gauge<R, NC> U, Geom g) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;  // (lex, mu)
+  if (i >= 4 * g.V) return;
+  const int lex = i >> 2, mu = i & 3;
+  int c[4];
+  int r = lex;
+  c[0] = r % g.L[0]; r /= g.L[0];
+  c[1] = r % g.L[1]; r /= g.L[1];
+  c[2] = r % g.L[2]; c[3] = r / g.L[2];
+  const int s = cb_index(g, c);
+  M3<R> m;
+  const double* src = canon + (size_t)i * 18;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) m.e[k / 3][k % 3] = cx<R>(R(src[2 * k]), R(src[2 * k + 1]));
+  U.store(mu, s, m);
+}
+
+template <typename R, int NC>
+__global__ void gauge_to_canon_kernel(Gauge<R, NC> U, double* __restrict__ canon, Geom g) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 4 * g.V) return;
+  const int lex = i >> 2, mu = i & 3;
+  int c[4];
+  int r = lex;
+  c[0] = r % g.L[0]; r /= g.L[0];
+  c[1] = r % g.L[1]; r /= g.L[1];
+  c[2] = r % g.L[2]; c[3] = r / g.L[2];
+  const M3<R> m = U.load(mu, cb_index(g, c));
+  double* dst = canon + (size_t)i * 18;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    dst[2 * k] = m.e[k / 3][k % 3].re;
+    dst[2 * k + 1] = m.e[k / 3][k % 3].im;
+  }
+}
+
+template <typename R>
+__global__ void mom_to_device_kernel(const double* __restrict__ canon, Mom<R> P, Geom g) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 4 * g.V) return;
+  const int lex = i >> 2, mu = i & 3;
+  int c[4];
+  int r = lex;
+  c[0] = r % g.L[0]; r /= g.L[0];
+  c[1] = r % g.L[1]; r /= g.L[1];
+  c[2] = r % g.L[2]; c[3] = r / g.L[2];
+  R p[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) p[k] = R(canon[(size_t)i * 8 + k]);
+  P.store(mu, cb_index(g, c), p);
+}
+
+template <typename R>
+__global__ void mom_to_canon_kernel(Mom<R> P, double* __restrict__ canon, Geom g) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 4 * g.V) return;
+  const int lex = i >> 2, mu = i & 3;
+  int c[4];
+  int r = lex;
+  c[0] = r % g.L[0]; r /= g.L[0];
+  c[1] = r % g.L[1]; r /= g.L[1];
+  c[2] = r % g.L[2]; c[3] = r / g.L[2];
+  R p[8];
+  P.load(mu, cb_index(g, c), p);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) canon[(size_t)i * 8 + k] = p[k];
+}
+
+// ---------------------------------------------------------------------------
+// Launchers.
+template <typename R, int NC>
+static Gauge<R, NC> gauge_of(const void* p, int V) {
+  Gauge<R, NC> u;
+  u.p = (typename Vec2<R>::T*)p;
+  u.V = V;
+  return u;
+}
+template <typename R>
+static Mom<R> mom_of(const void* p, int V) {
+  Mom<R> m;
+  m.p = (typename Vec2<R>::T*)p;
+  m.V = V;
+  return m;
+}
+
+static inline dim3 link_grid(int V) { return dim3((V + kSitesPerBlock - 1) / kSitesPerBlock); }
+static inline dim3 link_block() { return dim3(kSitesPerBlock, 4); }
+
+template <typename R, int NC>
+cudaError_t launch_gauge_force(const GeomH& gh, int mode, const ForceArgs& a, cudaStream_t st) {
+  const Geom g = to_dev(gh);
+  const int V = g.V;
+  auto U = gauge_of<R, NC>(a.U, V);
+  auto P = mom_of<R>(a.P, V);
+  auto F = mom_of<R>(a.F, V);
+  auto FF = mom_of<R>(a.FF, V);
+  auto Ub = gauge_of<R, NC>(a.Ubase, V);
+  auto Uo = gauge_of<R, NC>(a.Uout, V);
+  const R b6 = R(a.beta / 6.0);
+  switch (mode) {
+    case FM_STORE:
+      gauge_force_kernel<R, NC, FM_STORE><<<link_grid(V), link_block(), 0, st>>>(
+          U, P, F, FF, Ub, Uo, g, b6, R(a.ckick), R(a.cdrift), R(a.cdisp), a.reunit);
+      break;
+    case FM_KICK:
+      gauge_force_kernel<R, NC, FM_KICK><<<link_grid(V), link_block(), 0, st>>>(
+          U, P, F, FF, Ub, Uo, g, b6, R(a.ckick), R(a.cdrift), R(a.cdisp), a.reunit);
+      break;
+    case FM_KICK_DRIFT:
+      gauge_force_kernel<R, NC, FM_KICK_DRIFT><<<link_grid(V), link_block(), 0, st>>>(
+          U, P, F, FF, Ub, Uo, g, b6, R(a.ckick), R(a.cdrift), R(a.cdisp), a.reunit);
+      break;
+    case FM_DISPLACE:
+      gauge_force_kernel<R, NC, FM_DISPLACE><<<link_grid(V), link_block(), 0, st>>>(
+          U, P, F, FF, Ub, Uo, g, b6, R(a.ckick), R(a.cdrift), R(a.cdisp), a.reunit);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <typename R, int NC>
+cudaError_t launch_drift(const GeomH& gh, const void* Uin, const void* P, void* Uout, double c,
+                         int reunit, cudaStream_t st) {
+  drift_kernel<R, NC><<<link_grid(gh.V), link_block(), 0, st>>>(
+      gauge_of<R, NC>(Uin, gh.V), mom_of<R>(P, gh.V), gauge_of<R, NC>(Uout, gh.V), gh.V, R(c), reunit);
+  return cudaGetLastError();
+}
+
+template <typename R, int NC>
+cudaError_t launch_unit_links(const GeomH& gh, void* U, cudaStream_t st) {
+  unit_links_kernel<R, NC><<<link_grid(gh.V), link_block(), 0, st>>>(gauge_of<R, NC>(U, gh.V), gh.V);
+  return cudaGetLastError();
+}
+
+template <typename R, int NC>
+cudaError_t launch_reunitarize(const GeomH& gh, void* U, cudaStream_t st) {
+  reunitarize_kernel<R, NC><<<link_grid(gh.V), link_block(), 0, st>>>(gauge_of<R, NC>(U, gh.V), gh.V);
+  return cudaGetLastError();
+}
+
+template <typename R, int NC>
+cudaError_t launch_energy(const GeomH& gh, const void* U, const void* P, double beta, int mode,
+                          double* h0, double* partial, int* nblocks, cudaStream_t st) {
+  const int nb = (gh.V + kEnergyThreads - 1) / kEnergyThreads;
+  *nblocks = nb;
+  energy_kernel<R, NC><<<nb, kEnergyThreads, 0, st>>>(gauge_of<R, NC>(U, gh.V), mom_of<R>(P, gh.V),
+                                                      to_dev(gh), beta, mode, h0, partial);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(const double* partial, int nblocks, int nv, double* out, int accumulate,
+                          cudaStream_t st) {
+  reduce_kernel<<<1, 1024, 0, st>>>(partial, nblocks, nv, out, accumulate);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_refresh_momenta(const GeomH& gh, void* P, uint64_t seed, uint32_t draw,
+                                   cudaStream_t st) {
+  refresh_momenta_kernel<R><<<link_grid(gh.V), link_block(), 0, st>>>(
+      mom_of<R>(P, gh.V), to_dev(gh), (uint32_t)seed, (uint32_t)(seed >> 32), draw);
+  return cudaGetLastError();
+}
+
+template <typename R, int NC>
+cudaError_t launch_gauge_to_device(const GeomH& gh, const double* canon, void* U, cudaStream_t st) {
+  gauge_to_device_kernel<R, NC><<<(4 * gh.V + 255) / 256, 256, 0, st>>>(canon, gauge_of<R, NC>(U, gh.V),
+                                                                       to_dev(gh));
+  return cudaGetLastError();
+}
+template <typename R, int NC>
+cudaError_t launch_gauge_to_canon(const GeomH& gh, const void* U, double* canon, cudaStream_t st) {
+  gauge_to_canon_kernel<R, NC><<<(4 * gh.V + 255) / 256, 256, 0, st>>>(gauge_of<R, NC>(U, gh.V), canon,
+                                                                      to_dev(gh));
+  return cudaGetLastError();
+}
+template <typename R>
+cudaError_t launch_mom_to_device(const GeomH& gh, const double* canon, void* P, cudaStream_t st) {
+  mom_to_device_kernel<R><<<(4 * gh.V + 255) / 256, 256, 0, st>>>(canon, mom_of<R>(P, gh.V), to_dev(gh));
+  return cudaGetLastError();
+}
+template <typename R>
+cudaError_t launch_mom_to_canon(const GeomH& gh, const void* P, double* canon, cudaStream_t st) {
+  mom_to_canon_kernel<R><<<(4 * gh.V + 255) / 256, 256, 0, st>>>(mom_of<R>(P, gh.V), canon, to_dev(gh));
+  return cudaGetLastError();
+}
+
+#define FG_INST_RNC(R, NC)                                                                          \
+  template cudaError_t launch_gauge_force<R, NC>(const GeomH&, int, const ForceArgs&, cudaStream_t); \
+  template cudaError_t launch_drift<R, NC>(const GeomH&, const void*, const void*, void*, double,   \
+                                           int, cudaStream_t);                                      \
+  template cudaError_t launch_reunitarize<R, NC>(const GeomH&, void*, cudaStream_t);                \
+  template cudaError_t launch_unit_links<R, NC>(const GeomH&, void*, cudaStream_t);                 \
+  template cudaError_t launch_energy<R, NC>(const GeomH&, const void*, const void*, double, int,    \
+                                            double*, double*, int*, cudaStream_t);                  \
+  template cudaError_t launch_gauge_to_device<R, NC>(const GeomH&, const double*, void*,            \
+                                                     cudaStream_t);                                 \
+  template cudaError_t launch_gauge_to_canon<R, NC>(const GeomH&, const void*, double*, cudaStream_t);
+
+FG_INST_RNC(double, 9)
+FG_INST_RNC(double, 6)
+FG_INST_RNC(float, 9)
+FG_INST_RNC(float, 6)
+
+template cudaError_t launch_refresh_momenta<double>(const GeomH&, void*, uint64_t, uint32_t, cudaStream_t);
+template cudaError_t launch_refresh_momenta<float>(const GeomH&, void*, uint64_t, uint32_t, cudaStream_t);
+template cudaError_t launch_mom_to_device<double>(const GeomH&, const double*, void*, cudaStream_t);
+template cudaError_t launch_mom_to_device<float>(const GeomH&, const double*, void*, cudaStream_t);
+template cudaError_t launch_mom_to_canon<double>(const GeomH&, const void*, double*, cudaStream_t);
+template cudaError_t launch_mom_to_canon<float>(const GeomH&, const void*, double*, cudaStream_t);
+
+}  // namespace fg

@@ -1,0 +1,271 @@
+"""ctypes binding of ``libfg_lattice.so`` (C ABI in ``include/fg_lattice.h``).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  The names follow the C ABI (``fg_set_gauge`` -> ``Lattice.set_gauge``
+and so on).  Host arrays use the canonical FP64 layouts documented in
+``paper_0910_2950_gb300.inputs`` and in the header.  If the library is
+missing or cannot be loaded, every entry point raises: there is no CPU
+fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libfg_lattice.so")
+
+FG_OK, FG_EINVAL, FG_ENOMEM, FG_ECUDA, FG_ENOCONV, FG_ETIMEOUT, FG_ESTATE = range(7)
+STATUS_NAMES = {0: "FG_OK", 1: "FG_EINVAL", 2: "FG_ENOMEM", 3: "FG_ECUDA", 4: "FG_ENOCONV",
+                5: "FG_ETIMEOUT", 6: "FG_ESTATE"}
+INTEGRATORS = {"leapfrog": 0, "omelyan": 1, "fg": 2, "force_gradient": 2, "campostrini": 3, "qpq": 4}
+PRECISIONS = {"fp64": 0, "fp32": 1}
+
+# Every function the header declares, with its ctypes signature.
+_vp, _dp, _i, _d = C.c_void_p, C.POINTER(C.c_double), C.c_int, C.c_double
+
+
+class FgParams(C.Structure):
+    _fields_ = [("dims", C.c_int * 4), ("beta", C.c_double), ("kappa", C.c_double),
+                ("alpha", C.c_double), ("precision", C.c_int), ("link_reals", C.c_int),
+                ("reunitarize", C.c_int), ("cg_tol", C.c_double), ("cg_tol_action", C.c_double),
+                ("cg_maxiter", C.c_int), ("cg_delta", C.c_double), ("seed", C.c_ulonglong),
+                ("cuda_stream", C.c_void_p)]
+
+
+class FgTrajResult(C.Structure):
+    _fields_ = [("dH", C.c_double), ("H0", C.c_double), ("H1", C.c_double),
+                ("S_gauge0", C.c_double), ("S_gauge1", C.c_double),
+                ("S_ferm0", C.c_double), ("S_ferm1", C.c_double),
+                ("T0", C.c_double), ("T1", C.c_double), ("accepted", C.c_int),
+                ("n_steps", C.c_int), ("n_force", C.c_int), ("n_solves", C.c_int),
+                ("cg_iters", C.c_longlong)]
+
+
+class FgCgResult(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("reliable_updates", C.c_int),
+                ("true_residual", C.c_double)]
+
+
+SIGNATURES = {
+    "fg_params_default": (_i, [C.POINTER(FgParams)]),
+    "fg_lattice_create": (_i, [C.POINTER(FgParams), C.POINTER(_vp)]),
+    "fg_lattice_destroy": (None, [_vp]),
+    "fg_last_error": (C.c_char_p, [_vp]),
+    "fg_set_gauge": (_i, [_vp, _dp]),
+    "fg_get_gauge": (_i, [_vp, _dp]),
+    "fg_set_momenta": (_i, [_vp, _dp]),
+    "fg_get_momenta": (_i, [_vp, _dp]),
+    "fg_refresh_momenta": (_i, [_vp]),
+    "fg_set_pseudofermion": (_i, [_vp, _dp]),
+    "fg_refresh_pseudofermion": (_i, [_vp]),
+    "fg_force": (_i, [_vp, _dp]),
+    "fg_action": (_i, [_vp, _dp, _dp, _dp]),
+    "fg_plaquette": (_i, [_vp, _dp]),
+    "fg_md_step": (_i, [_vp, _i, _d]),
+    "fg_fg_step": (_i, [_vp, _d]),
+    "fg_trajectory": (_i, [_vp, _i, _d, _d, _i, _d, C.POINTER(FgTrajResult)]),
+    "fg_apply_mhat": (_i, [_vp, _dp, _dp, _i]),
+    "fg_cg_solve": (_i, [_vp, _dp, _dp, C.POINTER(FgCgResult)]),
+    "fg_reunitarize": (_i, [_vp]),
+    "fg_timing_enable": (_i, [_vp, _i]),
+    "fg_timing_reset": (_i, [_vp]),
+    "fg_kernel_time": (_i, [_vp, C.c_char_p, _dp, C.POINTER(C.c_longlong)]),
+    "fg_launch_count": (C.c_longlong, [_vp]),
+    "fg_sync": (_i, [_vp]),
+    "fg_device_bytes": (C.c_ulonglong, [_vp]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libfg_lattice.so and attach signatures; raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with `python -m paper_0910_2950_gb300.build`")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class FgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+def _f64(a, shape):
+    a = np.ascontiguousarray(a)
+    if a.dtype == np.complex128:
+        a = a.view(np.float64)
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.size != int(np.prod(shape)):
+        raise ValueError(f"expected {int(np.prod(shape))} doubles, got {a.size}")
+    return a
+
+
+class Lattice:
+    """One lattice handle (``fg_lattice*``)."""
+
+    def __init__(self, dims, beta=6.0, kappa=0.0, precision="fp64", link_reals=18, alpha=0.1932,
+                 cg_tol=1e-10, cg_tol_action=1e-12, cg_maxiter=20000, cg_delta=0.1, seed=1,
+                 reunitarize=None, stream=None):
+        lib = load()
+        p = FgParams()
+        _check(lib.fg_params_default(C.byref(p)), None)
+        for i, d in enumerate(dims):
+            p.dims[i] = int(d)
+        p.beta, p.kappa, p.alpha = float(beta), float(kappa), float(alpha)
+        p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        p.link_reals = int(link_reals)
+        p.cg_tol, p.cg_tol_action, p.cg_maxiter, p.cg_delta = cg_tol, cg_tol_action, cg_maxiter, cg_delta
+        p.seed = int(seed)
+        p.reunitarize = -1 if reunitarize is None else int(reunitarize)
+        p.cuda_stream = stream
+        self._lib = lib
+        self._h = C.c_void_p()
+        st = lib.fg_lattice_create(C.byref(p), C.byref(self._h))
+        if st != FG_OK:
+            raise FgError(st, "fg_lattice_create failed")
+        self.dims = tuple(int(d) for d in dims)
+        self.V = int(np.prod(self.dims))
+        lx, ly, lz, lt = self.dims
+        self.site_shape = (lt, lz, ly, lx)
+
+    # -- lifetime
+    def close(self):
+        if self._h:
+            self._lib.fg_lattice_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _call(self, name, *args):
+        st = getattr(self._lib, name)(self._h, *args)
+        if st != FG_OK:
+            raise FgError(st, self._lib.fg_last_error(self._h).decode())
+        return st
+
+    # -- fields
+    def set_gauge(self, u):
+        a = _f64(u, (self.V, 4, 18))
+        self._call("fg_set_gauge", _ptr(a))
+
+    def get_gauge(self):
+        a = np.empty(self.V * 4 * 18, dtype=np.float64)
+        self._call("fg_get_gauge", _ptr(a))
+        return a.view(np.complex128).reshape(self.site_shape + (4, 3, 3))
+
+    def set_momenta(self, p):
+        self._call("fg_set_momenta", _ptr(_f64(p, (self.V, 4, 8))))
+
+    def get_momenta(self):
+        a = np.empty(self.V * 32, dtype=np.float64)
+        self._call("fg_get_momenta", _ptr(a))
+        return a.reshape(self.site_shape + (4, 8))
+
+    def refresh_momenta(self):
+        self._call("fg_refresh_momenta")
+
+    def set_pseudofermion(self, chi_even):
+        self._call("fg_set_pseudofermion", _ptr(_f64(chi_even, (self.V // 2, 24))))
+
+    def refresh_pseudofermion(self):
+        self._call("fg_refresh_pseudofermion")
+
+    # -- observables
+    def force(self):
+        a = np.empty(self.V * 32, dtype=np.float64)
+        self._call("fg_force", _ptr(a))
+        return a.reshape(self.site_shape + (4, 8))
+
+    def action(self):
+        sg, sf, t = C.c_double(), C.c_double(), C.c_double()
+        self._call("fg_action", C.byref(sg), C.byref(sf), C.byref(t))
+        return sg.value, sf.value, t.value
+
+    def plaquette(self):
+        x = C.c_double()
+        self._call("fg_plaquette", C.byref(x))
+        return x.value
+
+    # -- molecular dynamics
+    def md_step(self, integrator, dt):
+        self._call("fg_md_step", INTEGRATORS[integrator], float(dt))
+
+    def fg_step(self, dt):
+        self._call("fg_fg_step", float(dt))
+
+    def trajectory(self, integrator, dt, tau=1.0, refresh=True, u_accept=-1.0):
+        r = FgTrajResult()
+        self._call("fg_trajectory", INTEGRATORS[integrator], float(dt), float(tau), int(bool(refresh)),
+                   float(u_accept), C.byref(r))
+        return {k: getattr(r, k) for k, _ in FgTrajResult._fields_}
+
+    # -- fermion building blocks
+    def apply_mhat(self, x_even, dagger=False):
+        a = _f64(x_even, (self.V // 2, 24))
+        out = np.empty(self.V // 2 * 24, dtype=np.float64)
+        self._call("fg_apply_mhat", _ptr(a), _ptr(out), int(bool(dagger)))
+        return out.view(np.complex128).reshape(self.V // 2, 4, 3)
+
+    def cg_solve(self, b_even):
+        a = _f64(b_even, (self.V // 2, 24))
+        out = np.empty(self.V // 2 * 24, dtype=np.float64)
+        r = FgCgResult()
+        self._call("fg_cg_solve", _ptr(a), _ptr(out), C.byref(r))
+        return out.view(np.complex128).reshape(self.V // 2, 4, 3), {
+            k: getattr(r, k) for k, _ in FgCgResult._fields_}
+
+    def reunitarize(self):
+        self._call("fg_reunitarize")
+
+    # -- instrumentation
+    def timing(self, on=True):
+        self._call("fg_timing_enable", int(bool(on)))
+
+    def timing_reset(self):
+        self._call("fg_timing_reset")
+
+    def kernel_time(self, cls):
+        ms, n = C.c_double(), C.c_longlong()
+        self._call("fg_kernel_time", cls.encode(), C.byref(ms), C.byref(n))
+        return ms.value, n.value
+
+    def launch_count(self):
+        return int(self._lib.fg_launch_count(self._h))
+
+    def sync(self):
+        self._call("fg_sync")
+
+    def device_bytes(self):
+        return int(self._lib.fg_device_bytes(self._h))
+
+
+def _check(st, h):
+    if st != FG_OK:
+        raise FgError(st, "call failed")

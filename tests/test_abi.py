@@ -1,0 +1,76 @@
+"""The C-ABI library builds, loads and exports every symbol include/fg_lattice.h declares.
+
+These run without a GPU: nothing here launches a kernel.
+"""
+
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_0910_2950_gb300 import build, fg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _header_functions():
+    names = []
+    for hdr in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not hdr.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", hdr)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"\b(fg_[a-z0-9_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return fg.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _header_functions()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared but not exported"
+
+
+def test_binding_covers_the_header():
+    names = set(_header_functions())
+    assert names <= set(fg.SIGNATURES), sorted(names - set(fg.SIGNATURES))
+
+
+def test_params_default(lib):
+    p = fg.FgParams()
+    assert lib.fg_params_default(C.byref(p)) == fg.FG_OK
+    assert list(p.dims) == [4, 4, 4, 4]
+    assert p.beta == 6.0 and p.kappa == 0.0 and abs(p.alpha - 0.1932) < 1e-15
+    assert p.link_reals == 18 and p.cg_tol == 1e-10 and p.cg_maxiter == 20000
+    assert lib.fg_params_default(None) == fg.FG_EINVAL
+
+
+@pytest.mark.parametrize("field,value", [("dims", (3, 4, 4, 4)), ("dims", (4, 4, 0, 4)),
+                                         ("link_reals", 10), ("precision", 7), ("cg_maxiter", 0),
+                                         ("cg_tol", 0.0), ("cg_delta", 1.5)])
+def test_create_rejects_bad_parameters_before_touching_the_device(lib, field, value):
+    p = fg.FgParams()
+    lib.fg_params_default(C.byref(p))
+    if field == "dims":
+        for i, d in enumerate(value):
+            p.dims[i] = d
+    else:
+        setattr(p, field, value)
+    h = C.c_void_p()
+    assert lib.fg_lattice_create(C.byref(p), C.byref(h)) == fg.FG_EINVAL
+    assert not h.value
+
+
+def test_null_handle_calls_fail_cleanly(lib):
+    assert lib.fg_refresh_momenta(None) == fg.FG_EINVAL
+    assert lib.fg_sync(None) == fg.FG_EINVAL
+    assert lib.fg_launch_count(None) == -1
+    assert lib.fg_last_error(None) == b"null handle"
+    lib.fg_lattice_destroy(None)
