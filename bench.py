@@ -309,8 +309,7 @@ def run_ours(args):
             lat.set_gauge(hu)
             lat.set_momenta(hp)
             r = lat.trajectory(args.integrator, args.dt, TAU, refresh=False, u_accept=-1.0)
-            out = lat.get_gauge()
-            hu[:] = out.view(np.float64).ravel()
+            lat.get_gauge(out=hu)
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
         te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")

@@ -118,6 +118,15 @@ def _f64(a, shape):
     return a
 
 
+def _out(out, n):
+    if out is None:
+        return np.empty(n, dtype=np.float64)
+    a = out.view(np.float64) if out.dtype == np.complex128 else out
+    if a.dtype != np.float64 or not a.flags.c_contiguous or a.size != n:
+        raise ValueError(f"out must be a contiguous float64 buffer of {n} doubles")
+    return a.reshape(-1)
+
+
 class Lattice:
     """One lattice handle (``fg_lattice*``)."""
 
@@ -175,16 +184,18 @@ class Lattice:
         a = _f64(u, (self.V, 4, 18))
         self._call("fg_set_gauge", _ptr(a))
 
-    def get_gauge(self):
-        a = np.empty(self.V * 4 * 18, dtype=np.float64)
+    def get_gauge(self, out=None):
+        """Links as complex128[Lt,Lz,Ly,Lx,4,3,3]; `out` (contiguous float64 or
+        complex128 of the right size, e.g. pinned memory) is filled in place."""
+        a = _out(out, self.V * 4 * 18)
         self._call("fg_get_gauge", _ptr(a))
-        return a.view(np.complex128).reshape(self.site_shape + (4, 3, 3))
+        return a.reshape(-1).view(np.complex128).reshape(self.site_shape + (4, 3, 3))
 
     def set_momenta(self, p):
         self._call("fg_set_momenta", _ptr(_f64(p, (self.V, 4, 8))))
 
-    def get_momenta(self):
-        a = np.empty(self.V * 32, dtype=np.float64)
+    def get_momenta(self, out=None):
+        a = _out(out, self.V * 32)
         self._call("fg_get_momenta", _ptr(a))
         return a.reshape(self.site_shape + (4, 8))
 

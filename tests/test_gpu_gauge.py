@@ -161,15 +161,23 @@ def test_config1_trajectory_dh_fp64(fgmod, config1_oracle, name):
 
 
 def test_reject_restores_links(fgmod):
+    """Run a trajectory, then run back from its end with reversed momenta: by
+    reversibility dH is minus the first one (large and positive), so a uniform
+    close to 1 rejects and the links must be restored bit for bit."""
     dims = (4, 4, 4, 4)
     u = inputs.hot_start(dims, 1)
     p = inputs.gaussian_momenta(dims, 1)
     with fgmod.Lattice(dims, BETA) as lat:
         lat.set_gauge(u)
         lat.set_momenta(p)
-        r = lat.trajectory("leapfrog", 0.25, 1.0, refresh=False, u_accept=0.999999)
-        assert r["dH"] > 1.0 and r["accepted"] == 0
-        assert np.array_equal(lat.get_gauge(), u)
+        r1 = lat.trajectory("leapfrog", 0.25, 1.0, refresh=False, u_accept=0.0)
+        assert r1["dH"] < -1.0 and r1["accepted"] == 1
+        u1 = lat.get_gauge()
+        lat.set_momenta(-lat.get_momenta())
+        r2 = lat.trajectory("leapfrog", 0.25, 1.0, refresh=False, u_accept=0.999999)
+        assert abs(r2["dH"] + r1["dH"]) < 1e-8 * abs(r1["H0"])
+        assert r2["accepted"] == 0
+        assert np.array_equal(lat.get_gauge(), u1)
 
 
 def test_device_momentum_refresh_statistics(fgmod):
