@@ -1,41 +1,55 @@
 // Backend<R, NC>: device fields of one lattice in precision R with NC complex
-// entries stored per link, and the host-side sequencing of the kernels.
+// entries stored per link, and the host-side sequencing of the kernels:
+// the integrator executor (fused force kernels), the HMC trajectory with its
+// FP64 dH, and for Nf = 2 Wilson fermions the CG driver, the pseudofermion
+// heat bath and the pseudofermion force.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
 #include <string>
-#include <algorithm>
 #include <utility>
 #include <vector>
 
 #include "fg_common.cuh"
+#include "fg_fermion.h"
 #include "fg_kernels.h"
 #include "fg_runtime.h"
 
 namespace fg {
+
+// Host-visible scalars written by kernels (pinned, mapped memory).
+struct Mapped {
+  double bb;
+  double true_rr;
+  double pad[6];
+  double hist[1];   // residual history, one entry per CG iteration (allocated longer)
+};
 
 template <typename R, int NC>
 class Backend final : public IBackend {
  public:
   typedef typename Vec2<R>::T C2;
 
-  explicit Backend(fg_lattice* h) : h_(h), g_(h->g), st_(h->st) {}
+  explicit Backend(fg_lattice* h) : h_(h), g_(h->g), st_(h->st), ferm_(h->prm.kappa > 0.0) {}
 
   ~Backend() override {
     for (void* p : allocs_) cudaFree(p);
     if (host_out_) cudaFreeHost(host_out_);
+    if (mapped_) cudaFreeHost(mapped_);
+    for (int i = 0; i < 2; ++i)
+      if (ev_[i]) cudaEventDestroy(ev_[i]);
   }
 
   fg_status init() {
     const size_t V = (size_t)g_.V;
-    const size_t gauge_bytes = (size_t)4 * NC * V * sizeof(C2);
     const size_t mom_bytes = (size_t)4 * 4 * V * sizeof(C2);
     fg_status s;
-    if ((s = alloc(&U_, gauge_bytes)) != FG_OK) return s;
-    if ((s = alloc(&Ualt_, gauge_bytes)) != FG_OK) return s;
-    if ((s = alloc(&Ubak_, gauge_bytes)) != FG_OK) return s;
+    if ((s = alloc(&U_, gauge_bytes())) != FG_OK) return s;
+    if ((s = alloc(&Ualt_, gauge_bytes())) != FG_OK) return s;
+    if ((s = alloc(&Ubak_, gauge_bytes())) != FG_OK) return s;
     if ((s = alloc(&P_, mom_bytes)) != FG_OK) return s;
     if ((s = alloc(&F_, mom_bytes)) != FG_OK) return s;
     if ((s = alloc((void**)&h0_, V * sizeof(double))) != FG_OK) return s;
@@ -47,7 +61,7 @@ class Backend final : public IBackend {
       return h_->fail(FG_ENOMEM, "pinned host allocation failed");
     }
     if (cudaMemsetAsync(P_, 0, mom_bytes, st_) != cudaSuccess) return cuda_fail("memset");
-    // cold start: unit links
+    if (ferm_ && (s = init_fermions()) != FG_OK) return s;
     s = run(KC_CONVERT, [&] { return launch_unit_links<R, NC>(g_, U_, st_); });
     if (s != FG_OK) return s;
     return sync();
@@ -62,6 +76,7 @@ class Backend final : public IBackend {
       return cuda_fail("gauge upload");
     s = run(KC_CONVERT, [&] { return launch_gauge_to_device<R, NC>(g_, canon_, U_, st_); });
     if (s != FG_OK) return s;
+    sf0_valid_ = false;
     return sync();
   }
   fg_status get_gauge(double* host) override {
@@ -91,15 +106,42 @@ class Backend final : public IBackend {
     return run(KC_MOMENTA, [&] { return launch_refresh_momenta<R>(g_, P_, h_->prm.seed, d, st_); });
   }
 
-  fg_status set_pseudofermion(const double*) override { return no_fermions(); }
-  fg_status refresh_pseudofermion() override { return no_fermions(); }
-  fg_status apply_mhat(const double*, double*, int) override { return no_fermions(); }
-  fg_status cg_solve(const double*, double*, fg_cg_result*) override { return no_fermions(); }
+  // ---------------------------------------------------------------- fermions (ABI)
+  fg_status set_pseudofermion(const double* chi) override {
+    fg_status s = upload_spinor(chi, chi64_);
+    if (s != FG_OK) return s;
+    if ((s = heatbath_from_chi()) != FG_OK) return s;
+    return sync();
+  }
+  fg_status refresh_pseudofermion() override {
+    const uint32_t d = pf_draw_++;
+    fg_status s = run(KC_MOMENTA, [&] { return launch_gaussian_spinor<double>(chi64_, g_.Vh, h_->prm.seed, d, st_); });
+    if (s != FG_OK) return s;
+    return heatbath_from_chi();
+  }
+  fg_status apply_mhat(const double* in, double* out, int dagger) override {
+    fg_status s = upload_spinor(in, b64_);
+    if (s != FG_OK) return s;
+    if ((s = apply_mhat64(ax64_, b64_, U_, dagger)) != FG_OK) return s;
+    return download_spinor(ax64_, out);
+  }
+  fg_status cg_solve(const double* b, double* x, fg_cg_result* r) override {
+    fg_status s = upload_spinor(b, b64_);
+    if (s != FG_OK) return s;
+    CgStats cs;
+    s = cg(U_, b64_, h_->prm.cg_tol, &cs);
+    r->iterations = cs.iters;
+    r->reliable_updates = cs.nru;
+    r->true_residual = cs.true_res;
+    if (s != FG_OK) return s;
+    return download_spinor(x64_, x);
+  }
 
+  // ---------------------------------------------------------------- observables
   fg_status force(double* host_f8) override {
     ForceArgs a = force_args(U_);
     a.F = F_;
-    fg_status s = run(KC_GAUGE_FORCE, [&] { return launch_gauge_force<R, NC>(g_, FM_STORE, a, st_); });
+    fg_status s = force_launch(FM_STORE, a);
     if (s != FG_OK) return s;
     return download_mom(F_, host_f8);
   }
@@ -118,13 +160,18 @@ class Backend final : public IBackend {
     if ((s = fetch(3)) != FG_OK) return s;
     if (sg) *sg = host_out_[0];
     if (t) *t = host_out_[1];
-    if (sf) *sf = 0.0;
+    double f = 0.0;
+    if (ferm_ && sf) {
+      if ((s = fermion_action(U_, &f)) != FG_OK) return s;
+    }
+    if (sf) *sf = f;
     return FG_OK;
   }
 
   fg_status reunitarize_all() override {
     fg_status s = run(KC_DRIFT, [&] { return launch_reunitarize<R, NC>(g_, U_, st_); });
     if (s != FG_OK) return s;
+    sf0_valid_ = false;
     return sync();
   }
 
@@ -133,14 +180,26 @@ class Backend final : public IBackend {
     std::vector<Op> ops = trajectory_ops(integ, h_->prm.alpha, 1, false);
     fg_status s = execute(ops, dt);
     if (s != FG_OK) return s;
+    sf0_valid_ = false;
     return sync();
   }
 
   fg_status trajectory(int integ, double dt, int nsteps, int refresh, double u_accept,
                        fg_traj_result* r) override {
     fg_status s;
+    solves_ = 0;
+    cg_iters_ = 0;
     if (refresh) {
       if ((s = refresh_momenta()) != FG_OK) return s;
+      if (ferm_ && (s = refresh_pseudofermion()) != FG_OK) return s;
+    }
+    double sf0 = 0.0;
+    if (ferm_) {
+      if (!sf0_valid_) {
+        if ((s = fermion_action(U_, &sf0_)) != FG_OK) return s;
+        sf0_valid_ = true;
+      }
+      sf0 = sf0_;
     }
     // H at the start: per-site energies kept for the site-by-site dH sum
     if ((s = energy(0, P_, 0)) != FG_OK) return s;
@@ -150,33 +209,49 @@ class Backend final : public IBackend {
     if ((s = execute(ops, dt)) != FG_OK) return s;
     if ((s = energy(1, P_, 3)) != FG_OK) return s;
     if ((s = fetch(6)) != FG_OK) return s;
-    const double* o = host_out_;
+    double o[6];
+    std::memcpy(o, host_out_, sizeof(o));
+    double sf1 = 0.0;
+    if (ferm_ && (s = fermion_action(U_, &sf1)) != FG_OK) return s;
     r->S_gauge0 = o[0];
     r->T0 = o[1];
     r->S_gauge1 = o[3];
     r->T1 = o[4];
-    r->dH = o[5];
-    r->S_ferm0 = r->S_ferm1 = 0.0;
+    r->S_ferm0 = sf0;
+    r->S_ferm1 = sf1;
+    r->dH = o[5] + (sf1 - sf0);
     r->H0 = r->S_gauge0 + r->T0 + r->S_ferm0;
     r->H1 = r->S_gauge1 + r->T1 + r->S_ferm1;
     r->n_steps = nsteps;
     r->n_force = count_forces(ops);
-    r->n_solves = 0;
-    r->cg_iters = 0;
+    r->n_solves = solves_;
+    r->cg_iters = cg_iters_;
     const double u = (u_accept < 0.0) ? host_uniform() : u_accept;
     r->accepted = std::isfinite(r->dH) && (r->dH <= 0.0 || u < std::exp(-r->dH));
     if (!r->accepted) {
       if (cudaMemcpyAsync(U_, Ubak_, gauge_bytes(), cudaMemcpyDeviceToDevice, st_) != cudaSuccess)
         return cuda_fail("restore copy");
       if ((s = sync()) != FG_OK) return s;
+      sf0_ = sf0;             // phi unchanged and the links are back: S_F is S_F0 again
+      sf0_valid_ = ferm_;
+    } else {
+      sf0_ = sf1;
+      sf0_valid_ = ferm_;
     }
     return FG_OK;
   }
 
  private:
+  struct CgStats {
+    int iters = 0;
+    int nru = 0;
+    double true_res = 0.0;
+  };
+
   fg_lattice* h_;
   GeomH g_;
   cudaStream_t st_;
+  bool ferm_;
   std::vector<void*> allocs_;
   void* U_ = nullptr;
   void* Ualt_ = nullptr;
@@ -190,8 +265,24 @@ class Backend final : public IBackend {
   size_t canon_n_ = 0;
   double* host_out_ = nullptr;
   uint32_t draw_ = 0;
+  uint32_t pf_draw_ = 0;
+  // fermions
+  void *chi64_ = nullptr, *phi64_ = nullptr, *b64_ = nullptr, *x64_ = nullptr, *r64_ = nullptr;
+  void *ax64_ = nullptr, *te64_ = nullptr, *to64_ = nullptr;
+  void *xs_ = nullptr, *rs_ = nullptr, *p_ = nullptr, *ap_ = nullptr, *te_ = nullptr, *to_ = nullptr;
+  void *Xe_ = nullptr, *Xo_ = nullptr, *Ye_ = nullptr, *Yo_ = nullptr, *FF_ = nullptr;
+  CgDev* cgd_ = nullptr;
+  double* part_pap_ = nullptr;
+  double* part_rr_ = nullptr;
+  Mapped* mapped_ = nullptr;
+  cudaEvent_t ev_[2] = {nullptr, nullptr};
+  double sf0_ = 0.0;
+  bool sf0_valid_ = false;
+  int solves_ = 0;
+  long long cg_iters_ = 0;
 
   size_t gauge_bytes() const { return (size_t)4 * NC * g_.V * sizeof(C2); }
+  int nvec() const { return 12 * g_.Vh; }
 
   fg_status alloc(void** p, size_t bytes) {
     *p = nullptr;
@@ -221,7 +312,6 @@ class Backend final : public IBackend {
     if (e != cudaSuccess) return h_->fail(FG_ECUDA, cudaGetErrorString(e));
     return FG_OK;
   }
-  fg_status no_fermions() { return h_->fail(FG_ESTATE, "fermion path not available in this build"); }
 
   template <class Fn>
   fg_status run(int cls, Fn&& fn) {
@@ -264,13 +354,22 @@ class Backend final : public IBackend {
     std::memset(&a, 0, sizeof(a));
     a.U = Uf;
     a.P = P_;
-    a.F = nullptr;
-    a.FF = nullptr;
     a.Ubase = Uf;
-    a.Uout = nullptr;
     a.beta = h_->prm.beta;
     a.reunit = h_->prm.reunitarize;
     return a;
+  }
+
+  // Total force at a.U: the pseudofermion part (CG solve + force kernel) goes
+  // into FF_, which the fused gauge-force kernel adds before it kicks, drifts,
+  // displaces or stores.
+  fg_status force_launch(int mode, ForceArgs a) {
+    if (ferm_) {
+      fg_status s = fermion_force(a.U, h_->prm.cg_tol);
+      if (s != FG_OK) return s;
+      a.FF = FF_;
+    }
+    return run(KC_GAUGE_FORCE, [&] { return launch_gauge_force<R, NC>(g_, mode, a, st_); });
   }
 
   // Runs a merged op list with fused kernels (see the file header of fg_lattice.cu).
@@ -287,13 +386,11 @@ class Backend final : public IBackend {
           a.cdrift = ops[i + 1].c * dt;
           a.Ubase = U_;
           a.Uout = Ualt_;
-          s = run(KC_GAUGE_FORCE, [&] { return launch_gauge_force<R, NC>(g_, FM_KICK_DRIFT, a, st_); });
-          if (s != FG_OK) return s;
+          if ((s = force_launch(FM_KICK_DRIFT, a)) != FG_OK) return s;
           std::swap(U_, Ualt_);
           i += 2;
         } else {
-          s = run(KC_GAUGE_FORCE, [&] { return launch_gauge_force<R, NC>(g_, FM_KICK, a, st_); });
-          if (s != FG_OK) return s;
+          if ((s = force_launch(FM_KICK, a)) != FG_OK) return s;
           i += 1;
         }
       } else if (o.kind == 'Q') {
@@ -302,22 +399,21 @@ class Backend final : public IBackend {
         });
         if (s != FG_OK) return s;
         i += 1;
-      } else {  // 'G'
+      } else {  // 'G': displace along the force, then kick with the force there
         ForceArgs d = force_args(U_);
         d.cdisp = o.d * dt * dt;
         d.Uout = Ualt_;
-        s = run(KC_GAUGE_FORCE, [&] { return launch_gauge_force<R, NC>(g_, FM_DISPLACE, d, st_); });
-        if (s != FG_OK) return s;
+        if ((s = force_launch(FM_DISPLACE, d)) != FG_OK) return s;
         ForceArgs a = force_args(Ualt_);
         a.ckick = o.c * dt;
         if (next_q) {
           a.cdrift = ops[i + 1].c * dt;
           a.Ubase = U_;
           a.Uout = U_;
-          s = run(KC_GAUGE_FORCE, [&] { return launch_gauge_force<R, NC>(g_, FM_KICK_DRIFT, a, st_); });
+          s = force_launch(FM_KICK_DRIFT, a);
           i += 2;
         } else {
-          s = run(KC_GAUGE_FORCE, [&] { return launch_gauge_force<R, NC>(g_, FM_KICK, a, st_); });
+          s = force_launch(FM_KICK, a);
           i += 1;
         }
         if (s != FG_OK) return s;
@@ -332,6 +428,243 @@ class Backend final : public IBackend {
     Philox::rounds(c, (uint32_t)h_->prm.seed, (uint32_t)(h_->prm.seed >> 32));
     const uint64_t bits = ((uint64_t)c[0] << 21) ^ ((uint64_t)c[1] >> 11);
     return (double)(bits & ((1ULL << 53) - 1)) * (1.0 / 9007199254740992.0);
+  }
+
+  // ---------------------------------------------------------------- fermion internals
+  fg_status init_fermions() {
+    const size_t n = (size_t)nvec();
+    const size_t b64 = n * sizeof(double2), bR = n * sizeof(C2);
+    fg_status s;
+    void** d64[] = {&chi64_, &phi64_, &b64_, &x64_, &r64_, &ax64_, &te64_, &to64_};
+    for (void** p : d64)
+      if ((s = alloc(p, b64)) != FG_OK) return s;
+    void** dR[] = {&xs_, &rs_, &p_, &ap_, &te_, &to_, &Xe_, &Xo_, &Ye_, &Yo_};
+    for (void** p : dR)
+      if ((s = alloc(p, bR)) != FG_OK) return s;
+    if ((s = alloc(&FF_, (size_t)4 * 4 * g_.V * sizeof(C2))) != FG_OK) return s;
+    if ((s = alloc((void**)&cgd_, sizeof(CgDev))) != FG_OK) return s;
+    if ((s = alloc((void**)&part_pap_, (dslash_blocks(g_.Vh) + 1) * sizeof(double))) != FG_OK) return s;
+    if ((s = alloc((void**)&part_rr_, (vec_blocks(nvec()) + 1) * sizeof(double))) != FG_OK) return s;
+    const size_t mbytes = sizeof(Mapped) + (size_t)(h_->prm.cg_maxiter + 8) * sizeof(double);
+    if (cudaHostAlloc((void**)&mapped_, mbytes, cudaHostAllocMapped) != cudaSuccess) {
+      mapped_ = nullptr;
+      return h_->fail(FG_ENOMEM, "mapped host allocation failed");
+    }
+    std::memset(mapped_, 0, mbytes);
+    for (int i = 0; i < 2; ++i)
+      if (cudaEventCreateWithFlags(&ev_[i], cudaEventDisableTiming) != cudaSuccess) return cuda_fail("event");
+    if (cudaMemsetAsync(chi64_, 0, b64, st_) != cudaSuccess || cudaMemsetAsync(phi64_, 0, b64, st_) != cudaSuccess)
+      return cuda_fail("memset");
+    return FG_OK;
+  }
+
+  fg_status upload_spinor(const double* host, void* dst64) {
+    const size_t nd = (size_t)nvec() * 2;
+    fg_status s = ensure_canon(nd);
+    if (s != FG_OK) return s;
+    if (cudaMemcpyAsync(canon_, host, nd * sizeof(double), cudaMemcpyHostToDevice, st_) != cudaSuccess)
+      return cuda_fail("spinor upload");
+    return run(KC_CONVERT, [&] { return launch_spinor_to_device<double>(canon_, dst64, g_.Vh, st_); });
+  }
+  fg_status download_spinor(const void* src64, double* host) {
+    const size_t nd = (size_t)nvec() * 2;
+    fg_status s = ensure_canon(nd);
+    if (s != FG_OK) return s;
+    s = run(KC_CONVERT, [&] { return launch_spinor_to_canon<double>(src64, canon_, g_.Vh, st_); });
+    if (s != FG_OK) return s;
+    if (cudaMemcpyAsync(host, canon_, nd * sizeof(double), cudaMemcpyDeviceToHost, st_) != cudaSuccess)
+      return cuda_fail("spinor download");
+    return sync();
+  }
+
+  // FP64 arithmetic on the stored links: out = Mhat in, or Mhat^dagger in.
+  fg_status apply_mhat64(void* out, const void* in, const void* U, int dag) {
+    const double k2 = h_->prm.kappa * h_->prm.kappa;
+    fg_status s = run(KC_DSLASH, [&] {
+      return launch_dslash<R, NC, double>(g_, to64_, in, nullptr, nullptr, U, 1, dag, 0, 1.0, nullptr, nullptr, st_);
+    });
+    if (s != FG_OK) return s;
+    return run(KC_DSLASH, [&] {
+      return launch_dslash<R, NC, double>(g_, out, to64_, in, nullptr, U, 0, dag, 1, -k2, nullptr, nullptr, st_);
+    });
+  }
+  fg_status apply_mdagm64(void* out, const void* in, const void* U) {
+    fg_status s = apply_mhat64(te64_, in, U, 0);
+    if (s != FG_OK) return s;
+    return apply_mhat64(out, te64_, U, 1);
+  }
+
+  // phi = Mhat^dagger chi at the current links; S_F at the heat bath = |chi|^2.
+  fg_status heatbath_from_chi() {
+    fg_status s = apply_mhat64(phi64_, chi64_, U_, 1);
+    if (s != FG_OK) return s;
+    if ((s = run(KC_CG_BLAS, [&] { return launch_dot64(chi64_, chi64_, part_rr_, nvec(), st_); })) != FG_OK) return s;
+    const int nb = vec_blocks(nvec());
+    if ((s = run(KC_REDUCE, [&] { return launch_reduce(part_rr_, nb, 1, dout_ + 8, 0, st_); })) != FG_OK) return s;
+    if (cudaMemcpyAsync(host_out_ + 8, dout_ + 8, sizeof(double), cudaMemcpyDeviceToHost, st_) != cudaSuccess)
+      return cuda_fail("download");
+    if ((s = sync()) != FG_OK) return s;
+    sf0_ = host_out_[8];
+    sf0_valid_ = true;
+    return FG_OK;
+  }
+
+  // S_F = phi^dagger (Mhat^dagger Mhat)^{-1} phi at links U (section 4's action).
+  fg_status fermion_action(const void* U, double* sf) {
+    CgStats cs;
+    fg_status s = cg(U, phi64_, h_->prm.cg_tol_action, &cs);
+    if (s != FG_OK) return s;
+    if ((s = run(KC_CG_BLAS, [&] { return launch_dot64(phi64_, x64_, part_rr_, nvec(), st_); })) != FG_OK) return s;
+    const int nb = vec_blocks(nvec());
+    if ((s = run(KC_REDUCE, [&] { return launch_reduce(part_rr_, nb, 1, dout_ + 9, 0, st_); })) != FG_OK) return s;
+    if (cudaMemcpyAsync(host_out_ + 9, dout_ + 9, sizeof(double), cudaMemcpyDeviceToHost, st_) != cudaSuccess)
+      return cuda_fail("download");
+    if ((s = sync()) != FG_OK) return s;
+    *sf = host_out_[9];
+    return FG_OK;
+  }
+
+  // Pseudofermion force at links U into FF_ (section 4: e_i(S) = -X^dagger e_i(M) X).
+  fg_status fermion_force(const void* U, double tol) {
+    CgStats cs;
+    fg_status s = cg(U, phi64_, tol, &cs);
+    if (s != FG_OK) return s;
+    const int n = nvec();
+    const double k2 = h_->prm.kappa * h_->prm.kappa;
+    if ((s = run(KC_CG_BLAS, [&] { return launch_convert<R, double>(Xe_, x64_, nullptr, n, st_); })) != FG_OK) return s;
+    // X_o = D_oe X_e; Y_e = X_e - kappa^2 D_eo X_o; Y_o = g5 D_oe g5 Y_e
+    if ((s = run(KC_DSLASH, [&] {
+           return launch_dslash<R, NC, R>(g_, Xo_, Xe_, nullptr, nullptr, U, 1, 0, 0, 1.0, nullptr, nullptr, st_);
+         })) != FG_OK) return s;
+    if ((s = run(KC_DSLASH, [&] {
+           return launch_dslash<R, NC, R>(g_, Ye_, Xo_, Xe_, nullptr, U, 0, 0, 1, -k2, nullptr, nullptr, st_);
+         })) != FG_OK) return s;
+    if ((s = run(KC_DSLASH, [&] {
+           return launch_dslash<R, NC, R>(g_, Yo_, Ye_, nullptr, nullptr, U, 1, 1, 0, 1.0, nullptr, nullptr, st_);
+         })) != FG_OK) return s;
+    return run(KC_FERMION_FORCE, [&] {
+      return launch_fermion_force<R, NC, R>(g_, U, Xe_, Xo_, Ye_, Yo_, FF_, k2, 0, st_);
+    });
+  }
+
+  // One CG iteration in the inner precision R (6 launches; all return at once
+  // after convergence through cgd_->done).
+  fg_status cg_iteration(const void* U, int k) {
+    const double k2 = h_->prm.kappa * h_->prm.kappa;
+    const int n = nvec();
+    const int* done = &cgd_->done;
+    fg_status s;
+    if ((s = run(KC_DSLASH, [&] {
+           return launch_dslash<R, NC, R>(g_, to_, p_, nullptr, nullptr, U, 1, 0, 0, 1.0, nullptr, done, st_);
+         })) != FG_OK) return s;
+    if ((s = run(KC_DSLASH, [&] {
+           return launch_dslash<R, NC, R>(g_, te_, to_, p_, nullptr, U, 0, 0, 1, -k2, nullptr, done, st_);
+         })) != FG_OK) return s;
+    if ((s = run(KC_DSLASH, [&] {
+           return launch_dslash<R, NC, R>(g_, to_, te_, nullptr, nullptr, U, 1, 1, 0, 1.0, nullptr, done, st_);
+         })) != FG_OK) return s;
+    if ((s = run(KC_DSLASH, [&] {
+           return launch_dslash<R, NC, R>(g_, ap_, to_, te_, p_, U, 0, 1, 2, -k2, part_pap_, done, st_);
+         })) != FG_OK) return s;
+    const int npap = dslash_blocks(g_.Vh);
+    if ((s = run(KC_CG_BLAS, [&] {
+           return launch_cg_axpy<R>(xs_, rs_, p_, ap_, part_pap_, npap, cgd_, k, part_rr_, n, st_);
+         })) != FG_OK) return s;
+    double* hist = mapped_->hist;
+    return run(KC_CG_BLAS, [&] {
+      return launch_cg_xpay<R>(p_, rs_, part_rr_, vec_blocks(n), cgd_, k, hist, n, st_);
+    });
+  }
+
+  // Reliable update after iteration k: x64 += x_s, r64 = b - M x64 in FP64,
+  // r_s = r64, rr = |r64|^2 (also published to the host).
+  fg_status reliable_update(const void* U, const void* b64, int k) {
+    const int n = nvec();
+    fg_status s;
+    if ((s = run(KC_CG_BLAS, [&] { return launch_ru_accumulate<R>(x64_, xs_, n, st_); })) != FG_OK) return s;
+    if ((s = apply_mdagm64(ax64_, x64_, U)) != FG_OK) return s;
+    if ((s = run(KC_CG_BLAS, [&] { return launch_ru_residual<R>(b64, ax64_, r64_, rs_, part_rr_, n, st_); })) != FG_OK)
+      return s;
+    double* tr = &mapped_->true_rr;
+    return run(KC_REDUCE, [&] { return launch_ru_publish(part_rr_, vec_blocks(n), cgd_, k, tr, st_); });
+  }
+
+  // Conjugate gradient on Mhat^dagger Mhat x = b (b FP64 on the device), x0 = 0,
+  // to |b - M x| <= tol |b| in FP64; solution in x64_.
+  //
+  // The iterations run in precision R with device-side scalars; the host
+  // never waits for the iteration it has just queued: after queueing
+  // iteration k it waits for iteration k-1 and reads its residual from mapped
+  // memory.  For R = float, a reliable update (FP64 true residual, Sleijpen
+  // and van der Vorst) is queued whenever the iterated residual has fallen by
+  // cg_delta since the last one; convergence is always confirmed by an FP64
+  // true residual.
+  fg_status cg(const void* U, const void* b64, double tol, CgStats* st) {
+    const int n = nvec();
+    const int nbv = vec_blocks(n);
+    const bool mixed = sizeof(R) < sizeof(double);
+    const double delta2 = h_->prm.cg_delta * h_->prm.cg_delta;
+    fg_status s;
+    ++solves_;
+    if (cudaMemsetAsync(x64_, 0, (size_t)n * sizeof(double2), st_) != cudaSuccess ||
+        cudaMemsetAsync(xs_, 0, (size_t)n * sizeof(C2), st_) != cudaSuccess ||
+        cudaMemcpyAsync(r64_, b64, (size_t)n * sizeof(double2), cudaMemcpyDeviceToDevice, st_) != cudaSuccess)
+      return cuda_fail("cg setup");
+    if ((s = run(KC_CG_BLAS, [&] { return launch_convert<R, double>(rs_, b64, part_rr_, n, st_); })) != FG_OK) return s;
+    double* bbp = &mapped_->bb;
+    if ((s = run(KC_REDUCE, [&] { return launch_cg_init(part_rr_, nbv, cgd_, tol * tol, bbp, st_); })) != FG_OK) return s;
+    if (cudaMemcpyAsync(p_, rs_, (size_t)n * sizeof(C2), cudaMemcpyDeviceToDevice, st_) != cudaSuccess)
+      return cuda_fail("cg setup");
+    if ((s = sync()) != FG_OK) return s;
+    const double bb = mapped_->bb;
+    st->iters = 0;
+    st->nru = 0;
+    st->true_res = 0.0;
+    if (bb == 0.0) return FG_OK;
+    const double tol2bb = tol * tol * bb;
+    double maxrr = bb;
+    int k = 0;
+    int iters = 0;
+    const int maxiter = h_->prm.cg_maxiter;
+    for (;;) {
+      bool converged = false;
+      while (!converged) {
+        if (k >= maxiter) {
+          cg_iters_ += k;
+          st->iters = k;
+          return h_->fail(FG_ENOCONV, "CG did not converge in " + std::to_string(maxiter) + " iterations");
+        }
+        ++k;
+        if ((s = cg_iteration(U, k)) != FG_OK) return s;
+        if (cudaEventRecord(ev_[k & 1], st_) != cudaSuccess) return cuda_fail("event");
+        if (k >= 2) {
+          if (cudaEventSynchronize(ev_[(k - 1) & 1]) != cudaSuccess) return cuda_fail("event sync");
+          const double rr = mapped_->hist[k - 1];
+          if (!(rr == rr)) return h_->fail(FG_ENOCONV, "CG residual is NaN");
+          if (rr <= tol2bb) {
+            converged = true;
+            iters = k - 1;
+          } else if (mixed && rr < delta2 * maxrr) {
+            if ((s = reliable_update(U, b64, k)) != FG_OK) return s;
+            ++st->nru;
+            maxrr = rr;
+          }
+        }
+      }
+      if ((s = reliable_update(U, b64, k)) != FG_OK) return s;
+      ++st->nru;
+      if ((s = sync()) != FG_OK) return s;
+      const double trr = mapped_->true_rr;
+      st->true_res = std::sqrt(trr / bb);
+      if (trr <= tol2bb) break;
+      // The FP64 residual is not yet below tol: restart the directions from it.
+      if (cudaMemcpyAsync(p_, rs_, (size_t)n * sizeof(C2), cudaMemcpyDeviceToDevice, st_) != cudaSuccess)
+        return cuda_fail("cg restart");
+      maxrr = trr;
+    }
+    st->iters = iters;
+    cg_iters_ += iters;
+    return FG_OK;
   }
 };
 

@@ -1,0 +1,620 @@
+// Wilson fermion kernels (sm_103a): even-odd hopping term, CG vector
+// updates, the pseudofermion force and the Gaussian heat bath.
+//
+// Section 4 of the paper writes the pseudofermion force as
+// e_i(S) = -X^dagger e_i(M) X with X = M^{-1} phi; with M = Mhat^dagger Mhat
+// and Mhat = 1 - kappa^2 D_eo D_oe this becomes, per link U_mu(x),
+//   F^a = -kappa^2 Im Tr(lambda^a W),  W = U M1 - M2 U^dagger,
+//   M1 = sum_s Xt(x+mu)_s ((1 - g_mu) Yt(x))_s^dagger,
+//   M2 = sum_s Xt(x)_s ((1 + g_mu) Yt(x+mu))_s^dagger,
+// with Xt = (X_e, D_oe X_e) and Yt = (Y_e, g5 D_oe g5 Y_e), Y_e = Mhat X_e.
+// The rank-2 spin projectors reduce each of M1, M2 to two colour outer
+// products of half spinors.
+//
+// Gamma matrices (DeGrand-Rossi): g_mu = [[0, A_mu], [A_mu^dagger, 0]] in 2x2
+// spin blocks with A_x = [[0, i], [i, 0]], A_y = [[0, -1], [1, 0]],
+// A_z = diag(i, -i), A_t = 1, so g5 = diag(1, 1, -1, -1) and
+// (1 - s g_mu) psi = (h, -s A_mu^dagger h) with h = psi_up - s A_mu psi_down.
+#include "fg_common.cuh"
+#include "fg_fermion.h"
+#include "fg_kernels.h"
+
+namespace fg {
+
+static inline Geom to_devg(const GeomH& h) {
+  Geom g;
+  for (int i = 0; i < 4; ++i) g.L[i] = h.L[i];
+  g.Lxh = h.Lxh; g.Vh = h.Vh; g.V = h.V;
+  return g;
+}
+
+template <typename R> struct Spinor {
+  Cx<R> s[4][3];
+};
+
+template <typename R>
+__device__ __forceinline__ Spinor<R> load_spinor(const typename Vec2<R>::T* __restrict__ f, int i, int Vh) {
+  Spinor<R> x;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    const typename Vec2<R>::T v = __ldg(f + (size_t)k * Vh + i);
+    x.s[k / 3][k % 3] = cx<R>(v.x, v.y);
+  }
+  return x;
+}
+template <typename R>
+__device__ __forceinline__ void store_spinor(typename Vec2<R>::T* __restrict__ f, int i, int Vh, const Spinor<R>& x) {
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    typename Vec2<R>::T v;
+    v.x = x.s[k / 3][k % 3].re;
+    v.y = x.s[k / 3][k % 3].im;
+    f[(size_t)k * Vh + i] = v;
+  }
+}
+
+template <typename RO, typename RI>
+__device__ __forceinline__ M3<RO> convert(const M3<RI>& m) {
+  M3<RO> o;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) o.e[i][j] = cx<RO>(RO(m.e[i][j].re), RO(m.e[i][j].im));
+  return o;
+}
+
+// h_k = psi_k - S (A_mu psi_down)_k, k = 0, 1
+template <int MU, int S, typename R>
+__device__ __forceinline__ void project(const Spinor<R>& p, Cx<R> h[2][3]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    Cx<R> a0, a1;  // (A_mu psi_down)_0, _1
+    if (MU == 0) { a0 = times_i(p.s[3][c]); a1 = times_i(p.s[2][c]); }
+    if (MU == 1) { a0 = cx<R>(-p.s[3][c].re, -p.s[3][c].im); a1 = p.s[2][c]; }
+    if (MU == 2) { a0 = times_i(p.s[2][c]); a1 = cx<R>(p.s[3][c].im, -p.s[3][c].re); }
+    if (MU == 3) { a0 = p.s[2][c]; a1 = p.s[3][c]; }
+    if (S > 0) { h[0][c] = p.s[0][c] - a0; h[1][c] = p.s[1][c] - a1; }
+    else { h[0][c] = p.s[0][c] + a0; h[1][c] = p.s[1][c] + a1; }
+  }
+}
+
+// acc_up += sign * w, acc_down += sign * (-S) A_mu^dagger w
+template <int MU, int S, typename R>
+__device__ __forceinline__ void reconstruct_add(Spinor<R>& acc, const Cx<R> w[2][3], R sign) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    Cx<R> b0, b1;  // (A_mu^dagger w)_0, _1
+    if (MU == 0) { b0 = cx<R>(w[1][c].im, -w[1][c].re); b1 = cx<R>(w[0][c].im, -w[0][c].re); }
+    if (MU == 1) { b0 = w[1][c]; b1 = cx<R>(-w[0][c].re, -w[0][c].im); }
+    if (MU == 2) { b0 = cx<R>(w[0][c].im, -w[0][c].re); b1 = times_i(w[1][c]); }
+    if (MU == 3) { b0 = w[0][c]; b1 = w[1][c]; }
+    const R sd = (S > 0) ? -sign : sign;
+    acc.s[0][c] = acc.s[0][c] + sign * w[0][c];
+    acc.s[1][c] = acc.s[1][c] + sign * w[1][c];
+    acc.s[2][c] = acc.s[2][c] + sd * b0;
+    acc.s[3][c] = acc.s[3][c] + sd * b1;
+  }
+}
+
+// w = U h (ADJ = 0) or U^dagger h (ADJ = 1), for both half-spinor rows
+template <int ADJ, typename R>
+__device__ __forceinline__ void mat_half(const M3<R>& u, const Cx<R> h[2][3], Cx<R> w[2][3]) {
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      Cx<R> s = cx<R>(0, 0);
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        if (ADJ) cmac_cj(s, u.e[b][a], h[k][b]);
+        else cmac(s, u.e[a][b], h[k][b]);
+      }
+      w[k][a] = s;
+    }
+}
+
+template <int MU, int DAG, typename RL, int NC, typename RS>
+__device__ __forceinline__ void hop_dir(Spinor<RS>& acc, const typename Vec2<RS>::T* __restrict__ in,
+                                        const Gauge<RL, NC>& U, const Geom& g, const int c[4], int s,
+                                        int in_off) {
+  constexpr int SF = DAG ? -1 : 1;   // forward hop: (1 - g_mu), (1 + g_mu) for the dagger
+  constexpr int SB = -SF;
+  {
+    const int sn = cb_neighbor(g, c, MU, +1);
+    const Spinor<RS> p = load_spinor<RS>(in, sn - in_off, g.Vh);
+    Cx<RS> h[2][3], w[2][3];
+    project<MU, SF>(p, h);
+    const M3<RS> u = convert<RS>(U.load(MU, s));
+    mat_half<0>(u, h, w);
+    const RS sign = (MU == 3 && c[3] == g.L[3] - 1) ? RS(-1) : RS(1);
+    reconstruct_add<MU, SF>(acc, w, sign);
+  }
+  {
+    const int sn = cb_neighbor(g, c, MU, -1);
+    const Spinor<RS> p = load_spinor<RS>(in, sn - in_off, g.Vh);
+    Cx<RS> h[2][3], w[2][3];
+    project<MU, SB>(p, h);
+    const M3<RS> u = convert<RS>(U.load(MU, sn));
+    mat_half<1>(u, h, w);
+    const RS sign = (MU == 3 && c[3] == 0) ? RS(-1) : RS(1);
+    reconstruct_add<MU, SB>(acc, w, sign);
+  }
+}
+
+constexpr int kDslashThreads = 128;
+
+// out = b D in (MODE 0), out = x + b D in (MODE 1), and MODE 2 also writes the
+// block partial sum of Re <pdot, out>.  `in` has parity 1 - out_par.
+template <typename RL, int NC, typename RS, int DAG, int MODE>
+__global__ void __launch_bounds__(kDslashThreads) dslash_kernel(
+    typename Vec2<RS>::T* __restrict__ out, const typename Vec2<RS>::T* __restrict__ in,
+    const typename Vec2<RS>::T* __restrict__ x, const typename Vec2<RS>::T* __restrict__ pdot,
+    Gauge<RL, NC> U, Geom g, int out_par, RS b, double* __restrict__ partial, const int* __restrict__ done) {
+  if (done != nullptr && *done) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double dot = 0.0;
+  if (i < g.Vh) {
+    const int s = out_par * g.Vh + i;
+    int c[4], par;
+    cb_coords(g, s, c, par);
+    const int in_off = (1 - out_par) * g.Vh;
+    Spinor<RS> acc;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) acc.s[k][cc] = cx<RS>(0, 0);
+    hop_dir<0, DAG>(acc, in, U, g, c, s, in_off);
+    hop_dir<1, DAG>(acc, in, U, g, c, s, in_off);
+    hop_dir<2, DAG>(acc, in, U, g, c, s, in_off);
+    hop_dir<3, DAG>(acc, in, U, g, c, s, in_off);
+    Spinor<RS> o;
+    if (MODE == 0) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) o.s[k][cc] = b * acc.s[k][cc];
+    } else {
+      const Spinor<RS> xv = load_spinor<RS>(x, i, g.Vh);
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) o.s[k][cc] = xv.s[k][cc] + b * acc.s[k][cc];
+      if (MODE == 2) {
+        const Spinor<RS> pv = load_spinor<RS>(pdot, i, g.Vh);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+          for (int cc = 0; cc < 3; ++cc)
+            dot += double(pv.s[k][cc].re) * o.s[k][cc].re + double(pv.s[k][cc].im) * o.s[k][cc].im;
+      }
+    }
+    store_spinor<RS>(out, i, g.Vh, o);
+  }
+  if (MODE == 2) {
+    double v[1] = {dot};
+    block_reduce_store<1>(v, partial, gridDim.x);
+  }
+}
+
+// --------------------------------------------------------------------------- force
+template <typename RL, int NC, typename RS>
+__global__ void __launch_bounds__(256) fermion_force_kernel(
+    Gauge<RL, NC> U, const typename Vec2<RS>::T* __restrict__ Xe, const typename Vec2<RS>::T* __restrict__ Xo,
+    const typename Vec2<RS>::T* __restrict__ Ye, const typename Vec2<RS>::T* __restrict__ Yo,
+    Mom<RL> FF, Geom g, RL kappa2, int accumulate) {
+  const int s = blockIdx.x * 64 + threadIdx.x;
+  const int mu = threadIdx.y;
+  if (s >= g.V) return;
+  int c[4], par;
+  cb_coords(g, s, c, par);
+  const int sn = cb_neighbor(g, c, mu, +1);
+  const int i = s - par * g.Vh, in = sn - (1 - par) * g.Vh;
+  const Spinor<RS> x0 = load_spinor<RS>(par ? Xo : Xe, i, g.Vh);
+  const Spinor<RS> y0 = load_spinor<RS>(par ? Yo : Ye, i, g.Vh);
+  const Spinor<RS> x1 = load_spinor<RS>(par ? Xe : Xo, in, g.Vh);
+  const Spinor<RS> y1 = load_spinor<RS>(par ? Ye : Yo, in, g.Vh);
+  Cx<RS> hx[2][3], hy[2][3], gx[2][3], gy[2][3];
+  switch (mu) {
+    case 0: project<0, 1>(x1, hx); project<0, 1>(y0, hy); project<0, -1>(x0, gx); project<0, -1>(y1, gy); break;
+    case 1: project<1, 1>(x1, hx); project<1, 1>(y0, hy); project<1, -1>(x0, gx); project<1, -1>(y1, gy); break;
+    case 2: project<2, 1>(x1, hx); project<2, 1>(y0, hy); project<2, -1>(x0, gx); project<2, -1>(y1, gy); break;
+    default: project<3, 1>(x1, hx); project<3, 1>(y0, hy); project<3, -1>(x0, gx); project<3, -1>(y1, gy); break;
+  }
+  M3<RS> m1, m2;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      Cx<RS> s1 = cx<RS>(0, 0), s2 = cx<RS>(0, 0);
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        cmac_jc(s1, hx[k][a], hy[k][b]);
+        cmac_jc(s2, gx[k][a], gy[k][b]);
+      }
+      m1.e[a][b] = s1;
+      m2.e[a][b] = s2;
+    }
+  const M3<RS> u = convert<RS>(U.load(mu, s));
+  M3<RS> w = mul(u, m1);
+  const M3<RS> t = mul_nd(m2, u);
+  const RS sign = (mu == 3 && c[3] == g.L[3] - 1) ? RS(-1) : RS(1);
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) w.e[a][b] = sign * (w.e[a][b] - t.e[a][b]);
+  RS f[8];
+  im_tr_gellmann(w, f);
+  RL out[8];
+  if (accumulate) FF.load(mu, s, out);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) out[k] = (accumulate ? out[k] : RL(0)) - kappa2 * RL(f[k]);
+  FF.store(mu, s, out);
+}
+
+// --------------------------------------------------------------------------- CG vectors
+constexpr int kVecThreads = 256;
+
+// Sum of `n` partials in a fixed order, computed by every block (so each block
+// derives the same scalar without another launch).
+__device__ __forceinline__ double block_sum_partials(const double* __restrict__ part, int n) {
+  __shared__ double sh[32];
+  double x = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) x += part[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) sh[warp] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    sh[0] = t;
+  }
+  __syncthreads();
+  const double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+// alpha = rr[(k-1)&1] / sum(pAp partials); x += alpha p; r -= alpha Ap; partial |r|^2.
+template <typename R>
+__global__ void __launch_bounds__(kVecThreads) cg_axpy_kernel(
+    typename Vec2<R>::T* __restrict__ x, typename Vec2<R>::T* __restrict__ r,
+    const typename Vec2<R>::T* __restrict__ p, const typename Vec2<R>::T* __restrict__ ap,
+    const double* __restrict__ pap_part, int npap, CgDev* __restrict__ cgd, int k,
+    double* __restrict__ rr_part, int n) {
+  if (cgd->done) return;
+  const double pap = block_sum_partials(pap_part, npap);
+  const double rr = cgd->rr[(k - 1) & 1];
+  const double alpha = pap > 0.0 ? rr / pap : 0.0;
+  const R a = R(alpha);
+  double acc = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    typename Vec2<R>::T xv = x[i], rv = r[i];
+    const typename Vec2<R>::T pv = p[i], av = ap[i];
+    xv.x = fma(a, pv.x, xv.x); xv.y = fma(a, pv.y, xv.y);
+    rv.x = fma(-a, av.x, rv.x); rv.y = fma(-a, av.y, rv.y);
+    x[i] = xv;
+    r[i] = rv;
+    acc += double(rv.x) * rv.x + double(rv.y) * rv.y;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) cgd->alpha = alpha;
+  double v[1] = {acc};
+  block_reduce_store<1>(v, rr_part, gridDim.x);
+}
+
+// rr_new = sum(rr partials); done if rr_new <= tol2 bb; beta = rr_new / rr_old;
+// p = r + beta p.  Block 0 publishes rr[k&1], the history entry and `done`.
+template <typename R>
+__global__ void __launch_bounds__(kVecThreads) cg_xpay_kernel(
+    typename Vec2<R>::T* __restrict__ p, const typename Vec2<R>::T* __restrict__ r,
+    const double* __restrict__ rr_part, int nrr, CgDev* __restrict__ cgd, int k,
+    double* __restrict__ hist, int n) {
+  if (cgd->done) return;
+  const double rr_new = block_sum_partials(rr_part, nrr);
+  const double rr_old = cgd->rr[(k - 1) & 1];
+  const bool conv = rr_new <= cgd->tol2bb;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    cgd->rr[k & 1] = rr_new;
+    hist[k] = rr_new;
+    cgd->iter = k;
+    if (conv) cgd->done = 1;
+  }
+  if (conv) return;
+  const R beta = R(rr_old > 0.0 ? rr_new / rr_old : 0.0);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    typename Vec2<R>::T pv = p[i];
+    const typename Vec2<R>::T rv = r[i];
+    pv.x = fma(beta, pv.x, rv.x);
+    pv.y = fma(beta, pv.y, rv.y);
+    p[i] = pv;
+  }
+}
+
+// Reliable update, first half: x64 += x_s; x_s = 0.
+template <typename RI>
+__global__ void __launch_bounds__(kVecThreads) ru_accumulate_kernel(double2* __restrict__ x,
+                                                                    typename Vec2<RI>::T* __restrict__ xs, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const typename Vec2<RI>::T v = xs[i];
+    double2 a = x[i];
+    a.x += double(v.x);
+    a.y += double(v.y);
+    x[i] = a;
+    typename Vec2<RI>::T z;
+    z.x = RI(0); z.y = RI(0);
+    xs[i] = z;
+  }
+}
+
+// Reliable update, second half: r64 = b - Ax; r_s = (RI) r64; partial |r64|^2.
+template <typename RI>
+__global__ void __launch_bounds__(kVecThreads) ru_residual_kernel(const double2* __restrict__ b,
+                                                                  const double2* __restrict__ ax,
+                                                                  double2* __restrict__ r,
+                                                                  typename Vec2<RI>::T* __restrict__ rs,
+                                                                  double* __restrict__ part, int n) {
+  double acc = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double2 bv = b[i], av = ax[i];
+    double2 rv;
+    rv.x = bv.x - av.x;
+    rv.y = bv.y - av.y;
+    r[i] = rv;
+    typename Vec2<RI>::T s;
+    s.x = RI(rv.x);
+    s.y = RI(rv.y);
+    rs[i] = s;
+    acc += rv.x * rv.x + rv.y * rv.y;
+  }
+  double v[1] = {acc};
+  block_reduce_store<1>(v, part, gridDim.x);
+}
+
+// Publishes a reliable-update residual: rr[k&1] = |r|^2, done = rr <= tol2 bb.
+__global__ void ru_publish_kernel(const double* __restrict__ part, int n, CgDev* __restrict__ cgd, int k,
+                                  double* __restrict__ true_rr) {
+  const double rr = block_sum_partials(part, n);
+  if (threadIdx.x == 0) {
+    cgd->rr[k & 1] = rr;
+    cgd->done = rr <= cgd->tol2bb ? 1 : 0;
+    *true_rr = rr;
+  }
+}
+
+// Start of a solve: bb = |b|^2 from partials, rr = bb, done = (bb == 0).
+__global__ void cg_init_kernel(const double* __restrict__ part, int n, CgDev* __restrict__ cgd, double tol2,
+                               double* __restrict__ bb_out) {
+  const double bb = block_sum_partials(part, n);
+  if (threadIdx.x == 0) {
+    cgd->bb = bb;
+    cgd->tol2bb = tol2 * bb;
+    cgd->rr[0] = cgd->rr[1] = bb;
+    cgd->done = bb == 0.0 ? 1 : 0;
+    cgd->iter = 0;
+    *bb_out = bb;
+  }
+}
+
+// dst = (RO) src; optional partial |src|^2.
+template <typename RO, typename RI>
+__global__ void __launch_bounds__(kVecThreads) convert_kernel(typename Vec2<RO>::T* __restrict__ dst,
+                                                              const typename Vec2<RI>::T* __restrict__ src,
+                                                              double* __restrict__ part, int n) {
+  double acc = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const typename Vec2<RI>::T v = src[i];
+    typename Vec2<RO>::T o;
+    o.x = RO(v.x);
+    o.y = RO(v.y);
+    dst[i] = o;
+    acc += double(v.x) * v.x + double(v.y) * v.y;
+  }
+  if (part != nullptr) {
+    double v[1] = {acc};
+    block_reduce_store<1>(v, part, gridDim.x);
+  }
+}
+
+__global__ void __launch_bounds__(kVecThreads) dot64_kernel(const double2* __restrict__ a,
+                                                             const double2* __restrict__ b,
+                                                             double* __restrict__ part, int n) {
+  double acc = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double2 x = a[i], y = b[i];
+    acc += x.x * y.x + x.y * y.y;
+  }
+  double v[1] = {acc};
+  block_reduce_store<1>(v, part, gridDim.x);
+}
+
+// Complex Gaussian spinor with density exp(-|chi|^2): re, im ~ N(0, 1/2).
+template <typename R>
+__global__ void __launch_bounds__(256) gaussian_spinor_kernel(typename Vec2<R>::T* __restrict__ chi, int Vh,
+                                                              uint32_t k0, uint32_t k1, uint32_t draw) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Vh) return;
+  const double inv_sqrt2 = 0.70710678118654752440;
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    uint32_t ctr[4] = {(uint32_t)i, draw, 1u /* stream: pseudofermion */, (uint32_t)q};
+    Philox::rounds(ctr, k0, k1);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const double u1 = ((double)ctr[2 * h] + 1.0) * 2.3283064365386963e-10;
+      const double u2 = (double)ctr[2 * h + 1] * 2.3283064365386963e-10;
+      const double rad = sqrt(-2.0 * log(u1)) * inv_sqrt2;
+      double sn, cs;
+      sincospi(2.0 * u2, &sn, &cs);
+      typename Vec2<R>::T v;
+      v.x = R(rad * cs);
+      v.y = R(rad * sn);
+      chi[(size_t)(2 * q + h) * Vh + i] = v;
+    }
+  }
+}
+
+template <typename R>
+__global__ void spinor_to_device_kernel(const double* __restrict__ canon, typename Vec2<R>::T* __restrict__ f, int Vh) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 12 * Vh) return;
+  const int i = t / 12, k = t % 12;
+  typename Vec2<R>::T v;
+  v.x = R(canon[(size_t)t * 2]);
+  v.y = R(canon[(size_t)t * 2 + 1]);
+  f[(size_t)k * Vh + i] = v;
+}
+
+template <typename R>
+__global__ void spinor_to_canon_kernel(const typename Vec2<R>::T* __restrict__ f, double* __restrict__ canon, int Vh) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 12 * Vh) return;
+  const int i = t / 12, k = t % 12;
+  const typename Vec2<R>::T v = f[(size_t)k * Vh + i];
+  canon[(size_t)t * 2] = v.x;
+  canon[(size_t)t * 2 + 1] = v.y;
+}
+
+// ============================================================================ launchers
+template <typename R> static typename Vec2<R>::T* v2(void* p) { return (typename Vec2<R>::T*)p; }
+template <typename R> static const typename Vec2<R>::T* cv2(const void* p) { return (const typename Vec2<R>::T*)p; }
+
+int vec_blocks(int n) {
+  int b = (n + kVecThreads - 1) / kVecThreads;
+  return b > 152 * 8 ? 152 * 8 : b;
+}
+int dslash_blocks(int Vh) { return (Vh + kDslashThreads - 1) / kDslashThreads; }
+
+template <typename RL, int NC, typename RS>
+cudaError_t launch_dslash(const GeomH& gh, void* out, const void* in, const void* x, const void* pdot,
+                          const void* U, int out_par, int dag, int mode, double b, double* partial,
+                          const int* done, cudaStream_t st) {
+  Gauge<RL, NC> u;
+  u.p = (typename Vec2<RL>::T*)U;
+  u.V = gh.V;
+  const Geom g = to_devg(gh);
+  const int nb = dslash_blocks(gh.Vh);
+#define FG_DS(D, M)                                                                                     \
+  dslash_kernel<RL, NC, RS, D, M><<<nb, kDslashThreads, 0, st>>>(v2<RS>(out), cv2<RS>(in), cv2<RS>(x),   \
+                                                                 cv2<RS>(pdot), u, g, out_par, RS(b),   \
+                                                                 partial, done)
+  if (dag) {
+    if (mode == 0) FG_DS(1, 0); else if (mode == 1) FG_DS(1, 1); else FG_DS(1, 2);
+  } else {
+    if (mode == 0) FG_DS(0, 0); else if (mode == 1) FG_DS(0, 1); else FG_DS(0, 2);
+  }
+#undef FG_DS
+  return cudaGetLastError();
+}
+
+template <typename RL, int NC, typename RS>
+cudaError_t launch_fermion_force(const GeomH& gh, const void* U, const void* Xe, const void* Xo, const void* Ye,
+                                 const void* Yo, void* FF, double kappa2, int accumulate, cudaStream_t st) {
+  Gauge<RL, NC> u;
+  u.p = (typename Vec2<RL>::T*)U;
+  u.V = gh.V;
+  Mom<RL> f;
+  f.p = (typename Vec2<RL>::T*)FF;
+  f.V = gh.V;
+  fermion_force_kernel<RL, NC, RS><<<(gh.V + 63) / 64, dim3(64, 4), 0, st>>>(
+      u, cv2<RS>(Xe), cv2<RS>(Xo), cv2<RS>(Ye), cv2<RS>(Yo), f, to_devg(gh), RL(kappa2), accumulate);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_cg_axpy(void* x, void* r, const void* p, const void* ap, const double* pap_part, int npap,
+                           CgDev* cgd, int k, double* rr_part, int n, cudaStream_t st) {
+  cg_axpy_kernel<R><<<vec_blocks(n), kVecThreads, 0, st>>>(v2<R>(x), v2<R>(r), cv2<R>(p), cv2<R>(ap), pap_part,
+                                                           npap, cgd, k, rr_part, n);
+  return cudaGetLastError();
+}
+template <typename R>
+cudaError_t launch_cg_xpay(void* p, const void* r, const double* rr_part, int nrr, CgDev* cgd, int k,
+                           double* hist, int n, cudaStream_t st) {
+  cg_xpay_kernel<R><<<vec_blocks(n), kVecThreads, 0, st>>>(v2<R>(p), cv2<R>(r), rr_part, nrr, cgd, k, hist, n);
+  return cudaGetLastError();
+}
+template <typename RI>
+cudaError_t launch_ru_accumulate(void* x64, void* xs, int n, cudaStream_t st) {
+  ru_accumulate_kernel<RI><<<vec_blocks(n), kVecThreads, 0, st>>>((double2*)x64, v2<RI>(xs), n);
+  return cudaGetLastError();
+}
+template <typename RI>
+cudaError_t launch_ru_residual(const void* b64, const void* ax64, void* r64, void* rs, double* part, int n,
+                               cudaStream_t st) {
+  ru_residual_kernel<RI><<<vec_blocks(n), kVecThreads, 0, st>>>((const double2*)b64, (const double2*)ax64,
+                                                                (double2*)r64, v2<RI>(rs), part, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_ru_publish(const double* part, int n, CgDev* cgd, int k, double* true_rr, cudaStream_t st) {
+  ru_publish_kernel<<<1, 1024, 0, st>>>(part, n, cgd, k, true_rr);
+  return cudaGetLastError();
+}
+cudaError_t launch_cg_init(const double* part, int n, CgDev* cgd, double tol2, double* bb_out, cudaStream_t st) {
+  cg_init_kernel<<<1, 1024, 0, st>>>(part, n, cgd, tol2, bb_out);
+  return cudaGetLastError();
+}
+template <typename RO, typename RI>
+cudaError_t launch_convert(void* dst, const void* src, double* part, int n, cudaStream_t st) {
+  convert_kernel<RO, RI><<<vec_blocks(n), kVecThreads, 0, st>>>(v2<RO>(dst), cv2<RI>(src), part, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_dot64(const void* a, const void* b, double* part, int n, cudaStream_t st) {
+  dot64_kernel<<<vec_blocks(n), kVecThreads, 0, st>>>((const double2*)a, (const double2*)b, part, n);
+  return cudaGetLastError();
+}
+template <typename R>
+cudaError_t launch_gaussian_spinor(void* chi, int Vh, uint64_t seed, uint32_t draw, cudaStream_t st) {
+  gaussian_spinor_kernel<R><<<(Vh + 255) / 256, 256, 0, st>>>(v2<R>(chi), Vh, (uint32_t)seed,
+                                                             (uint32_t)(seed >> 32), draw);
+  return cudaGetLastError();
+}
+template <typename R>
+cudaError_t launch_spinor_to_device(const double* canon, void* f, int Vh, cudaStream_t st) {
+  spinor_to_device_kernel<R><<<(12 * Vh + 255) / 256, 256, 0, st>>>(canon, v2<R>(f), Vh);
+  return cudaGetLastError();
+}
+template <typename R>
+cudaError_t launch_spinor_to_canon(const void* f, double* canon, int Vh, cudaStream_t st) {
+  spinor_to_canon_kernel<R><<<(12 * Vh + 255) / 256, 256, 0, st>>>(cv2<R>(f), canon, Vh);
+  return cudaGetLastError();
+}
+
+#define FG_INST_F(RL, NC, RS)                                                                                  \
+  template cudaError_t launch_dslash<RL, NC, RS>(const GeomH&, void*, const void*, const void*, const void*,  \
+                                                 const void*, int, int, int, double, double*, const int*,     \
+                                                 cudaStream_t);                                               \
+  template cudaError_t launch_fermion_force<RL, NC, RS>(const GeomH&, const void*, const void*, const void*,  \
+                                                        const void*, const void*, void*, double, int,         \
+                                                        cudaStream_t);
+FG_INST_F(double, 9, double)
+FG_INST_F(double, 6, double)
+FG_INST_F(float, 9, float)
+FG_INST_F(float, 6, float)
+FG_INST_F(float, 9, double)
+FG_INST_F(float, 6, double)
+
+template cudaError_t launch_cg_axpy<double>(void*, void*, const void*, const void*, const double*, int, CgDev*, int,
+                                            double*, int, cudaStream_t);
+template cudaError_t launch_cg_axpy<float>(void*, void*, const void*, const void*, const double*, int, CgDev*, int,
+                                           double*, int, cudaStream_t);
+template cudaError_t launch_cg_xpay<double>(void*, const void*, const double*, int, CgDev*, int, double*, int,
+                                            cudaStream_t);
+template cudaError_t launch_cg_xpay<float>(void*, const void*, const double*, int, CgDev*, int, double*, int,
+                                           cudaStream_t);
+template cudaError_t launch_ru_accumulate<double>(void*, void*, int, cudaStream_t);
+template cudaError_t launch_ru_accumulate<float>(void*, void*, int, cudaStream_t);
+template cudaError_t launch_ru_residual<double>(const void*, const void*, void*, void*, double*, int, cudaStream_t);
+template cudaError_t launch_ru_residual<float>(const void*, const void*, void*, void*, double*, int, cudaStream_t);
+template cudaError_t launch_convert<double, double>(void*, const void*, double*, int, cudaStream_t);
+template cudaError_t launch_convert<float, double>(void*, const void*, double*, int, cudaStream_t);
+template cudaError_t launch_convert<double, float>(void*, const void*, double*, int, cudaStream_t);
+template cudaError_t launch_convert<float, float>(void*, const void*, double*, int, cudaStream_t);
+template cudaError_t launch_gaussian_spinor<double>(void*, int, uint64_t, uint32_t, cudaStream_t);
+template cudaError_t launch_gaussian_spinor<float>(void*, int, uint64_t, uint32_t, cudaStream_t);
+template cudaError_t launch_spinor_to_device<double>(const double*, void*, int, cudaStream_t);
+template cudaError_t launch_spinor_to_device<float>(const double*, void*, int, cudaStream_t);
+template cudaError_t launch_spinor_to_canon<double>(const void*, double*, int, cudaStream_t);
+template cudaError_t launch_spinor_to_canon<float>(const void*, double*, int, cudaStream_t);
+
+}  // namespace fg

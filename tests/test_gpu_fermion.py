@@ -1,0 +1,249 @@
+"""GPU parity of the Wilson-fermion path (Dslash, CG, pseudofermion force,
+heat bath, fermion HMC) against the FP64 oracle, through the C ABI.
+
+Tolerances:
+* FP64 operator applications: normwise relative 1e-13.
+* Solves: the FP64 true residual must meet cg_tol (checked by the library and
+  here); solutions agree with the oracle to cg_tol times a condition factor.
+* Forces and MD steps use cg_tol = 1e-12 on both sides, so they agree to
+  ~1e-10 relative (the difference of two solves at that tolerance).
+"""
+
+import numpy as np
+import pytest
+
+from oracle import fermion as fe, gauge, integrators as it
+from paper_0910_2950_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+BETA, KAPPA = 5.6, 0.12
+
+
+@pytest.fixture(scope="module")
+def fgmod():
+    from paper_0910_2950_gb300 import build, fg
+    build.build()
+    fg.load()
+    return fg
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def _rand_even(dims, seed):
+    g = inputs.make_rng(seed)
+    v = inputs.volume(dims)
+    return g.standard_normal((v // 2, 4, 3)) + 1j * g.standard_normal((v // 2, 4, 3))
+
+
+DIMS = [(4, 4, 4, 4), (6, 4, 2, 6), (2, 2, 2, 4), (8, 4, 4, 8)]
+
+
+@pytest.mark.parametrize("dims", DIMS)
+@pytest.mark.parametrize("dagger", [False, True])
+@pytest.mark.parametrize("link_reals", [18, 12])
+def test_apply_mhat_fp64(fgmod, dims, dagger, link_reals):
+    u = inputs.hot_start(dims, 2)
+    psi = _rand_even(dims, 3)
+    with fgmod.Lattice(dims, BETA, kappa=KAPPA, link_reals=link_reals) as lat:
+        lat.set_gauge(u)
+        out = lat.apply_mhat(psi, dagger=dagger)
+    full = inputs.unpack_even(psi, dims)
+    ref = (fe.mhat_dag if dagger else fe.mhat)(u, KAPPA, full)
+    assert _rel(out, inputs.pack_even(ref, dims)) < 1e-13
+
+
+def test_apply_mhat_fp32_links_in_fp64_arithmetic(fgmod):
+    dims = (6, 4, 2, 6)
+    u = inputs.hot_start(dims, 2)
+    u32 = u.astype(np.complex64).astype(np.complex128)
+    psi = _rand_even(dims, 4)
+    with fgmod.Lattice(dims, BETA, kappa=KAPPA, precision="fp32") as lat:
+        lat.set_gauge(u)
+        out = lat.apply_mhat(psi)
+    ref = inputs.pack_even(fe.mhat(u32, KAPPA, inputs.unpack_even(psi, dims)), dims)
+    assert _rel(out, ref) < 1e-13
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 2, 6)])
+def test_cg_solve(fgmod, precision, dims):
+    u = inputs.hot_start(dims, 5)
+    b = _rand_even(dims, 6)
+    tol = 1e-10
+    with fgmod.Lattice(dims, BETA, kappa=0.158, precision=precision, cg_tol=tol) as lat:
+        lat.set_gauge(u)
+        x, info = lat.cg_solve(b)
+    assert info["true_residual"] <= tol
+    assert info["iterations"] > 0
+    if precision == "fp32":
+        assert info["reliable_updates"] >= 1
+    uu = u.astype(np.complex64).astype(np.complex128) if precision == "fp32" else u
+    full_x = inputs.unpack_even(x, dims)
+    res = inputs.unpack_even(b, dims) - fe.mdagm(uu, 0.158, full_x)
+    assert np.linalg.norm(res) <= 1.01 * tol * np.linalg.norm(b)
+    xo, _ = fe.cg(uu, 0.158, inputs.unpack_even(b, dims), tol=1e-13)
+    assert _rel(x, inputs.pack_even(xo, dims)) < 1e-7
+
+
+def test_cg_matches_dense_solve_2x2x2x2(fgmod):
+    dims = (2, 2, 2, 2)
+    u = inputs.hot_start(dims, 3)
+    b = _rand_even(dims, 8)
+    with fgmod.Lattice(dims, BETA, kappa=KAPPA, cg_tol=1e-13) as lat:
+        lat.set_gauge(u)
+        x, info = lat.cg_solve(b)
+    # dense M^dagger M on the 96 even-site unknowns, built column by column
+    n = 96
+    cols = []
+    for j in range(n):
+        e = np.zeros(n, dtype=np.complex128)
+        e[j] = 1
+        cols.append(inputs.pack_even(fe.mdagm(u, KAPPA, inputs.unpack_even(e.reshape(8, 4, 3), dims)),
+                                     dims).reshape(-1))
+    mat = np.array(cols).T
+    xd = np.linalg.solve(mat, b.reshape(-1))
+    assert _rel(x.reshape(-1), xd) < 1e-11
+
+
+def test_zero_rhs_and_state_errors(fgmod):
+    dims = (4, 4, 4, 4)
+    with fgmod.Lattice(dims, BETA, kappa=KAPPA) as lat:
+        x, info = lat.cg_solve(np.zeros((128, 4, 3), np.complex128))
+        assert np.all(x == 0) and info["iterations"] == 0
+    with fgmod.Lattice(dims, BETA) as lat:
+        with pytest.raises(fgmod.FgError) as e:
+            lat.apply_mhat(np.zeros((128, 4, 3), np.complex128))
+        assert e.value.status == fgmod.FG_ESTATE
+
+
+def test_cg_iteration_cap_reports_enoconv(fgmod):
+    dims = (4, 4, 4, 4)
+    with fgmod.Lattice(dims, BETA, kappa=0.158, cg_maxiter=3, cg_tol=1e-12) as lat:
+        lat.set_gauge(inputs.hot_start(dims, 1))
+        with pytest.raises(fgmod.FgError) as e:
+            lat.cg_solve(_rand_even(dims, 1))
+        assert e.value.status == fgmod.FG_ENOCONV
+        # the handle stays usable
+        x, info = lat.apply_mhat(_rand_even(dims, 2)), None
+        assert np.isfinite(x).all()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_heatbath_action(fgmod, precision):
+    dims = (6, 4, 2, 6)
+    u = inputs.hot_start(dims, 4)
+    chi = inputs.gaussian_spinor_even(dims, 5)
+    with fgmod.Lattice(dims, BETA, kappa=KAPPA, precision=precision, cg_tol_action=1e-12) as lat:
+        lat.set_gauge(u)
+        lat.set_pseudofermion(chi)
+        sg, sf, t = lat.action()
+    assert abs(sf - np.vdot(chi, chi).real) < 1e-9 * sf
+    assert abs(sg - gauge.wilson_action(u, BETA)) < (1e-12 if precision == "fp64" else 1e-5) * sg
+
+
+@pytest.mark.parametrize("link_reals", [18, 12])
+def test_total_force_fp64(fgmod, link_reals):
+    dims = (6, 4, 2, 6)
+    u = inputs.hot_start(dims, 6)
+    chi = inputs.gaussian_spinor_even(dims, 7)
+    with fgmod.Lattice(dims, BETA, kappa=KAPPA, cg_tol=1e-13, link_reals=link_reals) as lat:
+        lat.set_gauge(u)
+        lat.set_pseudofermion(chi)
+        f = lat.force()
+    phi = fe.heatbath_phi(u, KAPPA, inputs.unpack_even(chi, dims))
+    ref = gauge.gauge_force(u, BETA) + fe.fermion_force(u, KAPPA, phi, tol=1e-13)
+    assert _rel(f, ref) < 1e-10
+
+
+def test_fermion_force_fp32(fgmod):
+    dims = (6, 4, 2, 6)
+    u = inputs.hot_start(dims, 6)
+    chi = inputs.gaussian_spinor_even(dims, 7)
+    with fgmod.Lattice(dims, BETA, kappa=KAPPA, precision="fp32", cg_tol=1e-10) as lat:
+        lat.set_gauge(u)
+        lat.set_pseudofermion(chi)
+        f = lat.force()
+    phi = fe.heatbath_phi(u, KAPPA, inputs.unpack_even(chi, dims))
+    ref = gauge.gauge_force(u, BETA) + fe.fermion_force(u, KAPPA, phi, tol=1e-12)
+    assert _rel(f, ref) < 5e-6
+
+
+@pytest.mark.parametrize("name", ["fg", "omelyan", "leapfrog"])
+def test_fermion_md_step_fp64(fgmod, name):
+    dims = (4, 4, 2, 4)
+    u = inputs.hot_start(dims, 8)
+    p = inputs.gaussian_momenta(dims, 9)
+    chi = inputs.gaussian_spinor_even(dims, 10)
+    with fgmod.Lattice(dims, BETA, kappa=KAPPA, cg_tol=1e-13) as lat:
+        lat.set_gauge(u)
+        lat.set_pseudofermion(chi)
+        lat.set_momenta(p)
+        lat.md_step(name, 0.1)
+        ug, pg = lat.get_gauge(), lat.get_momenta()
+    phi = fe.heatbath_phi(u, KAPPA, inputs.unpack_even(chi, dims))
+    system = fe.FermionSystem(BETA, KAPPA, phi, tol=1e-13)
+    uo, po = it.md_step(system, it.Integrator(name), u, p, 0.1)
+    assert _rel(ug, uo) < 1e-11
+    assert _rel(pg, po) < 1e-10
+
+
+@pytest.fixture(scope="module")
+def fermion_traj_oracle():
+    dims = (4, 4, 2, 4)
+    u = inputs.hot_start(dims, 11)
+    p = inputs.gaussian_momenta(dims, 12)
+    chi = inputs.gaussian_spinor_even(dims, 13)
+    phi = fe.heatbath_phi(u, KAPPA, inputs.unpack_even(chi, dims))
+    out = {}
+    for dt in (0.25, 0.125):
+        system = fe.FermionSystem(BETA, KAPPA, phi, tol=1e-13)
+        u1, p1, h0, h1 = it.trajectory(system, it.Integrator("fg"), u, p, dt, 1.0)
+        out[dt] = (h1 - h0, h0, u1)
+    return dims, u, p, chi, out
+
+
+@pytest.mark.parametrize("dt", [0.25, 0.125])
+def test_fermion_fg_trajectory_dh_fp64(fgmod, fermion_traj_oracle, dt):
+    dims, u, p, chi, ref = fermion_traj_oracle
+    with fgmod.Lattice(dims, BETA, kappa=KAPPA, cg_tol=1e-13, cg_tol_action=1e-13) as lat:
+        lat.set_gauge(u)
+        lat.set_pseudofermion(chi)
+        lat.set_momenta(p)
+        r = lat.trajectory("fg", dt, 1.0, refresh=False, u_accept=0.0)
+        ug = lat.get_gauge()
+    dh_o, h0_o, u1_o = ref[dt]
+    assert abs(r["dH"] - dh_o) < 1e-6, (r["dH"], dh_o)
+    assert abs(r["H0"] - h0_o) < 1e-9 * abs(h0_o)
+    assert _rel(ug, u1_o) < 1e-10
+    n = r["n_steps"]
+    assert r["n_force"] == 3 * n + 1
+    # one solve per force evaluation plus the action solve at the end; S_F at
+    # the start is chi^dagger chi from the heat bath
+    assert r["n_solves"] == 3 * n + 1 + 1
+    assert r["cg_iters"] > 0
+
+
+def test_fermion_fg_trajectory_fp32_mixed(fgmod, fermion_traj_oracle):
+    dims, u, p, chi, ref = fermion_traj_oracle
+    with fgmod.Lattice(dims, BETA, kappa=KAPPA, precision="fp32", cg_tol=1e-10,
+                       cg_tol_action=1e-12) as lat:
+        lat.set_gauge(u)
+        lat.set_pseudofermion(chi)
+        lat.set_momenta(p)
+        r = lat.trajectory("fg", 0.125, 1.0, refresh=False, u_accept=0.0)
+    # FP32 links and forces: dH moves by ~1e-7 relative to the O(10^3) terms of H
+    assert abs(r["dH"] - ref[0.125][0]) < 5e-4, (r["dH"], ref[0.125][0])
+
+
+def test_device_pseudofermion_refresh(fgmod):
+    dims = (8, 8, 4, 8)
+    with fgmod.Lattice(dims, BETA, kappa=KAPPA, seed=77) as lat:
+        lat.set_gauge(inputs.hot_start(dims, 1))
+        lat.refresh_pseudofermion()
+        sg, sf, t = lat.action()
+    # S_F = chi^dagger chi ~ 12 V/2 (one unit per complex component)
+    v = inputs.volume(dims)
+    assert abs(sf / (12 * v / 2) - 1) < 5 * np.sqrt(1 / (12 * v / 2))
