@@ -221,6 +221,47 @@ fg_status fg_sync(fg_lattice *h);
 /* Device bytes held by the handle. */
 unsigned long long fg_device_bytes(const fg_lattice *h);
 
+
+/* ------------------------------------------------------------------------
+ * Allocation-free action sums (no handle).
+ *
+ * The paper has no counterpart to this entry point.  It is for callers that
+ * cannot let this library allocate device memory: a process whose GPU memory
+ * is already reserved in full by another allocator (for example the caching
+ * allocator of a framework that owns the device, where an extra cudaMalloc
+ * fails or fragments the pool), or a latency-critical loop in which a
+ * cudaMalloc/cudaFree pair would synchronise the device.
+ *
+ * It computes the same two sums as fg_action,
+ *   S_G = beta sum_{x, mu<nu} (1 - Re Tr U_{mu nu}(x) / 3)   -> dev_out[0]
+ *   T   = (1/2) sum_{links, a} (p^a)^2                       -> dev_out[1]
+ * (T = 0 if dev_momenta is NULL), in FP64, from caller-owned device arrays
+ * in the canonical host layout above (gauge double[V][4][3][3][2], momenta
+ * double[V][4][8]); dev_out is caller-owned device memory for two doubles.
+ * Work is queued on cuda_stream (NULL = the legacy default stream) and the
+ * call returns without synchronising.
+ *
+ * Scratch: the per-block partial sums go to one fixed 1 MiB device array
+ * inside the library, sized for at most FG_NOALLOC_MAX_SITES sites; every
+ * GPU that loads the library holds it until the process exits.  The call
+ * itself allocates nothing (no cudaMalloc, cudaFree or allocating library
+ * routine).  The first call on each device looks up the array's device
+ * address with that device current and caches it, so make that first call
+ * before any stream capture.  Every call shares the array and overwrites
+ * each entry it later reads, so nothing carries over from the previous
+ * call; calls whose kernels overlap on the GPU (other streams or other host
+ * threads on the same device) race on the array and must be serialised by
+ * the caller.
+ *
+ * Errors: FG_EINVAL for a null links/out/dims pointer, an odd or < 2 extent,
+ * or more than FG_NOALLOC_MAX_SITES sites (nothing is queued); FG_ECUDA if
+ * the address lookup or a launch fails.
+ */
+#define FG_NOALLOC_MAX_SITES (1LL << 24)
+fg_status fg_action_sums_noalloc(const double *dev_links, const double *dev_momenta,
+                                 const int dims[4], double beta, double *dev_out,
+                                 void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -77,6 +77,7 @@ SIGNATURES = {
     "fg_launch_count": (C.c_longlong, [_vp]),
     "fg_sync": (_i, [_vp]),
     "fg_device_bytes": (C.c_ulonglong, [_vp]),
+    "fg_action_sums_noalloc": (_i, [_vp, _vp, C.POINTER(C.c_int), _d, _vp, _vp]),
 }
 
 _lib = None
