@@ -40,8 +40,8 @@ def _flags(verbose_ptxas: bool) -> list:
     return f
 
 
-def _compile(nvcc, src, obj, verbose_ptxas):
-    cmd = [nvcc, "-c", os.path.join(CSRC, src), "-o", obj] + _flags(verbose_ptxas)
+def _compile(nvcc, src, obj, verbose_ptxas, extra=()):
+    cmd = [nvcc, "-c", os.path.join(CSRC, src), "-o", obj] + _flags(verbose_ptxas) + list(extra)
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"nvcc failed on {src}:\n{res.stdout}\n{res.stderr}")
@@ -57,27 +57,35 @@ def _stale(objs) -> bool:
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 
-def build(force: bool = False, verbose_ptxas: bool = False, quiet: bool = True) -> str:
-    """Build (if stale) and return the path of libfg_lattice.so."""
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose_ptxas: bool = False, quiet: bool = True,
+          extra_flags=(), out: str = None) -> str:
+    """Build (if stale) and return the path of libfg_lattice.so.
+
+    `extra_flags` are appended to every nvcc compile (e.g. -D tuning macros)
+    and `out` writes the library elsewhere (both imply a fresh build).
+    """
+    lib = out or LIB
+    bdir = BUILD if out is None else os.path.join(os.path.dirname(os.path.abspath(out)), "_build")
+    os.makedirs(bdir, exist_ok=True)
     sources = [s for s in SOURCES if os.path.exists(os.path.join(CSRC, s))]
-    objs = [os.path.join(BUILD, os.path.splitext(s)[0] + ".o") for s in sources]
-    if not force and not verbose_ptxas and not _stale(objs):
+    objs = [os.path.join(bdir, os.path.splitext(s)[0] + ".o") for s in sources]
+    if not force and not verbose_ptxas and not extra_flags and out is None and not _stale(objs):
         return LIB
     nvcc = nvcc_path()
     with cf.ThreadPoolExecutor(max_workers=len(sources)) as ex:
-        logs = list(ex.map(lambda so: _compile(nvcc, so[0], so[1], verbose_ptxas), zip(sources, objs)))
-    tmp = LIB + ".tmp"
+        logs = list(ex.map(lambda so: _compile(nvcc, so[0], so[1], verbose_ptxas, extra_flags),
+                           zip(sources, objs)))
+    tmp = lib + ".tmp"
     cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-cudart=static"]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     if not quiet or verbose_ptxas:
         for log in logs:
             if log.strip():
                 print(log, file=sys.stderr)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":

@@ -25,6 +25,9 @@ static inline Geom to_devg(const GeomH& h) {
   Geom g;
   for (int i = 0; i < 4; ++i) g.L[i] = h.L[i];
   g.Lxh = h.Lxh; g.Vh = h.Vh; g.V = h.V;
+  g.dLxh = make_fastdiv((uint32_t)h.Lxh);
+  g.dLy = make_fastdiv((uint32_t)h.L[1]);
+  g.dLz = make_fastdiv((uint32_t)h.L[2]);
   return g;
 }
 
@@ -32,25 +35,24 @@ template <typename R> struct Spinor {
   Cx<R> s[4][3];
 };
 
+// Spinor entry k = spin * 3 + colour sits in pair k / 2, slot k % 2.
 template <typename R>
 __device__ __forceinline__ Spinor<R> load_spinor(const typename Vec2<R>::T* __restrict__ f, int i, int Vh) {
   Spinor<R> x;
 #pragma unroll
-  for (int k = 0; k < 12; ++k) {
-    const typename Vec2<R>::T v = __ldg(f + (size_t)k * Vh + i);
-    x.s[k / 3][k % 3] = cx<R>(v.x, v.y);
+  for (int q = 0; q < 6; ++q) {
+    Cx<R> a, b;
+    Quad<R>::load(f, (size_t)q * Vh + i, a, b);
+    x.s[(2 * q) / 3][(2 * q) % 3] = a;
+    x.s[(2 * q + 1) / 3][(2 * q + 1) % 3] = b;
   }
   return x;
 }
 template <typename R>
 __device__ __forceinline__ void store_spinor(typename Vec2<R>::T* __restrict__ f, int i, int Vh, const Spinor<R>& x) {
 #pragma unroll
-  for (int k = 0; k < 12; ++k) {
-    typename Vec2<R>::T v;
-    v.x = x.s[k / 3][k % 3].re;
-    v.y = x.s[k / 3][k % 3].im;
-    f[(size_t)k * Vh + i] = v;
-  }
+  for (int q = 0; q < 6; ++q)
+    Quad<R>::store(f, (size_t)q * Vh + i, x.s[(2 * q) / 3][(2 * q) % 3], x.s[(2 * q + 1) / 3][(2 * q + 1) % 3]);
 }
 
 template <typename RO, typename RI>
@@ -197,29 +199,22 @@ __global__ void __launch_bounds__(kDslashThreads) dslash_kernel(
 }
 
 // --------------------------------------------------------------------------- force
-template <typename RL, int NC, typename RS>
-__global__ void __launch_bounds__(256) fermion_force_kernel(
-    Gauge<RL, NC> U, const typename Vec2<RS>::T* __restrict__ Xe, const typename Vec2<RS>::T* __restrict__ Xo,
+template <int MU, typename RL, int NC, typename RS>
+__device__ __forceinline__ void fermion_force_link(
+    const Gauge<RL, NC>& U, const typename Vec2<RS>::T* __restrict__ Xe, const typename Vec2<RS>::T* __restrict__ Xo,
     const typename Vec2<RS>::T* __restrict__ Ye, const typename Vec2<RS>::T* __restrict__ Yo,
-    Mom<RL> FF, Geom g, RL kappa2, int accumulate) {
-  const int s = blockIdx.x * 64 + threadIdx.x;
-  const int mu = threadIdx.y;
-  if (s >= g.V) return;
-  int c[4], par;
-  cb_coords(g, s, c, par);
-  const int sn = cb_neighbor(g, c, mu, +1);
+    const Mom<RL>& FF, const Geom& g, const int c[4], int s, int par, RL kappa2, int accumulate) {
+  const int sn = cb_neighbor(g, c, MU, +1);
   const int i = s - par * g.Vh, in = sn - (1 - par) * g.Vh;
   const Spinor<RS> x0 = load_spinor<RS>(par ? Xo : Xe, i, g.Vh);
   const Spinor<RS> y0 = load_spinor<RS>(par ? Yo : Ye, i, g.Vh);
   const Spinor<RS> x1 = load_spinor<RS>(par ? Xe : Xo, in, g.Vh);
   const Spinor<RS> y1 = load_spinor<RS>(par ? Ye : Yo, in, g.Vh);
   Cx<RS> hx[2][3], hy[2][3], gx[2][3], gy[2][3];
-  switch (mu) {
-    case 0: project<0, 1>(x1, hx); project<0, 1>(y0, hy); project<0, -1>(x0, gx); project<0, -1>(y1, gy); break;
-    case 1: project<1, 1>(x1, hx); project<1, 1>(y0, hy); project<1, -1>(x0, gx); project<1, -1>(y1, gy); break;
-    case 2: project<2, 1>(x1, hx); project<2, 1>(y0, hy); project<2, -1>(x0, gx); project<2, -1>(y1, gy); break;
-    default: project<3, 1>(x1, hx); project<3, 1>(y0, hy); project<3, -1>(x0, gx); project<3, -1>(y1, gy); break;
-  }
+  project<MU, 1>(x1, hx);
+  project<MU, 1>(y0, hy);
+  project<MU, -1>(x0, gx);
+  project<MU, -1>(y1, gy);
   M3<RS> m1, m2;
 #pragma unroll
   for (int a = 0; a < 3; ++a)
@@ -234,10 +229,10 @@ __global__ void __launch_bounds__(256) fermion_force_kernel(
       m1.e[a][b] = s1;
       m2.e[a][b] = s2;
     }
-  const M3<RS> u = convert<RS>(U.load(mu, s));
+  const M3<RS> u = convert<RS>(U.load(MU, s));
   M3<RS> w = mul(u, m1);
   const M3<RS> t = mul_nd(m2, u);
-  const RS sign = (mu == 3 && c[3] == g.L[3] - 1) ? RS(-1) : RS(1);
+  const RS sign = (MU == 3 && c[3] == g.L[3] - 1) ? RS(-1) : RS(1);
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -245,10 +240,27 @@ __global__ void __launch_bounds__(256) fermion_force_kernel(
   RS f[8];
   im_tr_gellmann(w, f);
   RL out[8];
-  if (accumulate) FF.load(mu, s, out);
+  if (accumulate) FF.load(MU, s, out);
 #pragma unroll
   for (int k = 0; k < 8; ++k) out[k] = (accumulate ? out[k] : RL(0)) - kappa2 * RL(f[k]);
-  FF.store(mu, s, out);
+  FF.store(MU, s, out);
+}
+
+template <typename RL, int NC, typename RS>
+__global__ void __launch_bounds__(256) fermion_force_kernel(
+    Gauge<RL, NC> U, const typename Vec2<RS>::T* __restrict__ Xe, const typename Vec2<RS>::T* __restrict__ Xo,
+    const typename Vec2<RS>::T* __restrict__ Ye, const typename Vec2<RS>::T* __restrict__ Yo,
+    Mom<RL> FF, Geom g, RL kappa2, int accumulate) {
+  const int s = blockIdx.x * 64 + threadIdx.x;
+  if (s >= g.V) return;
+  int c[4], par;
+  cb_coords(g, s, c, par);
+  switch (threadIdx.y) {
+    case 0: fermion_force_link<0, RL, NC, RS>(U, Xe, Xo, Ye, Yo, FF, g, c, s, par, kappa2, accumulate); break;
+    case 1: fermion_force_link<1, RL, NC, RS>(U, Xe, Xo, Ye, Yo, FF, g, c, s, par, kappa2, accumulate); break;
+    case 2: fermion_force_link<2, RL, NC, RS>(U, Xe, Xo, Ye, Yo, FF, g, c, s, par, kappa2, accumulate); break;
+    default: fermion_force_link<3, RL, NC, RS>(U, Xe, Xo, Ye, Yo, FF, g, c, s, par, kappa2, accumulate); break;
+  }
 }
 
 // --------------------------------------------------------------------------- CG vectors
@@ -454,6 +466,8 @@ __global__ void __launch_bounds__(256) gaussian_spinor_kernel(typename Vec2<R>::
   }
 }
 
+// canonical [Vh][12] complex <-> device pair-major (entry k of site i at
+// pair k / 2, slot k % 2: flat complex index ((k / 2) * Vh + i) * 2 + k % 2)
 template <typename R>
 __global__ void spinor_to_device_kernel(const double* __restrict__ canon, typename Vec2<R>::T* __restrict__ f, int Vh) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -462,7 +476,7 @@ __global__ void spinor_to_device_kernel(const double* __restrict__ canon, typena
   typename Vec2<R>::T v;
   v.x = R(canon[(size_t)t * 2]);
   v.y = R(canon[(size_t)t * 2 + 1]);
-  f[(size_t)k * Vh + i] = v;
+  f[((size_t)(k >> 1) * Vh + i) * 2 + (k & 1)] = v;
 }
 
 template <typename R>
@@ -470,7 +484,7 @@ __global__ void spinor_to_canon_kernel(const typename Vec2<R>::T* __restrict__ f
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 12 * Vh) return;
   const int i = t / 12, k = t % 12;
-  const typename Vec2<R>::T v = f[(size_t)k * Vh + i];
+  const typename Vec2<R>::T v = f[((size_t)(k >> 1) * Vh + i) * 2 + (k & 1)];
   canon[(size_t)t * 2] = v.x;
   canon[(size_t)t * 2 + 1] = v.y;
 }
@@ -490,7 +504,7 @@ cudaError_t launch_dslash(const GeomH& gh, void* out, const void* in, const void
                           const void* U, int out_par, int dag, int mode, double b, double* partial,
                           const int* done, cudaStream_t st) {
   Gauge<RL, NC> u;
-  u.p = (typename Vec2<RL>::T*)U;
+  u.p = const_cast<void*>(U);
   u.V = gh.V;
   const Geom g = to_devg(gh);
   const int nb = dslash_blocks(gh.Vh);
@@ -511,10 +525,10 @@ template <typename RL, int NC, typename RS>
 cudaError_t launch_fermion_force(const GeomH& gh, const void* U, const void* Xe, const void* Xo, const void* Ye,
                                  const void* Yo, void* FF, double kappa2, int accumulate, cudaStream_t st) {
   Gauge<RL, NC> u;
-  u.p = (typename Vec2<RL>::T*)U;
+  u.p = const_cast<void*>(U);
   u.V = gh.V;
   Mom<RL> f;
-  f.p = (typename Vec2<RL>::T*)FF;
+  f.p = FF;
   f.V = gh.V;
   fermion_force_kernel<RL, NC, RS><<<(gh.V + 63) / 64, dim3(64, 4), 0, st>>>(
       u, cv2<RS>(Xe), cv2<RS>(Xo), cv2<RS>(Ye), cv2<RS>(Yo), f, to_devg(gh), RL(kappa2), accumulate);

@@ -3,12 +3,13 @@
 // Device layout of every field (structure of arrays, checkerboard order):
 //   site index s = parity * Vh + lex / 2, parity = (x+y+z+t) & 1, Vh = V / 2,
 //   so each parity half is contiguous and a warp of consecutive s touches
-//   consecutive addresses for every component.
-//   gauge   Cplx2[4 mu][NC][V]   NC = 9 complex entries (18 reals) or 6 (12 reals:
-//                                rows 0-1, row 2 rebuilt as (row0 x row1)^*)
-//   momenta Cplx2[4 mu][4][V]    Gell-Mann coefficient pairs (p0,p1) .. (p6,p7)
-//   spinor  Cplx2[12][Vh]        spin-major (spin * 3 + colour), one parity
-// where Cplx2 is float2 or double2 (re, im).
+//   consecutive addresses for every component.  Complex entries are stored
+//   in pairs (2 complex = 16 bytes in FP32, 32 bytes in FP64):
+//   gauge   Pair[4 mu][NC/2][V] (+ Cplx[4 mu][V] for the 9th entry when NC = 9)
+//           NC = 9 complex entries (18 reals) or 6 (12 reals: rows 0-1, row 2
+//           rebuilt as (row0 x row1)^*)
+//   momenta Pair[4 mu][2][V]    Gell-Mann coefficients (p0..p3), (p4..p7)
+//   spinor  Pair[6][Vh]         entries spin * 3 + colour, two per pair, one parity
 #pragma once
 
 #include <cuda_runtime.h>
@@ -248,32 +249,47 @@ template <typename R> __device__ __forceinline__ void rebuild_row2(M3<R>& u) {
   u.e[2][2] = conj(u.e[0][0] * u.e[1][1] - u.e[0][1] * u.e[1][0]);
 }
 
-// Gram-Schmidt of rows 0-1 (norms in FP64), then row 2 from the cross product.
+// Gram-Schmidt of rows 0-1 in the link's own precision, then row 2 from the
+// cross product.
 template <typename R> __device__ __forceinline__ void reunitarize(M3<R>& u) {
-  double n0 = 0;
+  R n0 = 0;
 #pragma unroll
-  for (int j = 0; j < 3; ++j) n0 += double(u.e[0][j].re) * u.e[0][j].re + double(u.e[0][j].im) * u.e[0][j].im;
-  const double in0 = rsqrt(n0);
+  for (int j = 0; j < 3; ++j) n0 += u.e[0][j].re * u.e[0][j].re + u.e[0][j].im * u.e[0][j].im;
+  const R in0 = rsqrt(n0);
 #pragma unroll
-  for (int j = 0; j < 3; ++j) u.e[0][j] = cx<R>(R(u.e[0][j].re * in0), R(u.e[0][j].im * in0));
-  double pr = 0, pi = 0;  // <row0, row1>
+  for (int j = 0; j < 3; ++j) u.e[0][j] = in0 * u.e[0][j];
+  Cx<R> pr = cx<R>(0, 0);  // <row0, row1>
 #pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    pr += double(u.e[0][j].re) * u.e[1][j].re + double(u.e[0][j].im) * u.e[1][j].im;
-    pi += double(u.e[0][j].re) * u.e[1][j].im - double(u.e[0][j].im) * u.e[1][j].re;
-  }
-  double r1[3][2];
-  double n1 = 0;
+  for (int j = 0; j < 3; ++j) cmac_cj(pr, u.e[0][j], u.e[1][j]);
+  R n1 = 0;
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
-    r1[j][0] = u.e[1][j].re - (pr * u.e[0][j].re - pi * u.e[0][j].im);
-    r1[j][1] = u.e[1][j].im - (pr * u.e[0][j].im + pi * u.e[0][j].re);
-    n1 += r1[j][0] * r1[j][0] + r1[j][1] * r1[j][1];
+    u.e[1][j] = u.e[1][j] - pr * u.e[0][j];
+    n1 += u.e[1][j].re * u.e[1][j].re + u.e[1][j].im * u.e[1][j].im;
   }
-  const double in1 = rsqrt(n1);
+  const R in1 = rsqrt(n1);
 #pragma unroll
-  for (int j = 0; j < 3; ++j) u.e[1][j] = cx<R>(R(r1[j][0] * in1), R(r1[j][1] * in1));
+  for (int j = 0; j < 3; ++j) u.e[1][j] = in1 * u.e[1][j];
   rebuild_row2(u);
+}
+
+// ---------------------------------------------------------------------------
+// Exact division of a 32-bit n by a run-time constant d >= 1 without the
+// integer-divide sequence: q = floor(c n / 2^64) with c = floor((2^64-1)/d) + 1
+// (Lemire, Kaser and Kurz, "Faster remainder by direct computation", 2019);
+// d = 1 is special-cased because c would overflow.
+struct FastDiv {
+  uint32_t d;
+  unsigned long long c;
+};
+inline FastDiv make_fastdiv(uint32_t d) {
+  FastDiv f;
+  f.d = d;
+  f.c = d > 1 ? (~0ULL) / d + 1 : 0ULL;
+  return f;
+}
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f) {
+  return f.d == 1 ? n : (uint32_t)__umul64hi(f.c, (unsigned long long)n);
 }
 
 // ---------------------------------------------------------------------------
@@ -283,18 +299,20 @@ struct Geom {
   int Lxh;      // Lx / 2
   int Vh;       // V / 2
   int V;
+  FastDiv dLxh, dLy, dLz;
 };
 
 __device__ __forceinline__ void cb_coords(const Geom& g, int s, int c[4], int& par) {
   par = s >= g.Vh;
-  int i = s - par * g.Vh;
-  const int xh = i % g.Lxh;
-  i /= g.Lxh;
-  c[1] = i % g.L[1];
-  i /= g.L[1];
-  c[2] = i % g.L[2];
-  c[3] = i / g.L[2];
-  c[0] = 2 * xh + ((c[1] + c[2] + c[3] + par) & 1);
+  const uint32_t i = (uint32_t)(s - par * g.Vh);
+  const uint32_t q1 = fdiv(i, g.dLxh);
+  const uint32_t xh = i - q1 * (uint32_t)g.Lxh;
+  const uint32_t q2 = fdiv(q1, g.dLy);
+  c[1] = (int)(q1 - q2 * (uint32_t)g.L[1]);
+  const uint32_t q3 = fdiv(q2, g.dLz);
+  c[2] = (int)(q2 - q3 * (uint32_t)g.L[2]);
+  c[3] = (int)q3;
+  c[0] = 2 * (int)xh + ((c[1] + c[2] + c[3] + par) & 1);
 }
 
 __device__ __forceinline__ int cb_index(const Geom& g, const int c[4]) {
@@ -303,7 +321,9 @@ __device__ __forceinline__ int cb_index(const Geom& g, const int c[4]) {
   return par * g.Vh + (lex >> 1);
 }
 
-// Index of the neighbour x + d * mu-hat (d = +1 or -1), periodic.
+// Index of the neighbour x + d * mu-hat (d = +1 or -1), periodic.  Call with
+// compile-time mu (unrolled loops or template arguments) so that the
+// coordinate array stays in registers.
 __device__ __forceinline__ int cb_neighbor(const Geom& g, const int c[4], int mu, int d) {
   int n[4] = {c[0], c[1], c[2], c[3]};
   int v = n[mu] + d;
@@ -311,6 +331,32 @@ __device__ __forceinline__ int cb_neighbor(const Geom& g, const int c[4], int mu
   n[mu] = v;
   return cb_index(g, n);
 }
+// The same with a run-time direction, by selects instead of an indexed
+// coordinate array (which the compiler would place in local memory).
+__device__ __forceinline__ int sel4(const int v[4], int i) {
+  return i == 0 ? v[0] : (i == 1 ? v[1] : (i == 2 ? v[2] : v[3]));
+}
+__device__ __forceinline__ int cb_neighbor_rt(const Geom& g, const int c[4], int mu, int d) {
+  int n[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    int v = c[k] + (k == mu ? d : 0);
+    v = v < 0 ? v + g.L[k] : (v >= g.L[k] ? v - g.L[k] : v);
+    n[k] = v;
+  }
+  return cb_index(g, n);
+}
+__device__ __forceinline__ int cb_neighbor2_rt(const Geom& g, const int c[4], int mu1, int d1, int mu2, int d2) {
+  int n[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    int v = c[k] + (k == mu1 ? d1 : 0) + (k == mu2 ? d2 : 0);
+    v = v < 0 ? v + g.L[k] : (v >= g.L[k] ? v - g.L[k] : v);
+    n[k] = v;
+  }
+  return cb_index(g, n);
+}
+
 // x + d1 * mu1-hat + d2 * mu2-hat
 __device__ __forceinline__ int cb_neighbor2(const Geom& g, const int c[4], int mu1, int d1, int mu2, int d2) {
   int n[4] = {c[0], c[1], c[2], c[3]};
@@ -322,51 +368,106 @@ __device__ __forceinline__ int cb_neighbor2(const Geom& g, const int c[4], int m
 }
 
 // ---------------------------------------------------------------------------
-// Field access.
+// Field access.  Fields are stored "pair-major": complex entries are grouped
+// in pairs, and pair q of every site is contiguous, so that one thread moves
+// a pair with one 16-byte access in FP32 (float4) or two adjacent 16-byte
+// accesses in FP64.  The flat order of a field is therefore the same in both
+// precisions (pair, site, entry), which lets vector kernels convert and
+// combine fields element by element.
+template <typename R> struct Quad;
+template <> struct Quad<float> {
+  static __device__ __forceinline__ void load(const void* base, size_t idx, Cx<float>& a, Cx<float>& b) {
+    const float4 v = __ldg((const float4*)base + idx);
+    a = cx<float>(v.x, v.y);
+    b = cx<float>(v.z, v.w);
+  }
+  static __device__ __forceinline__ void load_cg(const void* base, size_t idx, Cx<float>& a, Cx<float>& b) {
+    const float4 v = ((const float4*)base)[idx];
+    a = cx<float>(v.x, v.y);
+    b = cx<float>(v.z, v.w);
+  }
+  static __device__ __forceinline__ void store(void* base, size_t idx, Cx<float> a, Cx<float> b) {
+    ((float4*)base)[idx] = make_float4(a.re, a.im, b.re, b.im);
+  }
+};
+template <> struct Quad<double> {
+  static __device__ __forceinline__ void load(const void* base, size_t idx, Cx<double>& a, Cx<double>& b) {
+    const double2* p = (const double2*)base + 2 * idx;
+    const double2 u = __ldg(p), v = __ldg(p + 1);
+    a = cx<double>(u.x, u.y);
+    b = cx<double>(v.x, v.y);
+  }
+  static __device__ __forceinline__ void load_cg(const void* base, size_t idx, Cx<double>& a, Cx<double>& b) {
+    const double2* p = (const double2*)base + 2 * idx;
+    const double2 u = p[0], v = p[1];
+    a = cx<double>(u.x, u.y);
+    b = cx<double>(v.x, v.y);
+  }
+  static __device__ __forceinline__ void store(void* base, size_t idx, Cx<double> a, Cx<double> b) {
+    double2* p = (double2*)base + 2 * idx;
+    p[0] = make_double2(a.re, a.im);
+    p[1] = make_double2(b.re, b.im);
+  }
+};
+
+// Links: NP = NC / 2 pairs per link in [mu][pair][site] order, then, for
+// NC = 9, the ninth entry of every link in [mu][site] order.
 template <typename R, int NC> struct Gauge {
   typedef typename Vec2<R>::T C2;
-  C2* __restrict__ p;
+  static constexpr int NP = NC / 2;
+  void* __restrict__ p;
   int V;
   __device__ __forceinline__ M3<R> load(int mu, int s) const {
     M3<R> m;
-    const C2* b = p + (size_t)mu * NC * V + s;
 #pragma unroll
-    for (int k = 0; k < NC; ++k) {
-      const C2 v = __ldg(b + (size_t)k * V);
-      m.e[k / 3][k % 3] = cx<R>(v.x, v.y);
+    for (int q = 0; q < NP; ++q) {
+      Cx<R> a, b;
+      Quad<R>::load(p, ((size_t)mu * NP + q) * V + s, a, b);
+      m.e[(2 * q) / 3][(2 * q) % 3] = a;
+      m.e[(2 * q + 1) / 3][(2 * q + 1) % 3] = b;
     }
-    if (NC == 6) rebuild_row2(m);
+    if (NC == 9) {
+      const C2* tail = (const C2*)((const char*)p + (size_t)4 * NP * V * 4 * sizeof(R));
+      const C2 v = __ldg(tail + (size_t)mu * V + s);
+      m.e[2][2] = cx<R>(v.x, v.y);
+    } else {
+      rebuild_row2(m);
+    }
     return m;
   }
   __device__ __forceinline__ void store(int mu, int s, const M3<R>& m) const {
-    C2* b = p + (size_t)mu * NC * V + s;
 #pragma unroll
-    for (int k = 0; k < NC; ++k) {
-      C2 v; v.x = m.e[k / 3][k % 3].re; v.y = m.e[k / 3][k % 3].im;
-      b[(size_t)k * V] = v;
+    for (int q = 0; q < NP; ++q)
+      Quad<R>::store(p, ((size_t)mu * NP + q) * V + s, m.e[(2 * q) / 3][(2 * q) % 3],
+                     m.e[(2 * q + 1) / 3][(2 * q + 1) % 3]);
+    if (NC == 9) {
+      C2* tail = (C2*)((char*)p + (size_t)4 * NP * V * 4 * sizeof(R));
+      C2 v;
+      v.x = m.e[2][2].re;
+      v.y = m.e[2][2].im;
+      tail[(size_t)mu * V + s] = v;
     }
   }
 };
 
+// Momenta and forces: the 8 Gell-Mann coefficients of a link as two pairs of
+// (re, im)-like slots, [mu][pair][site].
 template <typename R> struct Mom {
-  typedef typename Vec2<R>::T C2;
-  C2* __restrict__ p;
+  void* __restrict__ p;
   int V;
   __device__ __forceinline__ void load(int mu, int s, R out[8]) const {
-    const C2* b = p + (size_t)mu * 4 * V + s;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const C2 v = b[(size_t)k * V];
-      out[2 * k] = v.x; out[2 * k + 1] = v.y;
+    for (int q = 0; q < 2; ++q) {
+      Cx<R> a, b;
+      Quad<R>::load_cg(p, ((size_t)mu * 2 + q) * V + s, a, b);
+      out[4 * q] = a.re; out[4 * q + 1] = a.im; out[4 * q + 2] = b.re; out[4 * q + 3] = b.im;
     }
   }
   __device__ __forceinline__ void store(int mu, int s, const R in[8]) const {
-    C2* b = p + (size_t)mu * 4 * V + s;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      C2 v; v.x = in[2 * k]; v.y = in[2 * k + 1];
-      b[(size_t)k * V] = v;
-    }
+    for (int q = 0; q < 2; ++q)
+      Quad<R>::store(p, ((size_t)mu * 2 + q) * V + s, cx<R>(in[4 * q], in[4 * q + 1]),
+                     cx<R>(in[4 * q + 2], in[4 * q + 3]));
   }
 };
 

@@ -17,53 +17,64 @@
 
 namespace fg {
 
-static inline Geom to_dev(const GeomH& h) {
+static Geom to_dev(const GeomH& h) {
   Geom g;
   for (int i = 0; i < 4; ++i) g.L[i] = h.L[i];
   g.Lxh = h.Lxh; g.Vh = h.Vh; g.V = h.V;
+  g.dLxh = make_fastdiv((uint32_t)h.Lxh);
+  g.dLy = make_fastdiv((uint32_t)h.L[1]);
+  g.dLz = make_fastdiv((uint32_t)h.L[2]);
   return g;
 }
 
 constexpr int kSitesPerBlock = 64;
 
-template <typename R, int NC>
-__device__ __forceinline__ M3<R> staple_sum(const Gauge<R, NC>& U, const Geom& g, const int c[4],
-                                            int s, int mu) {
+// Tuning knobs of the gauge-force kernel: minimum resident blocks of 256
+// threads per SM (register cap) and whether the loop over the three staple
+// directions is unrolled.
+#ifndef FG_FORCE_MIN_BLOCKS
+#define FG_FORCE_MIN_BLOCKS 3
+#endif
+#ifndef FG_FORCE_UNROLL_NU
+#define FG_FORCE_UNROLL_NU 0
+#endif
+
+// Sum of the six staples that close a plaquette with U_MU(x); the direction
+// loop is unrolled so every neighbour index is formed with compile-time mu, nu.
+template <int MU, typename R, int NC>
+__device__ __forceinline__ M3<R> staple_sum(const Gauge<R, NC>& U, const Geom& g, const int c[4], int s) {
   M3<R> a;
   zero(a);
+  const int s_pmu = cb_neighbor(g, c, MU, +1);
+#if FG_FORCE_UNROLL_NU
+#pragma unroll
+#else
 #pragma unroll 1
+#endif
   for (int k = 1; k < 4; ++k) {
-    const int nu = (mu + k) & 3;
-    const int s_pmu = cb_neighbor(g, c, mu, +1);
-    const int s_pnu = cb_neighbor(g, c, nu, +1);
-    const int s_mnu = cb_neighbor(g, c, nu, -1);
-    const int s_pmu_mnu = cb_neighbor2(g, c, mu, +1, nu, -1);
+    const int nu = (MU + k) & 3;
     {
       // upper: U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag
-      const M3<R> t = mul_nd(U.load(nu, s_pmu), U.load(mu, s_pnu));
+      const M3<R> t = mul_nd(U.load(nu, s_pmu), U.load(MU, cb_neighbor_rt(g, c, nu, +1)));
       mac_nd(a, t, U.load(nu, s));
     }
     {
       // lower: U_nu(x+mu-nu)^dag U_mu(x-nu)^dag U_nu(x-nu) = (U_mu(x-nu) U_nu(x+mu-nu))^dag U_nu(x-nu)
-      const M3<R> t = mul(U.load(mu, s_mnu), U.load(nu, s_pmu_mnu));
+      const int s_mnu = cb_neighbor_rt(g, c, nu, -1);
+      const M3<R> t = mul(U.load(MU, s_mnu), U.load(nu, cb_neighbor2_rt(g, c, MU, +1, nu, -1)));
       mac_dn(a, t, U.load(nu, s_mnu));
     }
   }
   return a;
 }
 
-template <typename R, int NC, int MODE>
-__global__ void __launch_bounds__(256) gauge_force_kernel(Gauge<R, NC> U, Mom<R> P, Mom<R> F,
-                                                          Mom<R> FF, Gauge<R, NC> Ubase,
-                                                          Gauge<R, NC> Uout, Geom g, R beta6,
-                                                          R ckick, R cdrift, R cdisp, int reunit) {
-  const int s = blockIdx.x * kSitesPerBlock + threadIdx.x;
-  const int mu = threadIdx.y;
-  if (s >= g.V) return;
-  int c[4], par;
-  cb_coords(g, s, c, par);
-  const M3<R> a = staple_sum(U, g, c, s, mu);
-  const M3<R> ul = U.load(mu, s);
+template <int MU, typename R, int NC, int MODE>
+__device__ __forceinline__ void force_link(const Gauge<R, NC>& U, const Mom<R>& P, const Mom<R>& F,
+                                           const Mom<R>& FF, const Gauge<R, NC>& Ubase,
+                                           const Gauge<R, NC>& Uout, const Geom& g, const int c[4], int s,
+                                           R beta6, R ckick, R cdrift, R cdisp, int reunit) {
+  const M3<R> a = staple_sum<MU>(U, g, c, s);
+  const M3<R> ul = U.load(MU, s);
   const M3<R> omega = mul(ul, a);
   R f[8];
   im_tr_gellmann(omega, f);
@@ -71,26 +82,26 @@ __global__ void __launch_bounds__(256) gauge_force_kernel(Gauge<R, NC> U, Mom<R>
   for (int k = 0; k < 8; ++k) f[k] *= beta6;
   if (FF.p != nullptr) {
     R ff[8];
-    FF.load(mu, s, ff);
+    FF.load(MU, s, ff);
 #pragma unroll
     for (int k = 0; k < 8; ++k) f[k] += ff[k];
   }
   if (MODE == FM_STORE) {
-    F.store(mu, s, f);
+    F.store(MU, s, f);
   } else if (MODE == FM_KICK || MODE == FM_KICK_DRIFT) {
     R p[8];
-    P.load(mu, s, p);
+    P.load(MU, s, p);
 #pragma unroll
     for (int k = 0; k < 8; ++k) p[k] = fma(-ckick, f[k], p[k]);
-    P.store(mu, s, p);
+    P.store(MU, s, p);
     if (MODE == FM_KICK_DRIFT) {
 #pragma unroll
       for (int k = 0; k < 8; ++k) p[k] *= cdrift;
       const M3<R> e = expi_herm(alg_to_mat(p));
-      const M3<R> ub = (Ubase.p == U.p) ? ul : Ubase.load(mu, s);
+      const M3<R> ub = (Ubase.p == U.p) ? ul : Ubase.load(MU, s);
       M3<R> un = mul(e, ub);
       if (reunit) reunitarize(un);
-      Uout.store(mu, s, un);
+      Uout.store(MU, s, un);
     }
   } else {  // FM_DISPLACE
 #pragma unroll
@@ -98,7 +109,24 @@ __global__ void __launch_bounds__(256) gauge_force_kernel(Gauge<R, NC> U, Mom<R>
     const M3<R> e = expi_herm(alg_to_mat(f));
     M3<R> un = mul(e, ul);
     if (reunit) reunitarize(un);
-    Uout.store(mu, s, un);
+    Uout.store(MU, s, un);
+  }
+}
+
+template <typename R, int NC, int MODE>
+__global__ void __launch_bounds__(256, FG_FORCE_MIN_BLOCKS) gauge_force_kernel(Gauge<R, NC> U, Mom<R> P, Mom<R> F,
+                                                          Mom<R> FF, Gauge<R, NC> Ubase,
+                                                          Gauge<R, NC> Uout, Geom g, R beta6,
+                                                          R ckick, R cdrift, R cdisp, int reunit) {
+  const int s = blockIdx.x * kSitesPerBlock + threadIdx.x;
+  if (s >= g.V) return;
+  int c[4], par;
+  cb_coords(g, s, c, par);
+  switch (threadIdx.y) {
+    case 0: force_link<0, R, NC, MODE>(U, P, F, FF, Ubase, Uout, g, c, s, beta6, ckick, cdrift, cdisp, reunit); break;
+    case 1: force_link<1, R, NC, MODE>(U, P, F, FF, Ubase, Uout, g, c, s, beta6, ckick, cdrift, cdisp, reunit); break;
+    case 2: force_link<2, R, NC, MODE>(U, P, F, FF, Ubase, Uout, g, c, s, beta6, ckick, cdrift, cdisp, reunit); break;
+    default: force_link<3, R, NC, MODE>(U, P, F, FF, Ubase, Uout, g, c, s, beta6, ckick, cdrift, cdisp, reunit); break;
   }
 }
 
@@ -162,10 +190,10 @@ __global__ void __launch_bounds__(kEnergyThreads) energy_kernel(Gauge<R, NC> U, 
       t *= 0.5;
     }
     double sg = 0.0;
-#pragma unroll 1
+#pragma unroll
     for (int mu = 0; mu < 4; ++mu) {
       const M3<R> umu = U.load(mu, s);
-#pragma unroll 1
+#pragma unroll
       for (int nu = mu + 1; nu < 4; ++nu) {
         const M3<R> a = mul(umu, U.load(nu, cb_neighbor(g, c, mu, +1)));
         const M3<R> b = mul(U.load(nu, s), U.load(mu, cb_neighbor(g, c, nu, +1)));
@@ -204,16 +232,18 @@ __global__ void __launch_bounds__(1024) reduce_kernel(const double* __restrict__
   }
 }
 
-// Box-Muller on two 32-bit uniforms: u1 in (0, 1], u2 in [0, 1).
+// Box-Muller on two 32-bit uniforms, u1 in (0, 1], u2 in [0, 1), evaluated
+// in the precision of the momenta (GB300's FP64 unit is slow, and FP32
+// momenta cannot hold more than an FP32 draw).
 template <typename R>
 __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, R& z0, R& z1) {
-  const double u1 = ((double)a + 1.0) * 2.3283064365386963e-10;
-  const double u2 = (double)b * 2.3283064365386963e-10;
-  const double r = sqrt(-2.0 * log(u1));
-  double sn, cs;
-  sincospi(2.0 * u2, &sn, &cs);
-  z0 = R(r * cs);
-  z1 = R(r * sn);
+  const R u1 = (R(a) + R(1)) * R(2.3283064365386963e-10);
+  const R u2 = R(b) * R(2.3283064365386963e-10);
+  const R r = sqrt(R(-2) * log(u1));
+  R sn, cs;
+  sincospi(R(2) * u2, &sn, &cs);
+  z0 = r * cs;
+  z1 = r * sn;
 }
 
 template <typename R>
@@ -310,14 +340,14 @@ __global__ void mom_to_canon_kernel(Mom<R> P, double* __restrict__ canon, Geom g
 template <typename R, int NC>
 static Gauge<R, NC> gauge_of(const void* p, int V) {
   Gauge<R, NC> u;
-  u.p = (typename Vec2<R>::T*)p;
+  u.p = const_cast<void*>(p);
   u.V = V;
   return u;
 }
 template <typename R>
 static Mom<R> mom_of(const void* p, int V) {
   Mom<R> m;
-  m.p = (typename Vec2<R>::T*)p;
+  m.p = const_cast<void*>(p);
   m.V = V;
   return m;
 }

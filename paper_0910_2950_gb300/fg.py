@@ -16,7 +16,8 @@ import os
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libfg_lattice.so")
+# FG_LATTICE_LIB selects another build of the library (e.g. a tuning variant).
+LIB_PATH = os.environ.get("FG_LATTICE_LIB", os.path.join(_PKG, "libfg_lattice.so"))
 
 FG_OK, FG_EINVAL, FG_ENOMEM, FG_ECUDA, FG_ENOCONV, FG_ETIMEOUT, FG_ESTATE = range(7)
 STATUS_NAMES = {0: "FG_OK", 1: "FG_EINVAL", 2: "FG_ENOMEM", 3: "FG_ECUDA", 4: "FG_ENOCONV",
