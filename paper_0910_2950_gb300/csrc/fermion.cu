@@ -251,8 +251,8 @@ __global__ void __launch_bounds__(256) fermion_force_kernel(
     Gauge<RL, NC> U, const typename Vec2<RS>::T* __restrict__ Xe, const typename Vec2<RS>::T* __restrict__ Xo,
     const typename Vec2<RS>::T* __restrict__ Ye, const typename Vec2<RS>::T* __restrict__ Yo,
     Mom<RL> FF, Geom g, RL kappa2, int accumulate) {
-  const int s = blockIdx.x * 64 + threadIdx.x;
-  if (s >= g.V) return;
+  int s;
+  if (!link_site(g, s)) return;
   int c[4], par;
   cb_coords(g, s, c, par);
   switch (threadIdx.y) {
@@ -530,7 +530,7 @@ cudaError_t launch_fermion_force(const GeomH& gh, const void* U, const void* Xe,
   Mom<RL> f;
   f.p = FF;
   f.V = gh.V;
-  fermion_force_kernel<RL, NC, RS><<<(gh.V + 63) / 64, dim3(64, 4), 0, st>>>(
+  fermion_force_kernel<RL, NC, RS><<<(gh.Vh + 31) / 32, dim3(64, 4), 0, st>>>(
       u, cv2<RS>(Xe), cv2<RS>(Xo), cv2<RS>(Ye), cv2<RS>(Yo), f, to_devg(gh), RL(kappa2), accumulate);
   return cudaGetLastError();
 }

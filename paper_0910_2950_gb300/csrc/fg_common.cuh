@@ -367,6 +367,27 @@ __device__ __forceinline__ int cb_neighbor2(const Geom& g, const int c[4], int m
   return cb_index(g, n);
 }
 
+// Site of a link thread: a block of (64, 4) threads covers half-site indices
+// [32 b, 32 b + 32) in both parities (warp 0 even, warp 1 odd) and all four
+// directions, so the +-x neighbours of its sites are its own sites and both
+// parity halves of a field are swept together (L1 and L2 reuse).  Launch
+// with (V/2 + 31) / 32 blocks.
+__device__ __forceinline__ bool link_site(const Geom& g, int& s) {
+  const int i = blockIdx.x * 32 + (threadIdx.x & 31);
+  if (i >= g.Vh) return false;
+  s = (threadIdx.x >> 5) * g.Vh + i;
+  return true;
+}
+// The same for one thread per site and blocks of 2 * H threads: half-site
+// indices [H b, H b + H) of both parities.  Launch with (V/2 + H - 1) / H blocks.
+template <int H>
+__device__ __forceinline__ bool pair_site(const Geom& g, int& s) {
+  const int i = blockIdx.x * H + (threadIdx.x % H);
+  if (i >= g.Vh) return false;
+  s = (threadIdx.x / H) * g.Vh + i;
+  return true;
+}
+
 // ---------------------------------------------------------------------------
 // Field access.  Fields are stored "pair-major": complex entries are grouped
 // in pairs, and pair q of every site is contiguous, so that one thread moves

@@ -29,52 +29,55 @@ static Geom to_dev(const GeomH& h) {
 
 constexpr int kSitesPerBlock = 64;
 
+
 // Tuning knobs of the gauge-force kernel: minimum resident blocks of 256
 // threads per SM (register cap) and whether the loop over the three staple
 // directions is unrolled.
 #ifndef FG_FORCE_MIN_BLOCKS
-#define FG_FORCE_MIN_BLOCKS 3
+#define FG_FORCE_MIN_BLOCKS 2
 #endif
 #ifndef FG_FORCE_UNROLL_NU
 #define FG_FORCE_UNROLL_NU 0
 #endif
 
-// Sum of the six staples that close a plaquette with U_MU(x); the direction
-// loop is unrolled so every neighbour index is formed with compile-time mu, nu.
-template <int MU, typename R, int NC>
-__device__ __forceinline__ M3<R> staple_sum(const Gauge<R, NC>& U, const Geom& g, const int c[4], int s) {
+// Sum of the six staples that close a plaquette with U_mu(x).  Neighbour
+// indices are formed with selects, so mu and nu may be run-time values
+// without the coordinate array going to local memory; one copy of the body
+// keeps the kernel small enough for the instruction cache.
+template <typename R, int NC>
+__device__ __forceinline__ M3<R> staple_sum(const Gauge<R, NC>& U, const Geom& g, const int c[4], int s, int mu) {
   M3<R> a;
   zero(a);
-  const int s_pmu = cb_neighbor(g, c, MU, +1);
+  const int s_pmu = cb_neighbor_rt(g, c, mu, +1);
 #if FG_FORCE_UNROLL_NU
 #pragma unroll
 #else
 #pragma unroll 1
 #endif
   for (int k = 1; k < 4; ++k) {
-    const int nu = (MU + k) & 3;
+    const int nu = (mu + k) & 3;
     {
       // upper: U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag
-      const M3<R> t = mul_nd(U.load(nu, s_pmu), U.load(MU, cb_neighbor_rt(g, c, nu, +1)));
+      const M3<R> t = mul_nd(U.load(nu, s_pmu), U.load(mu, cb_neighbor_rt(g, c, nu, +1)));
       mac_nd(a, t, U.load(nu, s));
     }
     {
       // lower: U_nu(x+mu-nu)^dag U_mu(x-nu)^dag U_nu(x-nu) = (U_mu(x-nu) U_nu(x+mu-nu))^dag U_nu(x-nu)
       const int s_mnu = cb_neighbor_rt(g, c, nu, -1);
-      const M3<R> t = mul(U.load(MU, s_mnu), U.load(nu, cb_neighbor2_rt(g, c, MU, +1, nu, -1)));
+      const M3<R> t = mul(U.load(mu, s_mnu), U.load(nu, cb_neighbor2_rt(g, c, mu, +1, nu, -1)));
       mac_dn(a, t, U.load(nu, s_mnu));
     }
   }
   return a;
 }
 
-template <int MU, typename R, int NC, int MODE>
+template <typename R, int NC, int MODE>
 __device__ __forceinline__ void force_link(const Gauge<R, NC>& U, const Mom<R>& P, const Mom<R>& F,
                                            const Mom<R>& FF, const Gauge<R, NC>& Ubase,
                                            const Gauge<R, NC>& Uout, const Geom& g, const int c[4], int s,
-                                           R beta6, R ckick, R cdrift, R cdisp, int reunit) {
-  const M3<R> a = staple_sum<MU>(U, g, c, s);
-  const M3<R> ul = U.load(MU, s);
+                                           int mu, R beta6, R ckick, R cdrift, R cdisp, int reunit) {
+  const M3<R> a = staple_sum(U, g, c, s, mu);
+  const M3<R> ul = U.load(mu, s);
   const M3<R> omega = mul(ul, a);
   R f[8];
   im_tr_gellmann(omega, f);
@@ -82,26 +85,26 @@ __device__ __forceinline__ void force_link(const Gauge<R, NC>& U, const Mom<R>& 
   for (int k = 0; k < 8; ++k) f[k] *= beta6;
   if (FF.p != nullptr) {
     R ff[8];
-    FF.load(MU, s, ff);
+    FF.load(mu, s, ff);
 #pragma unroll
     for (int k = 0; k < 8; ++k) f[k] += ff[k];
   }
   if (MODE == FM_STORE) {
-    F.store(MU, s, f);
+    F.store(mu, s, f);
   } else if (MODE == FM_KICK || MODE == FM_KICK_DRIFT) {
     R p[8];
-    P.load(MU, s, p);
+    P.load(mu, s, p);
 #pragma unroll
     for (int k = 0; k < 8; ++k) p[k] = fma(-ckick, f[k], p[k]);
-    P.store(MU, s, p);
+    P.store(mu, s, p);
     if (MODE == FM_KICK_DRIFT) {
 #pragma unroll
       for (int k = 0; k < 8; ++k) p[k] *= cdrift;
       const M3<R> e = expi_herm(alg_to_mat(p));
-      const M3<R> ub = (Ubase.p == U.p) ? ul : Ubase.load(MU, s);
+      const M3<R> ub = (Ubase.p == U.p) ? ul : Ubase.load(mu, s);
       M3<R> un = mul(e, ub);
       if (reunit) reunitarize(un);
-      Uout.store(MU, s, un);
+      Uout.store(mu, s, un);
     }
   } else {  // FM_DISPLACE
 #pragma unroll
@@ -109,7 +112,7 @@ __device__ __forceinline__ void force_link(const Gauge<R, NC>& U, const Mom<R>& 
     const M3<R> e = expi_herm(alg_to_mat(f));
     M3<R> un = mul(e, ul);
     if (reunit) reunitarize(un);
-    Uout.store(MU, s, un);
+    Uout.store(mu, s, un);
   }
 }
 
@@ -118,16 +121,11 @@ __global__ void __launch_bounds__(256, FG_FORCE_MIN_BLOCKS) gauge_force_kernel(G
                                                           Mom<R> FF, Gauge<R, NC> Ubase,
                                                           Gauge<R, NC> Uout, Geom g, R beta6,
                                                           R ckick, R cdrift, R cdisp, int reunit) {
-  const int s = blockIdx.x * kSitesPerBlock + threadIdx.x;
-  if (s >= g.V) return;
+  int s;
+  if (!link_site(g, s)) return;
   int c[4], par;
   cb_coords(g, s, c, par);
-  switch (threadIdx.y) {
-    case 0: force_link<0, R, NC, MODE>(U, P, F, FF, Ubase, Uout, g, c, s, beta6, ckick, cdrift, cdisp, reunit); break;
-    case 1: force_link<1, R, NC, MODE>(U, P, F, FF, Ubase, Uout, g, c, s, beta6, ckick, cdrift, cdisp, reunit); break;
-    case 2: force_link<2, R, NC, MODE>(U, P, F, FF, Ubase, Uout, g, c, s, beta6, ckick, cdrift, cdisp, reunit); break;
-    default: force_link<3, R, NC, MODE>(U, P, F, FF, Ubase, Uout, g, c, s, beta6, ckick, cdrift, cdisp, reunit); break;
-  }
+  force_link<R, NC, MODE>(U, P, F, FF, Ubase, Uout, g, c, s, (int)threadIdx.y, beta6, ckick, cdrift, cdisp, reunit);
 }
 
 template <typename R, int NC>
@@ -173,9 +171,9 @@ __global__ void __launch_bounds__(kEnergyThreads) energy_kernel(Gauge<R, NC> U, 
                                                                 double beta, int mode,
                                                                 double* __restrict__ h0,
                                                                 double* __restrict__ partial) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  int s;
   double v[3] = {0.0, 0.0, 0.0};  // S_G, T, dh
-  if (s < g.V) {
+  if (pair_site<kEnergyThreads / 2>(g, s)) {
     int c[4], par;
     cb_coords(g, s, c, par);
     double t = 0.0;
@@ -353,6 +351,7 @@ static Mom<R> mom_of(const void* p, int V) {
 }
 
 static inline dim3 link_grid(int V) { return dim3((V + kSitesPerBlock - 1) / kSitesPerBlock); }
+static inline dim3 pair_grid(int V) { return dim3((V / 2 + 31) / 32); }
 static inline dim3 link_block() { return dim3(kSitesPerBlock, 4); }
 
 template <typename R, int NC>
@@ -368,19 +367,19 @@ cudaError_t launch_gauge_force(const GeomH& gh, int mode, const ForceArgs& a, cu
   const R b6 = R(a.beta / 6.0);
   switch (mode) {
     case FM_STORE:
-      gauge_force_kernel<R, NC, FM_STORE><<<link_grid(V), link_block(), 0, st>>>(
+      gauge_force_kernel<R, NC, FM_STORE><<<pair_grid(V), link_block(), 0, st>>>(
           U, P, F, FF, Ub, Uo, g, b6, R(a.ckick), R(a.cdrift), R(a.cdisp), a.reunit);
       break;
     case FM_KICK:
-      gauge_force_kernel<R, NC, FM_KICK><<<link_grid(V), link_block(), 0, st>>>(
+      gauge_force_kernel<R, NC, FM_KICK><<<pair_grid(V), link_block(), 0, st>>>(
           U, P, F, FF, Ub, Uo, g, b6, R(a.ckick), R(a.cdrift), R(a.cdisp), a.reunit);
       break;
     case FM_KICK_DRIFT:
-      gauge_force_kernel<R, NC, FM_KICK_DRIFT><<<link_grid(V), link_block(), 0, st>>>(
+      gauge_force_kernel<R, NC, FM_KICK_DRIFT><<<pair_grid(V), link_block(), 0, st>>>(
           U, P, F, FF, Ub, Uo, g, b6, R(a.ckick), R(a.cdrift), R(a.cdisp), a.reunit);
       break;
     case FM_DISPLACE:
-      gauge_force_kernel<R, NC, FM_DISPLACE><<<link_grid(V), link_block(), 0, st>>>(
+      gauge_force_kernel<R, NC, FM_DISPLACE><<<pair_grid(V), link_block(), 0, st>>>(
           U, P, F, FF, Ub, Uo, g, b6, R(a.ckick), R(a.cdrift), R(a.cdisp), a.reunit);
       break;
     default:
@@ -412,7 +411,7 @@ cudaError_t launch_reunitarize(const GeomH& gh, void* U, cudaStream_t st) {
 template <typename R, int NC>
 cudaError_t launch_energy(const GeomH& gh, const void* U, const void* P, double beta, int mode,
                           double* h0, double* partial, int* nblocks, cudaStream_t st) {
-  const int nb = (gh.V + kEnergyThreads - 1) / kEnergyThreads;
+  const int nb = (gh.Vh + kEnergyThreads / 2 - 1) / (kEnergyThreads / 2);
   *nblocks = nb;
   energy_kernel<R, NC><<<nb, kEnergyThreads, 0, st>>>(gauge_of<R, NC>(U, gh.V), mom_of<R>(P, gh.V),
                                                       to_dev(gh), beta, mode, h0, partial);
