@@ -5,8 +5,12 @@ a 32^4 lattice at beta = 6.0, force-gradient PQPQP integrator of Table 1 with
 dt = 0.25 and tau = 1 (4 MD steps, 13 force evaluations, 8 link drifts),
 FP32 links, momenta and forces with FP64 dH sums, 18-real links.  The chain
 starts from a seeded hot start thermalised by 10 force-gradient trajectories
-(dt = 1/8, always accepted); W warm-up trajectories with Metropolis follow,
-then K timed trajectories.
+(dt = 1/8, always accepted) and 150 untimed Metropolis FG trajectories at
+dt = 1/8; W warm-up trajectories follow, then K timed trajectories.
+
+A second, smaller measurement covers the Nf=2 Wilson-fermion path (16^3 x 32,
+beta = 5.6, kappa = 0.158, pure-gauge thermalised start): mixed-precision CG
+solves to 1e-10 with the even-odd Dslash timed per launch against HBM.
 
 Output: one JSON line (rank 0).  `value` is trajectories per second over all
 ranks with the fields resident in HBM; `e2e` is the same metric through the
@@ -40,6 +44,7 @@ DT = 0.25
 TAU = 1.0
 L_BENCH = 32
 THERM_TRAJ = 10
+EQUIL_TRAJ = 150
 METRIC = "FG-HMC trajectories/s at fixed acceptance"
 UNIT = "trajectories/s"
 # FP32 peak of the FMA pipes: 152 SMs x 128 lanes x 2 flop x 2070 MHz (maximum SM clock).
@@ -70,7 +75,17 @@ def parse():
     ap.add_argument("--link-reals", type=int, default=18)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fermion", action="store_true")
     return ap.parse_args()
+
+
+def hbm_peak():
+    """Measured copy bandwidth of the GB300s (GB/s), else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
 
 
 def dist_info():
@@ -132,7 +147,8 @@ def workload_config(args):
     return {
         "workload": f"pure-gauge SU(3) Wilson {L}^4, beta={BETA}, {args.integrator} integrator "
                     f"tau={TAU} dt={args.dt}, {args.precision} links/forces, FP64 dH sums, "
-                    f"{args.link_reals}-real links, hot start + {THERM_TRAJ} thermalising trajectories",
+                    f"{args.link_reals}-real links, hot start + {THERM_TRAJ} thermalising trajectories "
+                    f"(dt=1/8, always accepted) + {EQUIL_TRAJ} untimed Metropolis FG trajectories at dt=1/8",
         "lattice": [L] * 4, "beta": BETA, "integrator": args.integrator, "dt": args.dt, "tau": TAU,
         "precision": args.precision, "link_reals": args.link_reals,
         "l2": f"inputs larger than L2: gauge field "
@@ -156,7 +172,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -196,6 +212,64 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- our arm
+# Dslash algorithmic bytes per output site (FP32, 18-real links): 8 neighbour
+# spinors (96 B) + 8 links (72 B) read, one spinor (96 B) written.
+DSLASH_BYTES_FP32_18 = 8 * 96 + 8 * 72 + 96
+DSLASH_FLOP = 1320
+
+
+def fermion_measurement(fg, stream, rank, hbm_peak):
+    """CG on the 16^3 x 32 Nf=2 workload; returns a dict for the JSON line."""
+    dims = (16, 16, 16, 32)
+    gauge = fg.Lattice(dims, 5.6, precision="fp32", seed=300 + rank, stream=stream)
+    gauge.set_gauge(inputs.hot_start(dims, 3 + rank))
+    for _ in range(10):
+        gauge.trajectory("fg", 0.125, TAU, refresh=True, u_accept=0.0)
+    for _ in range(40):
+        gauge.trajectory("fg", 0.25, TAU, refresh=True, u_accept=-1.0)
+    u = gauge.get_gauge()
+    plaq = gauge.plaquette()
+    gauge.close()
+    lat = fg.Lattice(dims, 5.6, kappa=0.158, precision="fp32", cg_tol=1e-10, seed=400 + rank,
+                     stream=stream)
+    lat.set_gauge(u)
+    vh = inputs.volume(dims) // 2
+    b = inputs.gaussian_spinor_even(dims, 5 + rank)
+    lat.cg_solve(b)                        # warm-up
+    solves, iters, ru, res = 2, 0, 0, 0.0
+    t0 = time.perf_counter()
+    for k in range(solves):
+        _, info = lat.cg_solve(inputs.gaussian_spinor_even(dims, 6 + k + rank))
+        iters += info["iterations"]
+        ru += info["reliable_updates"]
+        res = max(res, info["true_residual"])
+    wall = time.perf_counter() - t0
+    # a second pass with per-launch CUDA-event timing for the kernel rooflines
+    lat.timing(True)
+    lat.timing_reset()
+    lat.timing(True)
+    lat.cg_solve(inputs.gaussian_spinor_even(dims, 9 + rank))
+    ds_ms, ds_n = lat.kernel_time("dslash")
+    blas_ms, blas_n = lat.kernel_time("cg_blas")
+    lat.timing(False)
+    lat.close()
+    avg = ds_ms / 1000.0 / max(ds_n, 1)
+    achieved = DSLASH_BYTES_FP32_18 * vh / avg / 1e9
+    return {
+        "workload": "Nf=2 Wilson 16^3x32, beta=5.6, kappa=0.158, even-odd CG on Mhat^dag Mhat to 1e-10 "
+                    "(FP32 inner, FP64 reliable updates), gauge field: hot start + 50 FG trajectories",
+        "plaquette": plaq, "cg_iterations_per_solve": iters / solves, "reliable_updates_per_solve": ru / solves,
+        "true_residual_max": res, "ms_per_solve": 1000 * wall / solves,
+        "us_per_cg_iteration": 1e6 * wall / max(iters, 1),
+        "dslash_roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                            "frac": achieved / hbm_peak, "traffic": None,
+                            "bytes_per_site": DSLASH_BYTES_FP32_18, "sites_per_launch": vh,
+                            "avg_launch_us": avg * 1e6, "launches": ds_n,
+                            "gflops": DSLASH_FLOP * vh / avg / 1e9},
+        "cg_blas_ms_share": blas_ms / max(ds_ms + blas_ms, 1e-9),
+    }
+
+
 def run_ours(args):
     rank, world, local = dist_info()
     import torch
@@ -227,6 +301,9 @@ def run_ours(args):
     del u0
     for _ in range(THERM_TRAJ):
         lat.trajectory("fg", 0.125, TAU, refresh=True, u_accept=0.0)
+    # equilibrate with Metropolis at dt = 1/8 (untimed)
+    for _ in range(EQUIL_TRAJ):
+        lat.trajectory("fg", 0.125, TAU, refresh=True, u_accept=-1.0)
     for _ in range(args.warmup):
         lat.trajectory(args.integrator, args.dt, TAU, refresh=True, u_accept=-1.0)
 
@@ -321,6 +398,10 @@ def run_ours(args):
                "note": "per trajectory: gauge field and momenta uploaded from pinned host memory "
                        "(canonical FP64), trajectory run, gauge field and result read back"}
 
+    ferm = None
+    if not args.no_fermion:
+        ferm = fermion_measurement(fg, stream.cuda_stream, rank, hbm_peak())
+
     if rank == 0:
         cfg = workload_config(args)
         cfg.update({"acceptance": acc, "mean_exp_minus_dH": emdh,
@@ -331,7 +412,7 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
-                "config": cfg, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "config": cfg, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fermion": ferm,
                 "gpu_launches": launches, "clocks": clk}
         print(json.dumps(line), flush=True)
     lat.close()

@@ -47,9 +47,9 @@ class Backend final : public IBackend {
     const size_t V = (size_t)g_.V;
     const size_t mom_bytes = (size_t)4 * 4 * V * sizeof(C2);
     fg_status s;
-    if ((s = alloc(&U_, gauge_bytes())) != FG_OK) return s;
-    if ((s = alloc(&Ualt_, gauge_bytes())) != FG_OK) return s;
-    if ((s = alloc(&Ubak_, gauge_bytes())) != FG_OK) return s;
+    for (int b = 0; b < 3; ++b)
+      if ((s = alloc(&buf_[b], gauge_bytes())) != FG_OK) return s;
+    U_ = buf_[0];
     if ((s = alloc(&P_, mom_bytes)) != FG_OK) return s;
     if ((s = alloc(&F_, mom_bytes)) != FG_OK) return s;
     if ((s = alloc((void**)&h0_, V * sizeof(double))) != FG_OK) return s;
@@ -178,7 +178,7 @@ class Backend final : public IBackend {
   // ---------------------------------------------------------------- MD
   fg_status md_step(int integ, double dt) override {
     std::vector<Op> ops = trajectory_ops(integ, h_->prm.alpha, 1, false);
-    fg_status s = execute(ops, dt);
+    fg_status s = execute(ops, dt, nullptr);
     if (s != FG_OK) return s;
     sf0_valid_ = false;
     return sync();
@@ -203,10 +203,11 @@ class Backend final : public IBackend {
     }
     // H at the start: per-site energies kept for the site-by-site dH sum
     if ((s = energy(0, P_, 0)) != FG_OK) return s;
-    if (cudaMemcpyAsync(Ubak_, U_, gauge_bytes(), cudaMemcpyDeviceToDevice, st_) != cudaSuccess)
-      return cuda_fail("backup copy");
+    // The start field is never written during the trajectory (see execute),
+    // so a rejection only has to point back at it.
+    void* const start = U_;
     std::vector<Op> ops = trajectory_ops(integ, h_->prm.alpha, nsteps, true);
-    if ((s = execute(ops, dt)) != FG_OK) return s;
+    if ((s = execute(ops, dt, start)) != FG_OK) return s;
     if ((s = energy(1, P_, 3)) != FG_OK) return s;
     if ((s = fetch(6)) != FG_OK) return s;
     double o[6];
@@ -229,9 +230,7 @@ class Backend final : public IBackend {
     const double u = (u_accept < 0.0) ? host_uniform() : u_accept;
     r->accepted = std::isfinite(r->dH) && (r->dH <= 0.0 || u < std::exp(-r->dH));
     if (!r->accepted) {
-      if (cudaMemcpyAsync(U_, Ubak_, gauge_bytes(), cudaMemcpyDeviceToDevice, st_) != cudaSuccess)
-        return cuda_fail("restore copy");
-      if ((s = sync()) != FG_OK) return s;
+      U_ = start;
       sf0_ = sf0;             // phi unchanged and the links are back: S_F is S_F0 again
       sf0_valid_ = ferm_;
     } else {
@@ -253,9 +252,8 @@ class Backend final : public IBackend {
   cudaStream_t st_;
   bool ferm_;
   std::vector<void*> allocs_;
+  void* buf_[3] = {nullptr, nullptr, nullptr};   // link buffers; U_ is one of them
   void* U_ = nullptr;
-  void* Ualt_ = nullptr;
-  void* Ubak_ = nullptr;
   void* P_ = nullptr;
   void* F_ = nullptr;
   double* h0_ = nullptr;
@@ -372,8 +370,19 @@ class Backend final : public IBackend {
     return run(KC_GAUGE_FORCE, [&] { return launch_gauge_force<R, NC>(g_, mode, a, st_); });
   }
 
-  // Runs a merged op list with fused kernels (see the file header of fg_lattice.cu).
-  fg_status execute(const std::vector<Op>& ops, double dt) {
+  // One of the three link buffers that is neither the current field nor the
+  // protected one.
+  void* free_buffer(const void* protect) const { return buffer_not(U_, protect); }
+  void* buffer_not(const void* a, const void* b) const {
+    for (void* c : buf_)
+      if (c != a && c != b) return c;
+    return nullptr;
+  }
+
+  // Runs a merged op list with fused kernels (see the file header of
+  // fg_lattice.cu).  The links rotate through three buffers; the buffer
+  // `protect` (the trajectory's start field, or null) is never written.
+  fg_status execute(const std::vector<Op>& ops, double dt, const void* protect) {
     fg_status s;
     const size_t n = ops.size();
     for (size_t i = 0; i < n;) {
@@ -383,34 +392,43 @@ class Backend final : public IBackend {
         ForceArgs a = force_args(U_);
         a.ckick = o.c * dt;
         if (next_q) {
+          void* out = free_buffer(protect);
           a.cdrift = ops[i + 1].c * dt;
           a.Ubase = U_;
-          a.Uout = Ualt_;
+          a.Uout = out;
           if ((s = force_launch(FM_KICK_DRIFT, a)) != FG_OK) return s;
-          std::swap(U_, Ualt_);
+          U_ = out;
           i += 2;
         } else {
           if ((s = force_launch(FM_KICK, a)) != FG_OK) return s;
           i += 1;
         }
       } else if (o.kind == 'Q') {
+        void* out = (U_ == protect) ? free_buffer(protect) : U_;
+        const void* in = U_;
         s = run(KC_DRIFT, [&] {
-          return launch_drift<R, NC>(g_, U_, P_, U_, o.c * dt, h_->prm.reunitarize, st_);
+          return launch_drift<R, NC>(g_, in, P_, out, o.c * dt, h_->prm.reunitarize, st_);
         });
         if (s != FG_OK) return s;
+        U_ = out;
         i += 1;
       } else {  // 'G': displace along the force, then kick with the force there
+        void* disp = free_buffer(protect);
         ForceArgs d = force_args(U_);
         d.cdisp = o.d * dt * dt;
-        d.Uout = Ualt_;
+        d.Uout = disp;
         if ((s = force_launch(FM_DISPLACE, d)) != FG_OK) return s;
-        ForceArgs a = force_args(Ualt_);
+        ForceArgs a = force_args(disp);
         a.ckick = o.c * dt;
         if (next_q) {
+          // the drift after the FG kick moves the current links; write it
+          // in place unless they are the protected start field
+          void* out = (U_ == protect) ? buffer_not(protect, disp) : U_;
           a.cdrift = ops[i + 1].c * dt;
           a.Ubase = U_;
-          a.Uout = U_;
+          a.Uout = out;
           s = force_launch(FM_KICK_DRIFT, a);
+          U_ = out;
           i += 2;
         } else {
           s = force_launch(FM_KICK, a);

@@ -87,12 +87,21 @@ int count_forces(const std::vector<Op>& ops) {
 
 // ---------------------------------------------------------------------------
 // Kernel timing with CUDA events.
+static cudaEvent_t pool_event(Timer& t) {
+  if (t.used == t.pool.size()) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    t.pool.push_back(e);
+  }
+  return t.pool[t.used++];
+}
 void Timer::begin(int cls, cudaStream_t st) {
   if (!on) return;
   Rec r;
   r.cls = cls;
-  cudaEventCreate(&r.a);
-  cudaEventCreate(&r.b);
+  r.a = pool_event(*this);
+  r.b = pool_event(*this);
+  if (!r.a || !r.b) return;
   cudaEventRecord(r.a, st);
   recs.push_back(r);
 }
@@ -101,11 +110,11 @@ void Timer::end(cudaStream_t st) {
   cudaEventRecord(recs.back().b, st);
 }
 void Timer::reset() {
-  for (Rec& r : recs) {
-    cudaEventDestroy(r.a);
-    cudaEventDestroy(r.b);
-  }
   recs.clear();
+  used = 0;
+}
+Timer::~Timer() {
+  for (cudaEvent_t e : pool) cudaEventDestroy(e);
 }
 bool Timer::total(int cls, double* ms, long long* n) {
   double t = 0;

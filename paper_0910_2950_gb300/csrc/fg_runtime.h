@@ -32,6 +32,9 @@ enum KernelClass {
 constexpr int kNumKernelClasses = 9;
 extern const char* kKernelClasses[];
 
+// Per-launch CUDA-event timing.  Events come from a pool that grows on
+// demand and is reused after reset(), so timing adds two event records per
+// launch and no event creation in steady state.
 struct Timer {
   struct Rec {
     int cls;
@@ -39,11 +42,13 @@ struct Timer {
   };
   bool on = false;
   std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
   void begin(int cls, cudaStream_t st);
   void end(cudaStream_t st);
   void reset();
   bool total(int cls, double* ms, long long* n);
-  ~Timer() { reset(); }
+  ~Timer();
 };
 
 struct IBackend {
