@@ -95,6 +95,27 @@ def dist_info():
     return rank, world, local
 
 
+def reduce_max(x: float, world: int, device) -> float:
+    """Maximum of x over all ranks (the slowest rank's time)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, world: int, max_seconds: float) -> float:
+    """Units processed by all ranks divided by the slowest rank's time."""
+    return world * units_per_rank / max_seconds
+
+
+def rank_seeds(rank: int) -> dict:
+    """Independent chains per rank: distinct start fields and RNG streams."""
+    return {"hot_start": 1 + rank, "device_rng": 1000 + rank, "e2e_momenta": 77 + rank}
+
+
 # ----------------------------------------------------------------------------- oracle legs
 def oracle_trajectory_rate(sample_l: int, target_l: int, integrator: str, dt: float, seed: int):
     """Time the FP64 CPU oracle on one trajectory of a sample_l^4 lattice and
@@ -294,9 +315,10 @@ def run_ours(args):
     L = args.lattice
     dims = (L,) * 4
     stream = torch.cuda.Stream()
+    seeds = rank_seeds(rank)
     lat = fg.Lattice(dims, BETA, precision=args.precision, link_reals=args.link_reals,
-                     seed=1000 + rank, stream=stream.cuda_stream)
-    u0 = inputs.hot_start(dims, 1 + rank)
+                     seed=seeds["device_rng"], stream=stream.cuda_stream)
+    u0 = inputs.hot_start(dims, seeds["hot_start"])
     lat.set_gauge(u0)
     del u0
     for _ in range(THERM_TRAJ):
@@ -331,11 +353,8 @@ def run_ours(args):
     force_ms, force_n = lat.kernel_time("gauge_force")
     lat.timing(False)
 
-    t = torch.tensor([elapsed_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    max_ms = float(t.item())
-    value = world * args.steps / (max_ms / 1000.0)
+    max_ms = reduce_max(elapsed_ms, world, "cuda")
+    value = whole_job_rate(args.steps, world, max_ms / 1000.0)
 
     acc = float(np.mean([r["accepted"] for r in results]))
     emdh = float(np.mean([np.exp(-r["dH"]) for r in results]))
@@ -375,7 +394,7 @@ def run_ours(args):
         hu = torch.empty(ncanon_u, dtype=torch.float64, pin_memory=True).numpy()
         hp = torch.empty(ncanon_p, dtype=torch.float64, pin_memory=True).numpy()
         hu[:] = lat.get_gauge().view(np.float64).ravel()
-        rng = inputs.make_rng(77 + rank)
+        rng = inputs.make_rng(seeds["e2e_momenta"])
         hp[:] = rng.standard_normal(ncanon_p)
         lat.set_gauge(hu)
         torch.cuda.synchronize()
@@ -388,11 +407,8 @@ def run_ours(args):
             r = lat.trajectory(args.integrator, args.dt, TAU, refresh=False, u_accept=-1.0)
             lat.get_gauge(out=hu)
         torch.cuda.synchronize()
-        e2e_s = time.perf_counter() - t0
-        te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * args.steps / float(te.item()), "unit": UNIT,
+        e2e_s = reduce_max(time.perf_counter() - t0, world, "cuda")
+        e2e = {"value": whole_job_rate(args.steps, world, e2e_s), "unit": UNIT,
                "h2d_bytes_per_step": (ncanon_u + ncanon_p) * 8,
                "d2h_bytes_per_step": ncanon_u * 8 + 14 * 8,
                "note": "per trajectory: gauge field and momenta uploaded from pinned host memory "

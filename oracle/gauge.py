@@ -81,6 +81,33 @@ def gauge_force(u: np.ndarray, beta: float) -> np.ndarray:
     return f
 
 
+def link_force(u: np.ndarray, site, mu: int, beta: float) -> np.ndarray:
+    """F^a for the single link U_mu(x) at site = (t, z, y, x): the same staple
+    definition as ``gauge_force``, evaluated with explicit neighbour indices
+    so that it can be sampled on lattices too large for whole-field numpy."""
+    lt, lz, ly, lx = u.shape[:4]
+    ext = (lx, ly, lz, lt)
+
+    def at(c, d):                       # c = (x, y, z, t), link U_d(c)
+        return u[c[3] % ext[3], c[2] % ext[2], c[1] % ext[1], c[0] % ext[0], d]
+
+    def step(c, d, k):
+        c = list(c)
+        c[d] += k
+        return c
+
+    t, z, y, x = site
+    c = [x, y, z, t]
+    a = np.zeros((3, 3), dtype=np.complex128)
+    for nu in range(4):
+        if nu == mu:
+            continue
+        a += at(step(c, mu, 1), nu) @ dag(at(step(c, nu, 1), mu)) @ dag(at(c, nu))
+        cm = step(c, nu, -1)
+        a += dag(at(step(cm, mu, 1), nu)) @ dag(at(cm, mu)) @ at(cm, nu)
+    return (beta / 6.0) * im_tr_gellmann(at(c, mu) @ a)
+
+
 def kinetic(p: np.ndarray) -> float:
     """T = (1/2) sum_links sum_a (p^a)^2 = sum_links Tr P^2."""
     return float(0.5 * np.sum(p * p))

@@ -113,3 +113,16 @@ def test_kinetic_term():
     # <T> = (8 / 2) * 4V = 16 V for unit-Gaussian momenta
     v = inputs.volume((4, 4, 4, 4))
     assert abs(gauge.kinetic(p) / (16 * v) - 1) < 5 * np.sqrt(2 / (32 * v))
+
+
+def test_link_force_equals_whole_lattice_force():
+    dims = (4, 6, 2, 4)
+    u = inputs.hot_start(dims, 12)
+    f = gauge.gauge_force(u, BETA)
+    for t in range(4):
+        for z in range(2):
+            for y in range(6):
+                for x in range(4):
+                    for mu in range(4):
+                        assert np.allclose(gauge.link_force(u, (t, z, y, x), mu, BETA), f[t, z, y, x, mu],
+                                           rtol=0, atol=1e-13)
