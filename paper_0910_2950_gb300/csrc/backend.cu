@@ -15,6 +15,13 @@
 
 #include "fg_common.cuh"
 #include "fg_fermion.h"
+
+#ifdef FG_CG_TRACE
+#include <cstdio>
+#define CG_TRACE(...) std::fprintf(stderr, __VA_ARGS__)
+#else
+#define CG_TRACE(...) ((void)0)
+#endif
 #include "fg_kernels.h"
 #include "fg_runtime.h"
 
@@ -24,7 +31,9 @@ namespace fg {
 struct Mapped {
   double bb;
   double true_rr;
-  double pad[6];
+  int dev_iter;     // last completed CG iteration (device numbering)
+  int pad_i;
+  double pad[5];
   double hist[1];   // residual history, one entry per CG iteration (allocated longer)
 };
 
@@ -41,6 +50,7 @@ class Backend final : public IBackend {
     if (mapped_) cudaFreeHost(mapped_);
     for (int i = 0; i < 2; ++i)
       if (ev_[i]) cudaEventDestroy(ev_[i]);
+    for (const CgGraph& c : cg_graphs_) cudaGraphExecDestroy(c.exec);
   }
 
   fg_status init() {
@@ -565,9 +575,32 @@ class Backend final : public IBackend {
     });
   }
 
-  // One CG iteration in the inner precision R (6 launches; all return at once
-  // after convergence through cgd_->done).
-  fg_status cg_iteration(const void* U, int k) {
+  // One CG iteration in the inner precision R: 4 Dslash + 2 vector kernels,
+  // which all return at once after convergence (cgd_->done).  Raw launches,
+  // usable inside stream capture.
+  cudaError_t cg_iteration_raw(const void* U) {
+    const double k2 = h_->prm.kappa * h_->prm.kappa;
+    const int n = nvec();
+    const int* done = &cgd_->done;
+    cudaError_t e;
+    if ((e = launch_dslash<R, NC, R>(g_, to_, p_, nullptr, nullptr, U, 1, 0, 0, 1.0, nullptr, done, st_)) != cudaSuccess)
+      return e;
+    if ((e = launch_dslash<R, NC, R>(g_, te_, to_, p_, nullptr, U, 0, 0, 1, -k2, nullptr, done, st_)) != cudaSuccess)
+      return e;
+    if ((e = launch_dslash<R, NC, R>(g_, to_, te_, nullptr, nullptr, U, 1, 1, 0, 1.0, nullptr, done, st_)) != cudaSuccess)
+      return e;
+    if ((e = launch_dslash<R, NC, R>(g_, ap_, to_, te_, p_, U, 0, 1, 2, -k2, part_pap_, done, st_)) != cudaSuccess)
+      return e;
+    if ((e = launch_cg_axpy<R>(xs_, rs_, p_, ap_, part_pap_, dslash_blocks(g_.Vh), cgd_, part_rr_, n, st_)) !=
+        cudaSuccess)
+      return e;
+    return launch_cg_xpay<R>(p_, rs_, part_rr_, vec_blocks(n), cgd_, mapped_->hist, &mapped_->dev_iter,
+                             h_->prm.cg_maxiter, n, st_);
+  }
+
+  // The same through run(), so that per-kernel timing and launch counting see
+  // each kernel (used when timing is on or a graph is not available).
+  fg_status cg_iteration(const void* U) {
     const double k2 = h_->prm.kappa * h_->prm.kappa;
     const int n = nvec();
     const int* done = &cgd_->done;
@@ -584,19 +617,73 @@ class Backend final : public IBackend {
     if ((s = run(KC_DSLASH, [&] {
            return launch_dslash<R, NC, R>(g_, ap_, to_, te_, p_, U, 0, 1, 2, -k2, part_pap_, done, st_);
          })) != FG_OK) return s;
-    const int npap = dslash_blocks(g_.Vh);
     if ((s = run(KC_CG_BLAS, [&] {
-           return launch_cg_axpy<R>(xs_, rs_, p_, ap_, part_pap_, npap, cgd_, k, part_rr_, n, st_);
+           return launch_cg_axpy<R>(xs_, rs_, p_, ap_, part_pap_, dslash_blocks(g_.Vh), cgd_, part_rr_, n, st_);
          })) != FG_OK) return s;
-    double* hist = mapped_->hist;
     return run(KC_CG_BLAS, [&] {
-      return launch_cg_xpay<R>(p_, rs_, part_rr_, vec_blocks(n), cgd_, k, hist, n, st_);
+      return launch_cg_xpay<R>(p_, rs_, part_rr_, vec_blocks(n), cgd_, mapped_->hist, &mapped_->dev_iter,
+                               h_->prm.cg_maxiter, n, st_);
     });
   }
 
-  // Reliable update after iteration k: x64 += x_s, r64 = b - M x64 in FP64,
-  // r_s = r64, rr = |r64|^2 (also published to the host).
-  fg_status reliable_update(const void* U, const void* b64, int k) {
+  // A CUDA graph of kCgBatch iterations on links U, captured on first use and
+  // cached per link buffer (the links are the only argument that changes
+  // between solves).  Null if capture is not possible on this stream.
+  static constexpr int kCgBatch = 8;
+  struct CgGraph {
+    const void* U;
+    cudaGraphExec_t exec;
+  };
+  std::vector<CgGraph> cg_graphs_;
+  bool cg_graphs_broken_ = false;
+
+  cudaGraphExec_t cg_graph(const void* U) {
+    for (const CgGraph& c : cg_graphs_)
+      if (c.U == U) return c.exec;
+    if (cg_graphs_broken_) return nullptr;
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(st_, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      cg_graphs_broken_ = true;
+      return nullptr;
+    }
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < kCgBatch && e == cudaSuccess; ++i) e = cg_iteration_raw(U);
+    cudaError_t e2 = cudaStreamEndCapture(st_, &graph);
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess && e2 == cudaSuccess && graph != nullptr &&
+        cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
+      cg_graphs_.push_back({U, exec});
+    } else {
+      cudaGetLastError();
+      exec = nullptr;
+      cg_graphs_broken_ = true;
+    }
+    if (graph) cudaGraphDestroy(graph);
+    return exec;
+  }
+
+  // Queue n iterations: one graph launch for a full batch when timing is off,
+  // single launches otherwise.
+  fg_status cg_batch(const void* U, int n) {
+    if (n == kCgBatch && !h_->timer.on) {
+      cudaGraphExec_t g = cg_graph(U);
+      if (g != nullptr) {
+        if (cudaGraphLaunch(g, st_) != cudaSuccess) return cuda_fail("cg graph launch");
+        h_->launches += 6 * kCgBatch;
+        return FG_OK;
+      }
+    }
+    for (int i = 0; i < n; ++i) {
+      fg_status s = cg_iteration(U);
+      if (s != FG_OK) return s;
+    }
+    return FG_OK;
+  }
+
+  // Reliable update after the last queued iteration: x64 += x_s,
+  // r64 = b - M x64 in FP64, r_s = r64, rr = |r64|^2 (also published to the host).
+  fg_status reliable_update(const void* U, const void* b64) {
     const int n = nvec();
     fg_status s;
     if ((s = run(KC_CG_BLAS, [&] { return launch_ru_accumulate<R>(x64_, xs_, n, st_); })) != FG_OK) return s;
@@ -604,7 +691,9 @@ class Backend final : public IBackend {
     if ((s = run(KC_CG_BLAS, [&] { return launch_ru_residual<R>(b64, ax64_, r64_, rs_, part_rr_, n, st_); })) != FG_OK)
       return s;
     double* tr = &mapped_->true_rr;
-    return run(KC_REDUCE, [&] { return launch_ru_publish(part_rr_, vec_blocks(n), cgd_, k, tr, st_); });
+    if ((s = run(KC_REDUCE, [&] { return launch_ru_publish(part_rr_, vec_blocks(n), cgd_, tr, st_); })) != FG_OK)
+      return s;
+    return run(KC_CG_BLAS, [&] { return launch_cg_restart<R>(p_, rs_, cgd_, n, st_); });
   }
 
   // Conjugate gradient on Mhat^dagger Mhat x = b (b FP64 on the device), x0 = 0,
@@ -641,44 +730,78 @@ class Backend final : public IBackend {
     if (bb == 0.0) return FG_OK;
     const double tol2bb = tol * tol * bb;
     double maxrr = bb;
-    int k = 0;
-    int iters = 0;
     const int maxiter = h_->prm.cg_maxiter;
+    int queued = 0;      // iterations queued so far (including ones that return at once)
+    int checked = 0;     // device iterations whose residual the host has read
+    int iters = 0;
+    int pending = -1;    // event slot of the batch queued before the last one
+    mapped_->dev_iter = 0;
     for (;;) {
       bool converged = false;
       while (!converged) {
-        if (k >= maxiter) {
-          cg_iters_ += k;
-          st->iters = k;
-          return h_->fail(FG_ENOCONV, "CG did not converge in " + std::to_string(maxiter) + " iterations");
+        if (queued >= maxiter) {
+          if ((s = sync()) != FG_OK) return s;
+          const int upto = mapped_->dev_iter;
+          for (int j = checked + 1; j <= upto; ++j)
+            if (mapped_->hist[j] <= tol2bb) { converged = true; iters = j; break; }
+          if (!converged) {
+            cg_iters_ += upto;
+            st->iters = upto;
+            return h_->fail(FG_ENOCONV, "CG did not converge in " + std::to_string(maxiter) + " iterations");
+          }
+          break;
         }
-        ++k;
-        if ((s = cg_iteration(U, k)) != FG_OK) return s;
-        if (cudaEventRecord(ev_[k & 1], st_) != cudaSuccess) return cuda_fail("event");
-        if (k >= 2) {
-          if (cudaEventSynchronize(ev_[(k - 1) & 1]) != cudaSuccess) return cuda_fail("event sync");
-          const double rr = mapped_->hist[k - 1];
-          if (!(rr == rr)) return h_->fail(FG_ENOCONV, "CG residual is NaN");
-          if (rr <= tol2bb) {
-            converged = true;
-            iters = k - 1;
-          } else if (mixed && rr < delta2 * maxrr) {
-            if ((s = reliable_update(U, b64, k)) != FG_OK) return s;
-            ++st->nru;
-            maxrr = rr;
+        const int nb = std::min(kCgBatch, maxiter - queued);
+        if ((s = cg_batch(U, nb)) != FG_OK) return s;
+        queued += nb;
+        const int slot = (pending + 1) & 1;
+        if (cudaEventRecord(ev_[slot], st_) != cudaSuccess) return cuda_fail("event");
+        if (pending >= 0) {
+          // wait for the batch before this one; the GPU keeps working on this one
+          if (cudaEventSynchronize(ev_[pending]) != cudaSuccess) return cuda_fail("event sync");
+          const int upto = *(volatile int*)&mapped_->dev_iter;
+          const int first = checked + 1;
+          double first_rr = -1.0, last = -1.0;
+          for (int j = first; j <= upto; ++j) {
+            const double rr = mapped_->hist[j];
+            CG_TRACE("cg it %d rr/bb %.3e (queued %d)\n", j, rr / bb, queued);
+            if (!(rr == rr)) return h_->fail(FG_ENOCONV, "CG residual is NaN");
+            if (first_rr < 0.0) first_rr = rr;
+            last = rr;
+            if (rr <= tol2bb) { converged = true; iters = j; break; }
+          }
+          checked = std::max(checked, upto);
+          if (!converged && mixed && last > 0.0) {
+            // extrapolate the residual to the last queued iteration with the
+            // convergence rate just seen, so the update is not late
+            double predicted = last;
+            if (first_rr > 0.0 && upto > first && last < first_rr) {
+              const double rate = std::pow(last / first_rr, 1.0 / (upto - first));
+              predicted = last * std::pow(rate, queued - upto);
+            }
+            if (predicted < delta2 * maxrr) {
+              CG_TRACE("cg reliable update after queued %d (last %.3e predicted %.3e)\n", queued, last / bb,
+                       predicted / bb);
+              if ((s = reliable_update(U, b64)) != FG_OK) return s;
+              ++st->nru;
+              maxrr = predicted;
+            }
           }
         }
+        pending = slot;
       }
-      if ((s = reliable_update(U, b64, k)) != FG_OK) return s;
+      if ((s = reliable_update(U, b64)) != FG_OK) return s;
       ++st->nru;
       if ((s = sync()) != FG_OK) return s;
       const double trr = mapped_->true_rr;
       st->true_res = std::sqrt(trr / bb);
+      CG_TRACE("cg final check: iters %d true rr/bb %.3e tol2 %.3e\n", iters, trr / bb, tol * tol);
       if (trr <= tol2bb) break;
-      // The FP64 residual is not yet below tol: restart the directions from it.
-      if (cudaMemcpyAsync(p_, rs_, (size_t)n * sizeof(C2), cudaMemcpyDeviceToDevice, st_) != cudaSuccess)
-        return cuda_fail("cg restart");
+      // The FP64 residual is not yet below tol: the reliable update has put
+      // it into r and cleared `done`; continue from there.
       maxrr = trr;
+      checked = mapped_->dev_iter;
+      pending = -1;
     }
     st->iters = iters;
     cg_iters_ += iters;

@@ -288,14 +288,19 @@ __device__ __forceinline__ double block_sum_partials(const double* __restrict__ 
   return r;
 }
 
-// alpha = rr[(k-1)&1] / sum(pAp partials); x += alpha p; r -= alpha Ap; partial |r|^2.
+// Iteration k = iter + 1 (iter was published by the previous iteration's
+// xpay kernel): alpha = rr[(k-1)&1] / sum(pAp partials); x += alpha p;
+// r -= alpha Ap; partial |r|^2.  Block 0 passes k on to xpay through k_axpy.
+// The kernels take no iteration argument, so a batch of iterations can be
+// captured once in a CUDA graph and replayed.
 template <typename R>
 __global__ void __launch_bounds__(kVecThreads) cg_axpy_kernel(
     typename Vec2<R>::T* __restrict__ x, typename Vec2<R>::T* __restrict__ r,
     const typename Vec2<R>::T* __restrict__ p, const typename Vec2<R>::T* __restrict__ ap,
-    const double* __restrict__ pap_part, int npap, CgDev* __restrict__ cgd, int k,
+    const double* __restrict__ pap_part, int npap, CgDev* __restrict__ cgd,
     double* __restrict__ rr_part, int n) {
   if (cgd->done) return;
+  const int k = cgd->iter + 1;
   const double pap = block_sum_partials(pap_part, npap);
   const double rr = cgd->rr[(k - 1) & 1];
   const double alpha = pap > 0.0 ? rr / pap : 0.0;
@@ -310,29 +315,36 @@ __global__ void __launch_bounds__(kVecThreads) cg_axpy_kernel(
     r[i] = rv;
     acc += double(rv.x) * rv.x + double(rv.y) * rv.y;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) cgd->alpha = alpha;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    cgd->alpha = alpha;
+    cgd->k_axpy = k;
+  }
   double v[1] = {acc};
   block_reduce_store<1>(v, rr_part, gridDim.x);
 }
 
 // rr_new = sum(rr partials); done if rr_new <= tol2 bb; beta = rr_new / rr_old;
-// p = r + beta p.  Block 0 publishes rr[k&1], the history entry and `done`.
+// p = r + beta p (also on the converging iteration, so that a reliable update
+// that finds the true residual still too large can simply continue).
+// Block 0 publishes rr[k&1], the history entry, iter = k (also to the host
+// through iter_out) and `done`; no block of this kernel reads those.
 template <typename R>
 __global__ void __launch_bounds__(kVecThreads) cg_xpay_kernel(
     typename Vec2<R>::T* __restrict__ p, const typename Vec2<R>::T* __restrict__ r,
-    const double* __restrict__ rr_part, int nrr, CgDev* __restrict__ cgd, int k,
-    double* __restrict__ hist, int n) {
+    const double* __restrict__ rr_part, int nrr, CgDev* __restrict__ cgd,
+    double* __restrict__ hist, int* __restrict__ iter_out, int maxiter, int n) {
   if (cgd->done) return;
+  const int k = cgd->k_axpy;
   const double rr_new = block_sum_partials(rr_part, nrr);
   const double rr_old = cgd->rr[(k - 1) & 1];
   const bool conv = rr_new <= cgd->tol2bb;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     cgd->rr[k & 1] = rr_new;
-    hist[k] = rr_new;
+    if (k <= maxiter) hist[k] = rr_new;
     cgd->iter = k;
+    *iter_out = k;
     if (conv) cgd->done = 1;
   }
-  if (conv) return;
   const R beta = R(rr_old > 0.0 ? rr_new / rr_old : 0.0);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     typename Vec2<R>::T pv = p[i];
@@ -383,15 +395,30 @@ __global__ void __launch_bounds__(kVecThreads) ru_residual_kernel(const double2*
   block_reduce_store<1>(v, part, gridDim.x);
 }
 
-// Publishes a reliable-update residual: rr[k&1] = |r|^2, done = rr <= tol2 bb.
-__global__ void ru_publish_kernel(const double* __restrict__ part, int n, CgDev* __restrict__ cgd, int k,
+// Publishes a reliable-update residual after iteration k = iter:
+// rr[k&1] = |r|^2, done = rr <= tol2 bb.  The search direction is kept (the
+// usual reliable update) while the true |r|^2 is within a factor 2 of the
+// recursive one it replaces; beyond that the recursion has drifted too far
+// for p to match r, and `restart` asks cg_restart_kernel to set p = r.
+__global__ void ru_publish_kernel(const double* __restrict__ part, int n, CgDev* __restrict__ cgd,
                                   double* __restrict__ true_rr) {
   const double rr = block_sum_partials(part, n);
   if (threadIdx.x == 0) {
-    cgd->rr[k & 1] = rr;
+    const double rr_iter = cgd->rr[cgd->iter & 1];
+    cgd->restart = (rr > 2.0 * rr_iter) ? 1 : 0;
+    cgd->rr[cgd->iter & 1] = rr;
     cgd->done = rr <= cgd->tol2bb ? 1 : 0;
     *true_rr = rr;
   }
+}
+
+// p = r_s after a reliable update that asked for a restart.
+template <typename R>
+__global__ void __launch_bounds__(kVecThreads) cg_restart_kernel(typename Vec2<R>::T* __restrict__ p,
+                                                                 const typename Vec2<R>::T* __restrict__ r,
+                                                                 const CgDev* __restrict__ cgd, int n) {
+  if (!cgd->restart) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = r[i];
 }
 
 // Start of a solve: bb = |b|^2 from partials, rr = bb, done = (bb == 0).
@@ -404,6 +431,8 @@ __global__ void cg_init_kernel(const double* __restrict__ part, int n, CgDev* __
     cgd->rr[0] = cgd->rr[1] = bb;
     cgd->done = bb == 0.0 ? 1 : 0;
     cgd->iter = 0;
+    cgd->k_axpy = 0;
+    cgd->restart = 0;
     *bb_out = bb;
   }
 }
@@ -537,15 +566,16 @@ cudaError_t launch_fermion_force(const GeomH& gh, const void* U, const void* Xe,
 
 template <typename R>
 cudaError_t launch_cg_axpy(void* x, void* r, const void* p, const void* ap, const double* pap_part, int npap,
-                           CgDev* cgd, int k, double* rr_part, int n, cudaStream_t st) {
+                           CgDev* cgd, double* rr_part, int n, cudaStream_t st) {
   cg_axpy_kernel<R><<<vec_blocks(n), kVecThreads, 0, st>>>(v2<R>(x), v2<R>(r), cv2<R>(p), cv2<R>(ap), pap_part,
-                                                           npap, cgd, k, rr_part, n);
+                                                           npap, cgd, rr_part, n);
   return cudaGetLastError();
 }
 template <typename R>
-cudaError_t launch_cg_xpay(void* p, const void* r, const double* rr_part, int nrr, CgDev* cgd, int k,
-                           double* hist, int n, cudaStream_t st) {
-  cg_xpay_kernel<R><<<vec_blocks(n), kVecThreads, 0, st>>>(v2<R>(p), cv2<R>(r), rr_part, nrr, cgd, k, hist, n);
+cudaError_t launch_cg_xpay(void* p, const void* r, const double* rr_part, int nrr, CgDev* cgd, double* hist,
+                           int* iter_out, int maxiter, int n, cudaStream_t st) {
+  cg_xpay_kernel<R><<<vec_blocks(n), kVecThreads, 0, st>>>(v2<R>(p), cv2<R>(r), rr_part, nrr, cgd, hist,
+                                                           iter_out, maxiter, n);
   return cudaGetLastError();
 }
 template <typename RI>
@@ -560,8 +590,13 @@ cudaError_t launch_ru_residual(const void* b64, const void* ax64, void* r64, voi
                                                                 (double2*)r64, v2<RI>(rs), part, n);
   return cudaGetLastError();
 }
-cudaError_t launch_ru_publish(const double* part, int n, CgDev* cgd, int k, double* true_rr, cudaStream_t st) {
-  ru_publish_kernel<<<1, 1024, 0, st>>>(part, n, cgd, k, true_rr);
+cudaError_t launch_ru_publish(const double* part, int n, CgDev* cgd, double* true_rr, cudaStream_t st) {
+  ru_publish_kernel<<<1, 1024, 0, st>>>(part, n, cgd, true_rr);
+  return cudaGetLastError();
+}
+template <typename R>
+cudaError_t launch_cg_restart(void* p, const void* r, const CgDev* cgd, int n, cudaStream_t st) {
+  cg_restart_kernel<R><<<vec_blocks(n), kVecThreads, 0, st>>>(v2<R>(p), cv2<R>(r), cgd, n);
   return cudaGetLastError();
 }
 cudaError_t launch_cg_init(const double* part, int n, CgDev* cgd, double tol2, double* bb_out, cudaStream_t st) {
@@ -608,14 +643,16 @@ FG_INST_F(float, 6, float)
 FG_INST_F(float, 9, double)
 FG_INST_F(float, 6, double)
 
-template cudaError_t launch_cg_axpy<double>(void*, void*, const void*, const void*, const double*, int, CgDev*, int,
+template cudaError_t launch_cg_axpy<double>(void*, void*, const void*, const void*, const double*, int, CgDev*,
                                             double*, int, cudaStream_t);
-template cudaError_t launch_cg_axpy<float>(void*, void*, const void*, const void*, const double*, int, CgDev*, int,
+template cudaError_t launch_cg_axpy<float>(void*, void*, const void*, const void*, const double*, int, CgDev*,
                                            double*, int, cudaStream_t);
-template cudaError_t launch_cg_xpay<double>(void*, const void*, const double*, int, CgDev*, int, double*, int,
-                                            cudaStream_t);
-template cudaError_t launch_cg_xpay<float>(void*, const void*, const double*, int, CgDev*, int, double*, int,
+template cudaError_t launch_cg_xpay<double>(void*, const void*, const double*, int, CgDev*, double*, int*, int,
+                                            int, cudaStream_t);
+template cudaError_t launch_cg_xpay<float>(void*, const void*, const double*, int, CgDev*, double*, int*, int, int,
                                            cudaStream_t);
+template cudaError_t launch_cg_restart<double>(void*, const void*, const CgDev*, int, cudaStream_t);
+template cudaError_t launch_cg_restart<float>(void*, const void*, const CgDev*, int, cudaStream_t);
 template cudaError_t launch_ru_accumulate<double>(void*, void*, int, cudaStream_t);
 template cudaError_t launch_ru_accumulate<float>(void*, void*, int, cudaStream_t);
 template cudaError_t launch_ru_residual<double>(const void*, const void*, void*, void*, double*, int, cudaStream_t);

@@ -19,7 +19,9 @@ struct CgDev {
   double tol2bb;
   double alpha;
   int done;
-  int iter;
+  int iter;     // last completed iteration (written by xpay's block 0)
+  int k_axpy;   // iteration in progress (written by axpy's block 0)
+  int restart;  // set by a reliable update whose true residual left the recursion far behind
 };
 
 int vec_blocks(int n);
@@ -43,16 +45,20 @@ cudaError_t launch_fermion_force(const GeomH& g, const void* U, const void* Xe, 
 
 template <typename R>
 cudaError_t launch_cg_axpy(void* x, void* r, const void* p, const void* ap, const double* pap_part, int npap,
-                           CgDev* cgd, int k, double* rr_part, int n, cudaStream_t st);
+                           CgDev* cgd, double* rr_part, int n, cudaStream_t st);
+// hist[k] receives |r_k|^2 for k <= maxiter and *iter_out the iteration k.
 template <typename R>
-cudaError_t launch_cg_xpay(void* p, const void* r, const double* rr_part, int nrr, CgDev* cgd, int k,
-                           double* hist, int n, cudaStream_t st);
+cudaError_t launch_cg_xpay(void* p, const void* r, const double* rr_part, int nrr, CgDev* cgd, double* hist,
+                           int* iter_out, int maxiter, int n, cudaStream_t st);
 template <typename RI>
 cudaError_t launch_ru_accumulate(void* x64, void* xs, int n, cudaStream_t st);
 template <typename RI>
 cudaError_t launch_ru_residual(const void* b64, const void* ax64, void* r64, void* rs, double* part, int n,
                                cudaStream_t st);
-cudaError_t launch_ru_publish(const double* part, int n, CgDev* cgd, int k, double* true_rr, cudaStream_t st);
+cudaError_t launch_ru_publish(const double* part, int n, CgDev* cgd, double* true_rr, cudaStream_t st);
+// p = r when the last reliable update asked for a restart (cgd->restart).
+template <typename R>
+cudaError_t launch_cg_restart(void* p, const void* r, const CgDev* cgd, int n, cudaStream_t st);
 cudaError_t launch_cg_init(const double* part, int n, CgDev* cgd, double tol2, double* bb_out, cudaStream_t st);
 // dst = (RO) src, with block partials of |src|^2 if part != nullptr.
 template <typename RO, typename RI>
