@@ -223,6 +223,58 @@ unsigned long long fg_device_bytes(const fg_lattice *h);
 
 
 /* ------------------------------------------------------------------------
+ * Batches of independent pure-gauge chains (many small lattices at once).
+ *
+ * A batch holds nchains independent lattices of different volumes and
+ * couplings, all advanced with the same integrator and step size.  Each MD
+ * sub-step of section 3 / Table 1 (kick, drift, force-gradient displacement)
+ * is one persistent launch over the links of every chain; the HMC accept /
+ * reject of section 5 runs per chain on the device, so one trajectory of all
+ * chains is a single CUDA graph launch (use_graphs = 1).  A chain gives the
+ * same links alone (fg_lattice) and in a batch: the per-link arithmetic is
+ * shared.  Pure gauge only.
+ */
+typedef struct fg_batch fg_batch;
+
+typedef struct {
+  int nchains;             /* number of chains, >= 1 */
+  const int *dims;         /* nchains x 4 extents (Lx, Ly, Lz, Lt; even, >= 2); copied */
+  const double *beta;      /* nchains couplings; copied */
+  int precision;           /* FG_FP32 (default) or FG_FP64 */
+  int link_reals;          /* 18 or 12 */
+  int reunitarize;         /* -1: after every drift for FP32, never for FP64 */
+  double alpha;            /* PQPQP parameter for FG_OMELYAN (0.1932) */
+  int tile;                /* half-sites per block: 16, 32 or 64; 0 = time all three on the
+                              first trajectory and keep the fastest (autotuning) */
+  int use_graphs;          /* 1 (default): capture each trajectory as one CUDA graph */
+  unsigned long long seed; /* device momentum and accept RNG */
+  void *cuda_stream;       /* stream to run on, NULL => the batch creates one */
+} fg_batch_params;
+
+fg_status fg_batch_params_default(fg_batch_params *p);
+/* Validates *p (FG_EINVAL on bad extents, couplings or tile) and allocates
+ * all chains on the device with cold-start links. */
+fg_status fg_batch_create(const fg_batch_params *p, fg_batch **out);
+void fg_batch_destroy(fg_batch *b);
+const char *fg_batch_last_error(const fg_batch *b);
+/* Fields of one chain, host layouts as for fg_lattice (chain in [0, nchains)). */
+fg_status fg_batch_set_gauge(fg_batch *b, int chain, const double *host_links);
+fg_status fg_batch_get_gauge(fg_batch *b, int chain, double *host_links);
+fg_status fg_batch_set_momenta(fg_batch *b, int chain, const double *host_p8);
+fg_status fg_batch_get_momenta(fg_batch *b, int chain, double *host_p8);
+/* One trajectory of length tau = n dt for every chain.  refresh != 0 draws
+ * momenta on the device first; accept_mode 0 = Metropolis per chain with a
+ * device uniform, 1 = accept every finite dH (thermalisation, tests).
+ * out (may be NULL) receives nchains results (dH, H0, H1, action parts,
+ * accepted, n_steps, n_force). */
+fg_status fg_batch_trajectory(fg_batch *b, fg_integrator integ, double dt, double tau, int refresh,
+                              int accept_mode, fg_traj_result *out);
+/* Tile size in use (0 until the autotuner has run). */
+fg_status fg_batch_tile(const fg_batch *b, int *tile);
+/* Kernels launched by the batch (a graph launch counts its kernels). */
+long long fg_batch_launch_count(const fg_batch *b);
+
+/* ------------------------------------------------------------------------
  * Allocation-free action sums (no handle).
  *
  * The paper has no counterpart to this entry point.  It is for callers that

@@ -51,6 +51,13 @@ class FgCgResult(C.Structure):
                 ("true_residual", C.c_double)]
 
 
+class FgBatchParams(C.Structure):
+    _fields_ = [("nchains", C.c_int), ("dims", C.POINTER(C.c_int)), ("beta", C.POINTER(C.c_double)),
+                ("precision", C.c_int), ("link_reals", C.c_int), ("reunitarize", C.c_int),
+                ("alpha", C.c_double), ("tile", C.c_int), ("use_graphs", C.c_int),
+                ("seed", C.c_ulonglong), ("cuda_stream", C.c_void_p)]
+
+
 SIGNATURES = {
     "fg_params_default": (_i, [C.POINTER(FgParams)]),
     "fg_lattice_create": (_i, [C.POINTER(FgParams), C.POINTER(_vp)]),
@@ -79,6 +86,17 @@ SIGNATURES = {
     "fg_sync": (_i, [_vp]),
     "fg_device_bytes": (C.c_ulonglong, [_vp]),
     "fg_action_sums_noalloc": (_i, [_vp, _vp, C.POINTER(C.c_int), _d, _vp, _vp]),
+    "fg_batch_params_default": (_i, [C.POINTER(FgBatchParams)]),
+    "fg_batch_create": (_i, [C.POINTER(FgBatchParams), C.POINTER(_vp)]),
+    "fg_batch_destroy": (None, [_vp]),
+    "fg_batch_last_error": (C.c_char_p, [_vp]),
+    "fg_batch_set_gauge": (_i, [_vp, _i, _dp]),
+    "fg_batch_get_gauge": (_i, [_vp, _i, _dp]),
+    "fg_batch_set_momenta": (_i, [_vp, _i, _dp]),
+    "fg_batch_get_momenta": (_i, [_vp, _i, _dp]),
+    "fg_batch_trajectory": (_i, [_vp, _i, _d, _d, _i, _i, C.POINTER(FgTrajResult)]),
+    "fg_batch_tile": (_i, [_vp, C.POINTER(_i)]),
+    "fg_batch_launch_count": (C.c_longlong, [_vp]),
 }
 
 _lib = None
@@ -277,6 +295,94 @@ class Lattice:
 
     def device_bytes(self):
         return int(self._lib.fg_device_bytes(self._h))
+
+
+class Batch:
+    """Many independent pure-gauge chains advanced together (``fg_batch*``)."""
+
+    def __init__(self, dims_list, betas, precision="fp32", link_reals=18, alpha=0.1932, tile=0,
+                 use_graphs=True, seed=1, reunitarize=None, stream=None):
+        lib = load()
+        p = FgBatchParams()
+        _check(lib.fg_batch_params_default(C.byref(p)), None)
+        n = len(dims_list)
+        self._dims = (C.c_int * (4 * n))(*[int(d) for dims in dims_list for d in dims])
+        self._beta = (C.c_double * n)(*[float(b) for b in betas])
+        p.nchains = n
+        p.dims = self._dims
+        p.beta = self._beta
+        p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        p.link_reals, p.alpha, p.tile = int(link_reals), float(alpha), int(tile)
+        p.use_graphs = int(bool(use_graphs))
+        p.seed = int(seed)
+        p.reunitarize = -1 if reunitarize is None else int(reunitarize)
+        p.cuda_stream = stream
+        self._lib = lib
+        self._h = C.c_void_p()
+        st = lib.fg_batch_create(C.byref(p), C.byref(self._h))
+        if st != FG_OK:
+            raise FgError(st, "fg_batch_create failed")
+        self.dims = [tuple(int(x) for x in d) for d in dims_list]
+        self.n = n
+
+    def close(self):
+        if self._h:
+            self._lib.fg_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _call(self, name, *args):
+        st = getattr(self._lib, name)(self._h, *args)
+        if st != FG_OK:
+            raise FgError(st, self._lib.fg_batch_last_error(self._h).decode())
+
+    def _v(self, c):
+        return int(np.prod(self.dims[c]))
+
+    def _shape(self, c):
+        lx, ly, lz, lt = self.dims[c]
+        return (lt, lz, ly, lx)
+
+    def set_gauge(self, c, u):
+        self._call("fg_batch_set_gauge", int(c), _ptr(_f64(u, (self._v(c), 4, 18))))
+
+    def get_gauge(self, c):
+        a = np.empty(self._v(c) * 72, dtype=np.float64)
+        self._call("fg_batch_get_gauge", int(c), _ptr(a))
+        return a.view(np.complex128).reshape(self._shape(c) + (4, 3, 3))
+
+    def set_momenta(self, c, p):
+        self._call("fg_batch_set_momenta", int(c), _ptr(_f64(p, (self._v(c), 4, 8))))
+
+    def get_momenta(self, c):
+        a = np.empty(self._v(c) * 32, dtype=np.float64)
+        self._call("fg_batch_get_momenta", int(c), _ptr(a))
+        return a.reshape(self._shape(c) + (4, 8))
+
+    def trajectory(self, integrator, dt, tau=1.0, refresh=True, always_accept=False):
+        res = (FgTrajResult * self.n)()
+        self._call("fg_batch_trajectory", INTEGRATORS[integrator], float(dt), float(tau), int(bool(refresh)),
+                   int(bool(always_accept)), res)
+        return [{k: getattr(r, k) for k, _ in FgTrajResult._fields_} for r in res]
+
+    def tile(self):
+        t = C.c_int()
+        self._call("fg_batch_tile", C.byref(t))
+        return t.value
+
+    def launch_count(self):
+        return int(self._lib.fg_batch_launch_count(self._h))
 
 
 def _check(st, h):
