@@ -76,6 +76,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fermion", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     return ap.parse_args()
 
 
@@ -291,6 +292,66 @@ def fermion_measurement(fg, stream, rank, hbm_peak):
     }
 
 
+def batched_measurement(fg, stream, rank, n_traj=6):
+    """64 independent chains, volumes drawn from {4,6,8,10,12}^4 and beta from
+    U[5.7, 6.2] (seed 4), FG tau=1 dt=1/8: the FP32 batch (one launch per MD
+    sub-step for all chains, one CUDA graph per trajectory, autotuned tiles)
+    against the plain FP64 one-chain-per-launch path on the same
+    configurations.  Reports accepted trajectories per second and <exp(-dH)>."""
+    rng = inputs.make_rng(4 + 1000 * rank)
+    extents = rng.choice([4, 6, 8, 10, 12], size=64)
+    betas = rng.uniform(5.7, 6.2, size=64)
+    dims_list = [(int(L),) * 4 for L in extents]
+    sites = int(sum(L ** 4 for L in extents))
+    bat = fg.Batch(dims_list, betas, precision="fp32", tile=0, use_graphs=True, seed=500 + rank, stream=stream)
+    for k, d in enumerate(dims_list):
+        bat.set_gauge(k, inputs.hot_start(d, 700 + k + 1000 * rank))
+    for _ in range(20):
+        bat.trajectory("fg", 0.125, 1.0, refresh=True, always_accept=True)
+    for _ in range(20):
+        bat.trajectory("fg", 0.125, 1.0, refresh=True, always_accept=False)
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res_b = [bat.trajectory("fg", 0.125, 1.0, refresh=True, always_accept=False) for _ in range(n_traj)]
+    tb = time.perf_counter() - t0
+    tile = bat.tile()
+    starts = [bat.get_gauge(k) for k in range(64)]
+    bat.close()
+    # one chain per launch, FP64, same configurations
+    lats = []
+    for k, d in enumerate(dims_list):
+        lat = fg.Lattice(d, float(betas[k]), precision="fp64", seed=900 + k + 1000 * rank, stream=stream)
+        lat.set_gauge(starts[k])
+        lats.append(lat)
+    for lat in lats:      # warm-up
+        lat.trajectory("fg", 0.125, 1.0, refresh=True, u_accept=-1.0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res_s = [[lat.trajectory("fg", 0.125, 1.0, refresh=True, u_accept=-1.0) for lat in lats]
+             for _ in range(n_traj)]
+    ts = time.perf_counter() - t0
+    for lat in lats:
+        lat.close()
+
+    def stats(res, secs):
+        flat = [r for sweep in res for r in sweep]
+        acc = sum(r["accepted"] for r in flat)
+        e = np.array([np.exp(-r["dH"]) for r in flat])
+        return {"accepted_traj_per_s": acc / secs, "traj_per_s": len(flat) / secs,
+                "acceptance": acc / len(flat), "mean_exp_minus_dH": float(e.mean()),
+                "mean_exp_minus_dH_err": float(e.std(ddof=1) / np.sqrt(len(e)))}
+
+    b = stats(res_b, tb)
+    s1 = stats(res_s, ts)
+    return {"workload": "64 pure-gauge chains, L^4 with L drawn from {4,6,8,10,12} and beta from U[5.7,6.2] "
+                        "(seed 4), FG tau=1 dt=1/8", "sites_total": sites,
+            "batched_fp32_graphs": dict(b, tile=tile),
+            "one_chain_per_launch_fp64": s1,
+            "speedup_accepted_per_s": b["accepted_traj_per_s"] / s1["accepted_traj_per_s"],
+            "trajectories_timed_per_chain": n_traj}
+
+
 def run_ours(args):
     rank, world, local = dist_info()
     import torch
@@ -417,6 +478,9 @@ def run_ours(args):
     ferm = None
     if not args.no_fermion:
         ferm = fermion_measurement(fg, stream.cuda_stream, rank, hbm_peak())
+    batched = None
+    if not args.no_batch:
+        batched = batched_measurement(fg, stream.cuda_stream, rank)
 
     if rank == 0:
         cfg = workload_config(args)
@@ -429,6 +493,7 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
                 "config": cfg, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fermion": ferm,
+                "batched_chains": batched,
                 "gpu_launches": launches, "clocks": clk}
         print(json.dumps(line), flush=True)
     lat.close()
