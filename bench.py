@@ -77,6 +77,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fermion", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
     return ap.parse_args()
 
 
@@ -352,6 +353,36 @@ def batched_measurement(fg, stream, rank, n_traj=6):
             "trajectories_timed_per_chain": n_traj}
 
 
+def serving_measurement(duration_s=4.0, rate_hz=200.0, slots=8, budget_gb=24.0):
+    """Poisson stream of trajectory requests (seed 5) over 32 resident chains
+    (70% pure gauge at 8^4..24^4, 30% Nf=2 Wilson at 8^3x16 / 12^3x24),
+    Omelyan or FG with dt 1/8 or 1/12, FP32, admission by HBM footprint."""
+    from paper_0910_2950_gb300 import serve
+    chains = serve.served_chain_mix(32, seed=5)
+    reqs = serve.poisson_stream(rate_hz, duration_s, chains, seed=5)
+    srv = serve.TrajectoryServer(slots=slots, hbm_budget_bytes=int(budget_gb * (1 << 30)))
+    res, wall, busy = srv.serve(reqs, realtime=True)
+    lat = np.array([r.latency for r in res])
+    nf2 = np.array([chains[r.chain].kappa > 0 for r in res])
+    out = {
+        "workload": f"Poisson {rate_hz:g} requests/s for {duration_s:g} s over 32 chains (70% pure gauge L^4, "
+                    "L in {8,12,16,24}, beta in [5.7,6.2]; 30% Nf=2 Wilson 8^3x16 / 12^3x24, kappa in "
+                    "[0.155,0.159]); Omelyan or FG, dt 1/8 or 1/12, FP32; chains resident on device",
+        "requests": len(res), "slots": slots, "hbm_budget_gb": budget_gb,
+        "trajectories_per_s": len(res) / wall, "wall_s": wall, "utilisation": busy / wall,
+        "latency_ms": {"p50": 1000 * float(np.percentile(lat, 50)), "p99": 1000 * float(np.percentile(lat, 99)),
+                       "max": 1000 * float(lat.max())},
+        "latency_ms_pure_gauge_p50_p99": [1000 * float(np.percentile(lat[~nf2], q)) for q in (50, 99)]
+        if (~nf2).any() else None,
+        "latency_ms_nf2_p50_p99": [1000 * float(np.percentile(lat[nf2], q)) for q in (50, 99)] if nf2.any() else None,
+        "acceptance": float(np.mean([r.accepted for r in res])),
+        "evictions": srv.evictions, "peak_resident_gb": srv.peak_resident_bytes / (1 << 30),
+        "offered_load_stable": bool(wall < duration_s * 1.5),
+    }
+    srv.close()
+    return out
+
+
 def run_ours(args):
     rank, world, local = dist_info()
     import torch
@@ -481,6 +512,9 @@ def run_ours(args):
     batched = None
     if not args.no_batch:
         batched = batched_measurement(fg, stream.cuda_stream, rank)
+    served = None
+    if not args.no_serve:
+        served = serving_measurement()
 
     if rank == 0:
         cfg = workload_config(args)
@@ -493,7 +527,7 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
                 "config": cfg, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fermion": ferm,
-                "batched_chains": batched,
+                "batched_chains": batched, "serving": served,
                 "gpu_launches": launches, "clocks": clk}
         print(json.dumps(line), flush=True)
     lat.close()

@@ -198,6 +198,16 @@ fg_status fg_apply_mhat(fg_lattice *h, const double *host_in_even, double *host_
 fg_status fg_cg_solve(fg_lattice *h, const double *host_b_even, double *host_x_even,
                       fg_cg_result *res);
 
+/* Haar-random links drawn on the device (a hot start without a host
+ * transfer; Philox keyed by fg_params.seed, every call draws new links). */
+fg_status fg_random_gauge(fg_lattice *h);
+
+/* Position of the handle's random streams: the next momentum refresh,
+ * pseudofermion heat bath and host accept uniform all use draw `pos`.  A
+ * caller that sets it to the chain's trajectory index before each trajectory
+ * gets results that do not depend on what else ran in between. */
+fg_status fg_set_rng_position(fg_lattice *h, unsigned long long pos);
+
 /* Re-project every link onto SU(3) (Gram-Schmidt of rows 1-2, row 3 = (row1 x row2)^*). */
 fg_status fg_reunitarize(fg_lattice *h);
 

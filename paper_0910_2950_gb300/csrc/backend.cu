@@ -185,6 +185,20 @@ class Backend final : public IBackend {
     return sync();
   }
 
+  fg_status random_gauge() override {
+    const uint32_t d = hot_draw_++;
+    fg_status s = run(KC_CONVERT, [&] { return launch_random_links<R, NC>(g_, U_, h_->prm.seed, d, st_); });
+    if (s != FG_OK) return s;
+    sf0_valid_ = false;
+    return sync();
+  }
+  fg_status set_rng_position(unsigned long long pos) override {
+    draw_ = (uint32_t)pos;
+    pf_draw_ = (uint32_t)pos;
+    h_->accept_draws = pos;
+    return FG_OK;
+  }
+
   // ---------------------------------------------------------------- MD
   fg_status md_step(int integ, double dt) override {
     std::vector<Op> ops = trajectory_ops(integ, h_->prm.alpha, 1, false);
@@ -274,6 +288,7 @@ class Backend final : public IBackend {
   double* host_out_ = nullptr;
   uint32_t draw_ = 0;
   uint32_t pf_draw_ = 0;
+  uint32_t hot_draw_ = 0;
   // fermions
   void *chi64_ = nullptr, *phi64_ = nullptr, *b64_ = nullptr, *x64_ = nullptr, *r64_ = nullptr;
   void *ax64_ = nullptr, *te64_ = nullptr, *to64_ = nullptr;

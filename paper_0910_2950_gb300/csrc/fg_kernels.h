@@ -45,6 +45,10 @@ cudaError_t launch_drift(const GeomH& g, const void* Uin, const void* P, void* U
 template <typename R, int NC>
 cudaError_t launch_unit_links(const GeomH& g, void* U, cudaStream_t st);
 
+// Haar-random SU(3) links (device hot start).
+template <typename R, int NC>
+cudaError_t launch_random_links(const GeomH& g, void* U, uint64_t seed, uint32_t draw, cudaStream_t st);
+
 template <typename R, int NC>
 cudaError_t launch_reunitarize(const GeomH& g, void* U, cudaStream_t st);
 

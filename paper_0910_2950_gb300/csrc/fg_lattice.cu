@@ -290,6 +290,14 @@ fg_status fg_cg_solve(fg_lattice* h, const double* b, double* x, fg_cg_result* r
   if (res) *res = r;
   return s;
 }
+fg_status fg_random_gauge(fg_lattice* h) {
+  FG_CHECK_HANDLE(h);
+  return h->be->random_gauge();
+}
+fg_status fg_set_rng_position(fg_lattice* h, unsigned long long pos) {
+  FG_CHECK_HANDLE(h);
+  return h->be->set_rng_position(pos);
+}
 fg_status fg_reunitarize(fg_lattice* h) {
   FG_CHECK_HANDLE(h);
   return h->be->reunitarize_all();

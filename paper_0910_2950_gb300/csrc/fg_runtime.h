@@ -69,6 +69,8 @@ struct IBackend {
   virtual fg_status apply_mhat(const double* in, double* out, int dagger) = 0;
   virtual fg_status cg_solve(const double* b, double* x, fg_cg_result* r) = 0;
   virtual fg_status reunitarize_all() = 0;
+  virtual fg_status random_gauge() = 0;
+  virtual fg_status set_rng_position(unsigned long long pos) = 0;
 };
 
 }  // namespace fg

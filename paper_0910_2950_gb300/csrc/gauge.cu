@@ -62,6 +62,38 @@ __global__ void __launch_bounds__(256) unit_links_kernel(Gauge<R, NC> U, int V) 
   U.store(mu, s, u);
 }
 
+// Haar-random SU(3) link from 12 Gaussians (Philox counter (4 lex + mu, draw,
+// stream 5, word)): Gram-Schmidt of two complex Gaussian rows gives the first
+// two rows of a Haar U(3) matrix, which fix the SU(3) matrix with the third
+// row (row1 x row2)^*; SU(3) is in one-to-one correspondence with such row
+// pairs, so the result is Haar on SU(3).
+template <typename R, int NC>
+__global__ void __launch_bounds__(256) random_links_kernel(Gauge<R, NC> U, Geom g, uint32_t k0, uint32_t k1,
+                                                           uint32_t draw) {
+  const int s = blockIdx.x * kSitesPerBlock + threadIdx.x;
+  const int mu = threadIdx.y;
+  if (s >= g.V) return;
+  int c[4], par;
+  cb_coords(g, s, c, par);
+  const uint32_t lex = (uint32_t)(c[0] + g.L[0] * (c[1] + g.L[1] * (c[2] + g.L[2] * c[3])));
+  R z[12];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    uint32_t ctr[4] = {lex * 4u + (uint32_t)mu, draw, 5u, (uint32_t)q};
+    Philox::rounds(ctr, k0, k1);
+    box_muller<R>(ctr[0], ctr[1], z[4 * q + 0], z[4 * q + 1]);
+    box_muller<R>(ctr[2], ctr[3], z[4 * q + 2], z[4 * q + 3]);
+  }
+  M3<R> u;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    u.e[0][j] = cx<R>(z[2 * j], z[2 * j + 1]);
+    u.e[1][j] = cx<R>(z[6 + 2 * j], z[6 + 2 * j + 1]);
+  }
+  reunitarize(u);
+  U.store(mu, s, u);
+}
+
 template <typename R, int NC>
 __global__ void __launch_bounds__(256) reunitarize_kernel(Gauge<R, NC> U, int V) {
   const int s = blockIdx.x * kSitesPerBlock + threadIdx.x;
@@ -255,6 +287,13 @@ cudaError_t launch_unit_links(const GeomH& gh, void* U, cudaStream_t st) {
 }
 
 template <typename R, int NC>
+cudaError_t launch_random_links(const GeomH& gh, void* U, uint64_t seed, uint32_t draw, cudaStream_t st) {
+  random_links_kernel<R, NC><<<link_grid(gh.V), link_block(), 0, st>>>(gauge_of<R, NC>(U, gh.V), to_dev(gh),
+                                                                       (uint32_t)seed, (uint32_t)(seed >> 32), draw);
+  return cudaGetLastError();
+}
+
+template <typename R, int NC>
 cudaError_t launch_reunitarize(const GeomH& gh, void* U, cudaStream_t st) {
   reunitarize_kernel<R, NC><<<link_grid(gh.V), link_block(), 0, st>>>(gauge_of<R, NC>(U, gh.V), gh.V);
   return cudaGetLastError();
@@ -313,6 +352,7 @@ cudaError_t launch_mom_to_canon(const GeomH& gh, const void* P, double* canon, c
                                            int, cudaStream_t);                                      \
   template cudaError_t launch_reunitarize<R, NC>(const GeomH&, void*, cudaStream_t);                \
   template cudaError_t launch_unit_links<R, NC>(const GeomH&, void*, cudaStream_t);                 \
+  template cudaError_t launch_random_links<R, NC>(const GeomH&, void*, uint64_t, uint32_t, cudaStream_t); \
   template cudaError_t launch_energy<R, NC>(const GeomH&, const void*, const void*, double, int,    \
                                             double*, double*, int*, cudaStream_t);                  \
   template cudaError_t launch_gauge_to_device<R, NC>(const GeomH&, const double*, void*,            \

@@ -79,6 +79,8 @@ SIGNATURES = {
     "fg_apply_mhat": (_i, [_vp, _dp, _dp, _i]),
     "fg_cg_solve": (_i, [_vp, _dp, _dp, C.POINTER(FgCgResult)]),
     "fg_reunitarize": (_i, [_vp]),
+    "fg_random_gauge": (_i, [_vp]),
+    "fg_set_rng_position": (_i, [_vp, C.c_ulonglong]),
     "fg_timing_enable": (_i, [_vp, _i]),
     "fg_timing_reset": (_i, [_vp]),
     "fg_kernel_time": (_i, [_vp, C.c_char_p, _dp, C.POINTER(C.c_longlong)]),
@@ -274,6 +276,12 @@ class Lattice:
 
     def reunitarize(self):
         self._call("fg_reunitarize")
+
+    def random_gauge(self):
+        self._call("fg_random_gauge")
+
+    def set_rng_position(self, pos):
+        self._call("fg_set_rng_position", C.c_ulonglong(int(pos)))
 
     # -- instrumentation
     def timing(self, on=True):
