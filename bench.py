@@ -515,6 +515,9 @@ def run_ours(args):
     served = None
     if not args.no_serve:
         served = serving_measurement()
+        # the same stream at a rate the GPU sustains (80% of the capacity just measured)
+        stable = 0.8 * served["trajectories_per_s"]
+        served["at_sustainable_rate"] = serving_measurement(rate_hz=stable)
 
     if rank == 0:
         cfg = workload_config(args)

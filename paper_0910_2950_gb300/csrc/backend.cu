@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -641,20 +642,26 @@ class Backend final : public IBackend {
     });
   }
 
-  // A CUDA graph of kCgBatch iterations on links U, captured on first use and
-  // cached per link buffer (the links are the only argument that changes
-  // between solves).  Null if capture is not possible on this stream.
+  // A CUDA graph of n iterations (n = 2, 4 or 8) on links U, captured on first
+  // use and cached per link buffer and n (the links are the only argument
+  // that changes between solves).  Null if capture is not possible.
   static constexpr int kCgBatch = 8;
   struct CgGraph {
     const void* U;
+    int n;
     cudaGraphExec_t exec;
   };
   std::vector<CgGraph> cg_graphs_;
   bool cg_graphs_broken_ = false;
+  // FG_CG_GRAPHS=0 in the environment turns the graph batches off (tuning).
+  const bool use_cg_graphs_ = [] {
+    const char* e = std::getenv("FG_CG_GRAPHS");
+    return !(e && e[0] == '0');
+  }();
 
-  cudaGraphExec_t cg_graph(const void* U) {
+  cudaGraphExec_t cg_graph(const void* U, int n) {
     for (const CgGraph& c : cg_graphs_)
-      if (c.U == U) return c.exec;
+      if (c.U == U && c.n == n) return c.exec;
     if (cg_graphs_broken_) return nullptr;
     cudaGraph_t graph = nullptr;
     if (cudaStreamBeginCapture(st_, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
@@ -663,12 +670,12 @@ class Backend final : public IBackend {
       return nullptr;
     }
     cudaError_t e = cudaSuccess;
-    for (int i = 0; i < kCgBatch && e == cudaSuccess; ++i) e = cg_iteration_raw(U);
+    for (int i = 0; i < n && e == cudaSuccess; ++i) e = cg_iteration_raw(U);
     cudaError_t e2 = cudaStreamEndCapture(st_, &graph);
     cudaGraphExec_t exec = nullptr;
     if (e == cudaSuccess && e2 == cudaSuccess && graph != nullptr &&
         cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
-      cg_graphs_.push_back({U, exec});
+      cg_graphs_.push_back({U, n, exec});
     } else {
       cudaGetLastError();
       exec = nullptr;
@@ -678,14 +685,14 @@ class Backend final : public IBackend {
     return exec;
   }
 
-  // Queue n iterations: one graph launch for a full batch when timing is off,
-  // single launches otherwise.
+  // Queue n iterations: one graph launch when n is 2, 4 or 8 and timing is
+  // off, single launches otherwise.
   fg_status cg_batch(const void* U, int n) {
-    if (n == kCgBatch && !h_->timer.on) {
-      cudaGraphExec_t g = cg_graph(U);
+    if ((n == 2 || n == 4 || n == 8) && !h_->timer.on && use_cg_graphs_) {
+      cudaGraphExec_t g = cg_graph(U, n);
       if (g != nullptr) {
         if (cudaGraphLaunch(g, st_) != cudaSuccess) return cuda_fail("cg graph launch");
-        h_->launches += 6 * kCgBatch;
+        h_->launches += 6 * n;
         return FG_OK;
       }
     }
@@ -737,14 +744,20 @@ class Backend final : public IBackend {
     if ((s = run(KC_REDUCE, [&] { return launch_cg_init(part_rr_, nbv, cgd_, tol * tol, bbp, st_); })) != FG_OK) return s;
     if (cudaMemcpyAsync(p_, rs_, (size_t)n * sizeof(C2), cudaMemcpyDeviceToDevice, st_) != cudaSuccess)
       return cuda_fail("cg setup");
-    if ((s = sync()) != FG_OK) return s;
-    const double bb = mapped_->bb;
     st->iters = 0;
     st->nru = 0;
     st->true_res = 0.0;
-    if (bb == 0.0) return FG_OK;
-    const double tol2bb = tol * tol * bb;
-    double maxrr = bb;
+    // |b|^2 reaches the host through mapped memory; it is read at the first
+    // check, which comes after the setup kernels, so the setup needs no sync.
+    double bb = -1.0, tol2bb = 0.0;
+    auto know_bb = [&]() {
+      if (bb < 0.0) {
+        bb = mapped_->bb;
+        tol2bb = tol * tol * bb;
+      }
+    };
+    double maxrr = 0.0;
+    double rate = -1.0;  // observed per-iteration factor of |r|^2
     const int maxiter = h_->prm.cg_maxiter;
     int queued = 0;      // iterations queued so far (including ones that return at once)
     int checked = 0;     // device iterations whose residual the host has read
@@ -756,6 +769,8 @@ class Backend final : public IBackend {
       while (!converged) {
         if (queued >= maxiter) {
           if ((s = sync()) != FG_OK) return s;
+          know_bb();
+          if (bb == 0.0) return FG_OK;
           const int upto = mapped_->dev_iter;
           for (int j = checked + 1; j <= upto; ++j)
             if (mapped_->hist[j] <= tol2bb) { converged = true; iters = j; break; }
@@ -766,7 +781,15 @@ class Backend final : public IBackend {
           }
           break;
         }
-        const int nb = std::min(kCgBatch, maxiter - queued);
+        // batch size: small enough that a reliable update decided on the
+        // last checked batch still lands within about half a factor delta^2
+        // of residual reduction (fast-converging systems get short batches)
+        int nb = kCgBatch;
+        if (mixed && rate > 0.0 && rate < 1.0) {
+          const double per_delta = std::log(delta2) / std::log(rate);
+          nb = per_delta >= 16.0 ? 8 : (per_delta >= 8.0 ? 4 : (per_delta >= 4.0 ? 2 : 1));
+        }
+        nb = std::min(nb, maxiter - queued);
         if ((s = cg_batch(U, nb)) != FG_OK) return s;
         queued += nb;
         const int slot = (pending + 1) & 1;
@@ -774,6 +797,14 @@ class Backend final : public IBackend {
         if (pending >= 0) {
           // wait for the batch before this one; the GPU keeps working on this one
           if (cudaEventSynchronize(ev_[pending]) != cudaSuccess) return cuda_fail("event sync");
+          if (bb < 0.0) {
+            know_bb();
+            maxrr = bb;
+            if (bb == 0.0) {            // b = 0: x = 0, nothing to iterate
+              if ((s = sync()) != FG_OK) return s;
+              return FG_OK;
+            }
+          }
           const int upto = *(volatile int*)&mapped_->dev_iter;
           const int first = checked + 1;
           double first_rr = -1.0, last = -1.0;
@@ -791,7 +822,7 @@ class Backend final : public IBackend {
             // convergence rate just seen, so the update is not late
             double predicted = last;
             if (first_rr > 0.0 && upto > first && last < first_rr) {
-              const double rate = std::pow(last / first_rr, 1.0 / (upto - first));
+              rate = std::pow(last / first_rr, 1.0 / (upto - first));
               predicted = last * std::pow(rate, queued - upto);
             }
             if (predicted < delta2 * maxrr) {
