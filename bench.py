@@ -78,6 +78,9 @@ def parse():
     ap.add_argument("--no-fermion", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--fermion-dims", default="16,16,16,32")
+    ap.add_argument("--compare-steps", type=int, default=20)
     return ap.parse_args()
 
 
@@ -241,9 +244,9 @@ DSLASH_BYTES_FP32_18 = 8 * 96 + 8 * 72 + 96
 DSLASH_FLOP = 1320
 
 
-def fermion_measurement(fg, stream, rank, hbm_peak):
-    """CG on the 16^3 x 32 Nf=2 workload; returns a dict for the JSON line."""
-    dims = (16, 16, 16, 32)
+def fermion_measurement(fg, stream, rank, hbm_peak, dims=(16, 16, 16, 32)):
+    """CG on the Nf=2 workload (16^3 x 32 by default); returns a dict for the JSON line."""
+    dims = tuple(dims)
     gauge = fg.Lattice(dims, 5.6, precision="fp32", seed=300 + rank, stream=stream)
     gauge.set_gauge(inputs.hot_start(dims, 3 + rank))
     for _ in range(10):
@@ -279,8 +282,8 @@ def fermion_measurement(fg, stream, rank, hbm_peak):
     avg = ds_ms / 1000.0 / max(ds_n, 1)
     achieved = DSLASH_BYTES_FP32_18 * vh / avg / 1e9
     return {
-        "workload": "Nf=2 Wilson 16^3x32, beta=5.6, kappa=0.158, even-odd CG on Mhat^dag Mhat to 1e-10 "
-                    "(FP32 inner, FP64 reliable updates), gauge field: hot start + 50 FG trajectories",
+        "workload": f"Nf=2 Wilson {dims[0]}^3x{dims[3]}, beta=5.6, kappa=0.158, even-odd CG on Mhat^dag Mhat "
+                    "to 1e-10 (FP32 inner, FP64 reliable updates), gauge field: hot start + 50 FG trajectories",
         "plaquette": plaq, "cg_iterations_per_solve": iters / solves, "reliable_updates_per_solve": ru / solves,
         "true_residual_max": res, "ms_per_solve": 1000 * wall / solves,
         "us_per_cg_iteration": 1e6 * wall / max(iters, 1),
@@ -478,6 +481,26 @@ def run_ours(args):
             "algorithmic_gbs": bytes_per_launch / avg_launch_s / 1e9,
             "share_of_step": force_ms / elapsed_ms}
 
+    # ---------------------------------------------------------------- FG vs Omelyan at matched acceptance
+    # Section 5 compares integrators at equal acceptance; on this chain: FG at
+    # the configured dt and at dt/2, Omelyan at the configured 0.125 and 1/16.
+    comparison = None
+    if not args.no_compare:
+        comparison = {}
+        for name, integ, dt in [("fg_dt_0.25", "fg", 0.25), ("fg_dt_0.125", "fg", 0.125),
+                                ("omelyan_dt_0.125", "omelyan", 0.125), ("omelyan_dt_0.0625", "omelyan", 0.0625)]:
+            for _ in range(2):
+                lat.trajectory(integ, dt, TAU, refresh=True, u_accept=-1.0)
+            torch.cuda.synchronize()
+            c0 = time.perf_counter()
+            rs = [lat.trajectory(integ, dt, TAU, refresh=True, u_accept=-1.0) for _ in range(args.compare_steps)]
+            torch.cuda.synchronize()
+            secs = time.perf_counter() - c0
+            acc = float(np.mean([r["accepted"] for r in rs]))
+            comparison[name] = {"dt": dt, "forces_per_trajectory": rs[0]["n_force"], "acceptance": acc,
+                                "mean_dH": float(np.mean([r["dH"] for r in rs])),
+                                "trajectories_per_s": len(rs) / secs, "accepted_per_s": acc * len(rs) / secs}
+
     # ---------------------------------------------------------------- e2e through host buffers
     e2e = None
     if not args.no_e2e:
@@ -508,7 +531,8 @@ def run_ours(args):
 
     ferm = None
     if not args.no_fermion:
-        ferm = fermion_measurement(fg, stream.cuda_stream, rank, hbm_peak())
+        ferm = fermion_measurement(fg, stream.cuda_stream, rank, hbm_peak(),
+                                   tuple(int(x) for x in args.fermion_dims.split(",")))
     batched = None
     if not args.no_batch:
         batched = batched_measurement(fg, stream.cuda_stream, rank)
@@ -530,7 +554,7 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
                 "config": cfg, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fermion": ferm,
-                "batched_chains": batched, "serving": served,
+                "batched_chains": batched, "serving": served, "integrator_comparison": comparison,
                 "gpu_launches": launches, "clocks": clk}
         print(json.dumps(line), flush=True)
     lat.close()
