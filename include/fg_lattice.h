@@ -104,7 +104,7 @@ typedef struct {
   double cg_tol_action;    /* the same for the action solve at trajectory end (1e-12) */
   int cg_maxiter;          /* CG iteration cap (default 20000) */
   double cg_delta;         /* FP32 inner CG: reliable update when the iterated residual
-                              falls by this factor (default 0.1) */
+                              |r| falls by this factor (default 0.01) */
   unsigned long long seed; /* device momentum / pseudofermion RNG and host accept RNG */
   void *cuda_stream;       /* cudaStream_t to run on; NULL => the handle creates one */
 } fg_params;
@@ -215,8 +215,11 @@ fg_status fg_reunitarize(fg_lattice *h);
  * every launch of the named kernel class is bracketed by events;
  * fg_kernel_time synchronises and returns the summed device time and the
  * number of launches since the last reset.  Classes: "gauge_force",
- * "drift", "energy", "reduce", "momenta", "dslash", "cg_blas",
- * "fermion_force", "convert". */
+ * "drift", "energy", "reduce", "momenta", "dslash" (Dslash in the inner
+ * precision), "cg_blas", "fermion_force", "convert", "dslash_fp64" (the
+ * FP64-arithmetic Dslash of the heat bath, of fg_apply_mhat and of the
+ * reliable update that certifies convergence), "dslash_df" (the
+ * double-float Dslash of the FP32 solver's other reliable updates). */
 fg_status fg_timing_enable(fg_lattice *h, int on);
 fg_status fg_timing_reset(fg_lattice *h);
 fg_status fg_kernel_time(fg_lattice *h, const char *kernel_class, double *total_ms,

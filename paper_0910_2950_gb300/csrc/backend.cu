@@ -14,6 +14,7 @@
 #include <utility>
 #include <vector>
 
+#include "df64.cuh"
 #include "fg_common.cuh"
 #include "fg_fermion.h"
 
@@ -293,6 +294,10 @@ class Backend final : public IBackend {
   // fermions
   void *chi64_ = nullptr, *phi64_ = nullptr, *b64_ = nullptr, *x64_ = nullptr, *r64_ = nullptr;
   void *ax64_ = nullptr, *te64_ = nullptr, *to64_ = nullptr;
+  // double-float solution and source of the FP32 solver's reliable updates
+  // (its Dslash temporaries reuse ax64_, te64_, to64_, which have the same size)
+  void *xdf_ = nullptr, *bdf_ = nullptr;
+  static constexpr bool kMixed = sizeof(R) < sizeof(double);
   void *xs_ = nullptr, *rs_ = nullptr, *p_ = nullptr, *ap_ = nullptr, *te_ = nullptr, *to_ = nullptr;
   void *Xe_ = nullptr, *Xo_ = nullptr, *Ye_ = nullptr, *Yo_ = nullptr, *FF_ = nullptr;
   CgDev* cgd_ = nullptr;
@@ -482,11 +487,16 @@ class Backend final : public IBackend {
     void** d64[] = {&chi64_, &phi64_, &b64_, &x64_, &r64_, &ax64_, &te64_, &to64_};
     for (void** p : d64)
       if ((s = alloc(p, b64)) != FG_OK) return s;
+    if (kMixed) {
+      if ((s = alloc(&xdf_, b64)) != FG_OK) return s;
+      if ((s = alloc(&bdf_, b64)) != FG_OK) return s;
+    }
     void** dR[] = {&xs_, &rs_, &p_, &ap_, &te_, &to_, &Xe_, &Xo_, &Ye_, &Yo_};
     for (void** p : dR)
       if ((s = alloc(p, bR)) != FG_OK) return s;
     if ((s = alloc(&FF_, (size_t)4 * 4 * g_.V * sizeof(C2))) != FG_OK) return s;
     if ((s = alloc((void**)&cgd_, sizeof(CgDev))) != FG_OK) return s;
+    if (cudaMemsetAsync(cgd_, 0, sizeof(CgDev), st_) != cudaSuccess) return cuda_fail("cg state init");
     if ((s = alloc((void**)&part_pap_, (dslash_blocks(g_.Vh) + 1) * sizeof(double))) != FG_OK) return s;
     if ((s = alloc((void**)&part_rr_, (vec_blocks(nvec()) + 1) * sizeof(double))) != FG_OK) return s;
     const size_t mbytes = sizeof(Mapped) + (size_t)(h_->prm.cg_maxiter + 8) * sizeof(double);
@@ -524,11 +534,11 @@ class Backend final : public IBackend {
   // FP64 arithmetic on the stored links: out = Mhat in, or Mhat^dagger in.
   fg_status apply_mhat64(void* out, const void* in, const void* U, int dag) {
     const double k2 = h_->prm.kappa * h_->prm.kappa;
-    fg_status s = run(KC_DSLASH, [&] {
+    fg_status s = run(KC_DSLASH64, [&] {
       return launch_dslash<R, NC, double>(g_, to64_, in, nullptr, nullptr, U, 1, dag, 0, 1.0, nullptr, nullptr, st_);
     });
     if (s != FG_OK) return s;
-    return run(KC_DSLASH, [&] {
+    return run(KC_DSLASH64, [&] {
       return launch_dslash<R, NC, double>(g_, out, to64_, in, nullptr, U, 0, dag, 1, -k2, nullptr, nullptr, st_);
     });
   }
@@ -536,6 +546,27 @@ class Backend final : public IBackend {
     fg_status s = apply_mhat64(te64_, in, U, 0);
     if (s != FG_OK) return s;
     return apply_mhat64(out, te64_, U, 1);
+  }
+
+  // The same in double-float arithmetic on double-float vectors (FP32 links only).
+  fg_status apply_mhat_df(void* out, const void* in, const void* U, int dag) {
+    if constexpr (kMixed) {
+      const double k2 = h_->prm.kappa * h_->prm.kappa;
+      fg_status s = run(KC_DSLASH_DF, [&] {
+        return launch_dslash<R, NC, DF>(g_, to64_, in, nullptr, nullptr, U, 1, dag, 0, 1.0, nullptr, nullptr, st_);
+      });
+      if (s != FG_OK) return s;
+      return run(KC_DSLASH_DF, [&] {
+        return launch_dslash<R, NC, DF>(g_, out, to64_, in, nullptr, U, 0, dag, 1, -k2, nullptr, nullptr, st_);
+      });
+    } else {
+      return h_->fail(FG_ESTATE, "double-float Dslash needs FP32 links");
+    }
+  }
+  fg_status apply_mdagm_df(void* out, const void* in, const void* U) {
+    fg_status s = apply_mhat_df(te64_, in, U, 0);
+    if (s != FG_OK) return s;
+    return apply_mhat_df(out, te64_, U, 1);
   }
 
   // phi = Mhat^dagger chi at the current links; S_F at the heat bath = |chi|^2.
@@ -597,20 +628,19 @@ class Backend final : public IBackend {
   cudaError_t cg_iteration_raw(const void* U) {
     const double k2 = h_->prm.kappa * h_->prm.kappa;
     const int n = nvec();
-    const int* done = &cgd_->done;
     cudaError_t e;
-    if ((e = launch_dslash<R, NC, R>(g_, to_, p_, nullptr, nullptr, U, 1, 0, 0, 1.0, nullptr, done, st_)) != cudaSuccess)
+    if ((e = launch_dslash<R, NC, R>(g_, to_, p_, nullptr, nullptr, U, 1, 0, 0, 1.0, nullptr, cgd_, st_)) != cudaSuccess)
       return e;
-    if ((e = launch_dslash<R, NC, R>(g_, te_, to_, p_, nullptr, U, 0, 0, 1, -k2, nullptr, done, st_)) != cudaSuccess)
+    if ((e = launch_dslash<R, NC, R>(g_, te_, to_, p_, nullptr, U, 0, 0, 1, -k2, nullptr, cgd_, st_)) != cudaSuccess)
       return e;
-    if ((e = launch_dslash<R, NC, R>(g_, to_, te_, nullptr, nullptr, U, 1, 1, 0, 1.0, nullptr, done, st_)) != cudaSuccess)
+    if ((e = launch_dslash<R, NC, R>(g_, to_, te_, nullptr, nullptr, U, 1, 1, 0, 1.0, nullptr, cgd_, st_)) != cudaSuccess)
       return e;
-    if ((e = launch_dslash<R, NC, R>(g_, ap_, to_, te_, p_, U, 0, 1, 2, -k2, part_pap_, done, st_)) != cudaSuccess)
+    if ((e = launch_dslash<R, NC, R>(g_, ap_, to_, te_, p_, U, 0, 1, 2, -k2, part_pap_, cgd_, st_)) != cudaSuccess)
       return e;
-    if ((e = launch_cg_axpy<R>(xs_, rs_, p_, ap_, part_pap_, dslash_blocks(g_.Vh), cgd_, part_rr_, n, st_)) !=
+    if ((e = launch_cg_axpy<R>(xs_, rs_, p_, ap_, cgd_, part_rr_, n, st_)) !=
         cudaSuccess)
       return e;
-    return launch_cg_xpay<R>(p_, rs_, part_rr_, vec_blocks(n), cgd_, mapped_->hist, &mapped_->dev_iter,
+    return launch_cg_xpay<R>(p_, rs_, cgd_, mapped_->hist, &mapped_->dev_iter,
                              h_->prm.cg_maxiter, n, st_);
   }
 
@@ -619,25 +649,24 @@ class Backend final : public IBackend {
   fg_status cg_iteration(const void* U) {
     const double k2 = h_->prm.kappa * h_->prm.kappa;
     const int n = nvec();
-    const int* done = &cgd_->done;
     fg_status s;
     if ((s = run(KC_DSLASH, [&] {
-           return launch_dslash<R, NC, R>(g_, to_, p_, nullptr, nullptr, U, 1, 0, 0, 1.0, nullptr, done, st_);
+           return launch_dslash<R, NC, R>(g_, to_, p_, nullptr, nullptr, U, 1, 0, 0, 1.0, nullptr, cgd_, st_);
          })) != FG_OK) return s;
     if ((s = run(KC_DSLASH, [&] {
-           return launch_dslash<R, NC, R>(g_, te_, to_, p_, nullptr, U, 0, 0, 1, -k2, nullptr, done, st_);
+           return launch_dslash<R, NC, R>(g_, te_, to_, p_, nullptr, U, 0, 0, 1, -k2, nullptr, cgd_, st_);
          })) != FG_OK) return s;
     if ((s = run(KC_DSLASH, [&] {
-           return launch_dslash<R, NC, R>(g_, to_, te_, nullptr, nullptr, U, 1, 1, 0, 1.0, nullptr, done, st_);
+           return launch_dslash<R, NC, R>(g_, to_, te_, nullptr, nullptr, U, 1, 1, 0, 1.0, nullptr, cgd_, st_);
          })) != FG_OK) return s;
     if ((s = run(KC_DSLASH, [&] {
-           return launch_dslash<R, NC, R>(g_, ap_, to_, te_, p_, U, 0, 1, 2, -k2, part_pap_, done, st_);
+           return launch_dslash<R, NC, R>(g_, ap_, to_, te_, p_, U, 0, 1, 2, -k2, part_pap_, cgd_, st_);
          })) != FG_OK) return s;
     if ((s = run(KC_CG_BLAS, [&] {
-           return launch_cg_axpy<R>(xs_, rs_, p_, ap_, part_pap_, dslash_blocks(g_.Vh), cgd_, part_rr_, n, st_);
+           return launch_cg_axpy<R>(xs_, rs_, p_, ap_, cgd_, part_rr_, n, st_);
          })) != FG_OK) return s;
     return run(KC_CG_BLAS, [&] {
-      return launch_cg_xpay<R>(p_, rs_, part_rr_, vec_blocks(n), cgd_, mapped_->hist, &mapped_->dev_iter,
+      return launch_cg_xpay<R>(p_, rs_, cgd_, mapped_->hist, &mapped_->dev_iter,
                                h_->prm.cg_maxiter, n, st_);
     });
   }
@@ -703,15 +732,34 @@ class Backend final : public IBackend {
     return FG_OK;
   }
 
-  // Reliable update after the last queued iteration: x64 += x_s,
-  // r64 = b - M x64 in FP64, r_s = r64, rr = |r64|^2 (also published to the host).
-  fg_status reliable_update(const void* U, const void* b64) {
+  // Reliable update after the last queued iteration: x += x_s, r = b - M x,
+  // r_s = r, rr = |r|^2 (also published to the host).  The FP64 solver keeps
+  // x in FP64.  The FP32 solver keeps x in double-float and evaluates the
+  // intermediate updates' M x in double-float arithmetic (GB300's FP64 rate
+  // is 1/64 of its FP32 rate); the final update, which certifies
+  // convergence, converts x to FP64 and applies M in FP64.
+  fg_status reliable_update(const void* U, const void* b64, bool final) {
     const int n = nvec();
     fg_status s;
-    if ((s = run(KC_CG_BLAS, [&] { return launch_ru_accumulate<R>(x64_, xs_, n, st_); })) != FG_OK) return s;
-    if ((s = apply_mdagm64(ax64_, x64_, U)) != FG_OK) return s;
-    if ((s = run(KC_CG_BLAS, [&] { return launch_ru_residual<R>(b64, ax64_, r64_, rs_, part_rr_, n, st_); })) != FG_OK)
-      return s;
+    if (kMixed) {
+      if ((s = run(KC_CG_BLAS, [&] { return launch_ru_accumulate_df(xdf_, xs_, n, st_); })) != FG_OK) return s;
+      if (!final) {
+        if ((s = apply_mdagm_df(ax64_, xdf_, U)) != FG_OK) return s;
+        if ((s = run(KC_CG_BLAS, [&] { return launch_ru_residual_df(bdf_, ax64_, rs_, part_rr_, n, st_); })) !=
+            FG_OK)
+          return s;
+      } else {
+        if ((s = run(KC_CG_BLAS, [&] { return launch_df_to_double(x64_, xdf_, n, st_); })) != FG_OK) return s;
+      }
+    } else {
+      if ((s = run(KC_CG_BLAS, [&] { return launch_ru_accumulate<R>(x64_, xs_, n, st_); })) != FG_OK) return s;
+    }
+    if (!kMixed || final) {
+      if ((s = apply_mdagm64(ax64_, x64_, U)) != FG_OK) return s;
+      if ((s = run(KC_CG_BLAS, [&] { return launch_ru_residual<R>(b64, ax64_, r64_, rs_, part_rr_, n, st_); })) !=
+          FG_OK)
+        return s;
+    }
     double* tr = &mapped_->true_rr;
     if ((s = run(KC_REDUCE, [&] { return launch_ru_publish(part_rr_, vec_blocks(n), cgd_, tr, st_); })) != FG_OK)
       return s;
@@ -738,6 +786,9 @@ class Backend final : public IBackend {
     if (cudaMemsetAsync(x64_, 0, (size_t)n * sizeof(double2), st_) != cudaSuccess ||
         cudaMemsetAsync(xs_, 0, (size_t)n * sizeof(C2), st_) != cudaSuccess ||
         cudaMemcpyAsync(r64_, b64, (size_t)n * sizeof(double2), cudaMemcpyDeviceToDevice, st_) != cudaSuccess)
+      return cuda_fail("cg setup");
+    if (kMixed && (cudaMemsetAsync(xdf_, 0, (size_t)n * sizeof(double2), st_) != cudaSuccess ||
+                   run(KC_CG_BLAS, [&] { return launch_df_from_double(bdf_, b64, n, st_); }) != FG_OK))
       return cuda_fail("cg setup");
     if ((s = run(KC_CG_BLAS, [&] { return launch_convert<R, double>(rs_, b64, part_rr_, n, st_); })) != FG_OK) return s;
     double* bbp = &mapped_->bb;
@@ -828,7 +879,7 @@ class Backend final : public IBackend {
             if (predicted < delta2 * maxrr) {
               CG_TRACE("cg reliable update after queued %d (last %.3e predicted %.3e)\n", queued, last / bb,
                        predicted / bb);
-              if ((s = reliable_update(U, b64)) != FG_OK) return s;
+              if ((s = reliable_update(U, b64, false)) != FG_OK) return s;
               ++st->nru;
               maxrr = predicted;
             }
@@ -836,7 +887,7 @@ class Backend final : public IBackend {
         }
         pending = slot;
       }
-      if ((s = reliable_update(U, b64)) != FG_OK) return s;
+      if ((s = reliable_update(U, b64, true)) != FG_OK) return s;
       ++st->nru;
       if ((s = sync()) != FG_OK) return s;
       const double trr = mapped_->true_rr;

@@ -15,6 +15,7 @@
 // spin blocks with A_x = [[0, i], [i, 0]], A_y = [[0, -1], [1, 0]],
 // A_z = diag(i, -i), A_t = 1, so g5 = diag(1, 1, -1, -1) and
 // (1 - s g_mu) psi = (h, -s A_mu^dagger h) with h = psi_up - s A_mu psi_down.
+#include "df64.cuh"
 #include "fg_common.cuh"
 #include "fg_fermion.h"
 #include "fg_kernels.h"
@@ -80,16 +81,22 @@ __device__ __forceinline__ void project(const Spinor<R>& p, Cx<R> h[2][3]) {
   }
 }
 
+// (b0, b1) = A_mu^dagger (w0, w1)
+template <int MU, typename R>
+__device__ __forceinline__ void adag_mu(const Cx<R>& w0, const Cx<R>& w1, Cx<R>& b0, Cx<R>& b1) {
+  if (MU == 0) { b0 = cx<R>(w1.im, -w1.re); b1 = cx<R>(w0.im, -w0.re); }
+  if (MU == 1) { b0 = w1; b1 = cx<R>(-w0.re, -w0.im); }
+  if (MU == 2) { b0 = cx<R>(w0.im, -w0.re); b1 = times_i(w1); }
+  if (MU == 3) { b0 = w0; b1 = w1; }
+}
+
 // acc_up += sign * w, acc_down += sign * (-S) A_mu^dagger w
 template <int MU, int S, typename R>
 __device__ __forceinline__ void reconstruct_add(Spinor<R>& acc, const Cx<R> w[2][3], R sign) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    Cx<R> b0, b1;  // (A_mu^dagger w)_0, _1
-    if (MU == 0) { b0 = cx<R>(w[1][c].im, -w[1][c].re); b1 = cx<R>(w[0][c].im, -w[0][c].re); }
-    if (MU == 1) { b0 = w[1][c]; b1 = cx<R>(-w[0][c].re, -w[0][c].im); }
-    if (MU == 2) { b0 = cx<R>(w[0][c].im, -w[0][c].re); b1 = times_i(w[1][c]); }
-    if (MU == 3) { b0 = w[0][c]; b1 = w[1][c]; }
+    Cx<R> b0, b1;
+    adag_mu<MU>(w[0][c], w[1][c], b0, b1);
     const R sd = (S > 0) ? -sign : sign;
     acc.s[0][c] = acc.s[0][c] + sign * w[0][c];
     acc.s[1][c] = acc.s[1][c] + sign * w[1][c];
@@ -113,6 +120,66 @@ __device__ __forceinline__ void mat_half(const M3<R>& u, const Cx<R> h[2][3], Cx
       }
       w[k][a] = s;
     }
+}
+
+// Double-float versions of the two inner steps.  The links are FP32, so a
+// product of a double-float half-spinor entry h and a link entry u is the
+// exact pair (fl(h.hi u), its error) plus h.lo u; the six products of each
+// output component are summed with two_sum on the high parts and the error
+// terms collected in FP32 (a compensated dot product, Ogita, Rump and
+// Oishi 2005), normalised once at the end.
+struct DfAcc {
+  float s, c;
+};
+__device__ __forceinline__ void dfacc_add(DfAcc& a, DF h, float u) {
+  const float p = __fmul_rn(h.hi, u);
+  float e = __fmaf_rn(h.hi, u, -p);
+  e = __fmaf_rn(h.lo, u, e);
+  const DF t = df_two_sum(a.s, p);
+  a.s = t.hi;
+  a.c = __fadd_rn(a.c, __fadd_rn(t.lo, e));
+}
+template <int ADJ>
+__device__ __forceinline__ void mat_half(const M3<DF>& u, const Cx<DF> h[2][3], Cx<DF> w[2][3]) {
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      DfAcc re = {0.0f, 0.0f}, im = {0.0f, 0.0f};
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        // u_ab h_b, or conj(u_ba) h_b
+        const float ur = ADJ ? u.e[b][a].re.hi : u.e[a][b].re.hi;
+        const float ui = ADJ ? -u.e[b][a].im.hi : u.e[a][b].im.hi;
+        dfacc_add(re, h[k][b].re, ur);
+        dfacc_add(re, h[k][b].im, -ui);
+        dfacc_add(im, h[k][b].im, ur);
+        dfacc_add(im, h[k][b].re, ui);
+      }
+      w[k][a] = cx<DF>(df_fast_two_sum(re.s, re.c), df_fast_two_sum(im.s, im.c));
+    }
+}
+// The same reconstruction with sign = +-1 applied exactly (no double-float product).
+__device__ __forceinline__ Cx<DF> df_scale_sign(const Cx<DF>& w, float sg) {
+  return cx<DF>(DF(sg * w.re.hi, sg * w.re.lo), DF(sg * w.im.hi, sg * w.im.lo));
+}
+template <int MU, int S>
+__device__ __forceinline__ void reconstruct_add(Spinor<DF>& acc, const Cx<DF> w[2][3], DF sign) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const Cx<DF> w0 = df_scale_sign(w[0][c], sign.hi), w1 = df_scale_sign(w[1][c], sign.hi);
+    Cx<DF> b0, b1;
+    adag_mu<MU>(w0, w1, b0, b1);
+    acc.s[0][c] = acc.s[0][c] + w0;
+    acc.s[1][c] = acc.s[1][c] + w1;
+    if (S > 0) {
+      acc.s[2][c] = acc.s[2][c] - b0;
+      acc.s[3][c] = acc.s[3][c] - b1;
+    } else {
+      acc.s[2][c] = acc.s[2][c] + b0;
+      acc.s[3][c] = acc.s[3][c] + b1;
+    }
+  }
 }
 
 template <int MU, int DAG, typename RL, int NC, typename RS>
@@ -147,14 +214,22 @@ constexpr int kDslashThreads = 128;
 
 // out = b D in (MODE 0), out = x + b D in (MODE 1), and MODE 2 also writes the
 // block partial sum of Re <pdot, out>.  `in` has parity 1 - out_par.
+// Resident blocks asked of the register allocator: the double-float hop is
+// latency-bound, so it is held to 128 registers for four blocks per SM.
+template <typename RS> struct DslashMinBlocks { static constexpr int value = 1; };
+#ifndef FG_DSLASH_DF_MIN_BLOCKS
+#define FG_DSLASH_DF_MIN_BLOCKS 4
+#endif
+template <> struct DslashMinBlocks<DF> { static constexpr int value = FG_DSLASH_DF_MIN_BLOCKS; };
+
 template <typename RL, int NC, typename RS, int DAG, int MODE>
-__global__ void __launch_bounds__(kDslashThreads) dslash_kernel(
+__global__ void __launch_bounds__(kDslashThreads, DslashMinBlocks<RS>::value) dslash_kernel(
     typename Vec2<RS>::T* __restrict__ out, const typename Vec2<RS>::T* __restrict__ in,
     const typename Vec2<RS>::T* __restrict__ x, const typename Vec2<RS>::T* __restrict__ pdot,
-    Gauge<RL, NC> U, Geom g, int out_par, RS b, double* __restrict__ partial, const int* __restrict__ done) {
-  if (done != nullptr && *done) return;
+    Gauge<RL, NC> U, Geom g, int out_par, RS b, double* __restrict__ partial, CgDev* __restrict__ cgd) {
+  if (cgd != nullptr && cgd->done) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double dot = 0.0;
+  RS dot = RS(0);  // one site's 24 terms in the spinor precision (GB300's FP64 unit is slow)
   if (i < g.Vh) {
     const int s = out_par * g.Vh + i;
     int c[4], par;
@@ -187,15 +262,12 @@ __global__ void __launch_bounds__(kDslashThreads) dslash_kernel(
         for (int k = 0; k < 4; ++k)
 #pragma unroll
           for (int cc = 0; cc < 3; ++cc)
-            dot += double(pv.s[k][cc].re) * o.s[k][cc].re + double(pv.s[k][cc].im) * o.s[k][cc].im;
+            dot += pv.s[k][cc].re * o.s[k][cc].re + pv.s[k][cc].im * o.s[k][cc].im;
       }
     }
     store_spinor<RS>(out, i, g.Vh, o);
   }
-  if (MODE == 2) {
-    double v[1] = {dot};
-    block_reduce_store<1>(v, partial, gridDim.x);
-  }
+  if (MODE == 2) block_reduce_total(double(dot), partial, &cgd->ticket[0], &cgd->pap);
 }
 
 // --------------------------------------------------------------------------- force
@@ -289,23 +361,22 @@ __device__ __forceinline__ double block_sum_partials(const double* __restrict__ 
 }
 
 // Iteration k = iter + 1 (iter was published by the previous iteration's
-// xpay kernel): alpha = rr[(k-1)&1] / sum(pAp partials); x += alpha p;
-// r -= alpha Ap; partial |r|^2.  Block 0 passes k on to xpay through k_axpy.
+// xpay kernel): alpha = rr[(k-1)&1] / pAp; x += alpha p; r -= alpha Ap;
+// |r|^2 into cgd->rr_next.  Block 0 passes k on to xpay through k_axpy.
 // The kernels take no iteration argument, so a batch of iterations can be
 // captured once in a CUDA graph and replayed.
 template <typename R>
 __global__ void __launch_bounds__(kVecThreads) cg_axpy_kernel(
     typename Vec2<R>::T* __restrict__ x, typename Vec2<R>::T* __restrict__ r,
     const typename Vec2<R>::T* __restrict__ p, const typename Vec2<R>::T* __restrict__ ap,
-    const double* __restrict__ pap_part, int npap, CgDev* __restrict__ cgd,
-    double* __restrict__ rr_part, int n) {
+    CgDev* __restrict__ cgd, double* __restrict__ rr_part, int n) {
   if (cgd->done) return;
   const int k = cgd->iter + 1;
-  const double pap = block_sum_partials(pap_part, npap);
+  const double pap = cgd->pap;
   const double rr = cgd->rr[(k - 1) & 1];
   const double alpha = pap > 0.0 ? rr / pap : 0.0;
   const R a = R(alpha);
-  double acc = 0.0;
+  R acc = R(0);  // a thread's few entries in R; blocks and the total in FP64
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     typename Vec2<R>::T xv = x[i], rv = r[i];
     const typename Vec2<R>::T pv = p[i], av = ap[i];
@@ -313,17 +384,17 @@ __global__ void __launch_bounds__(kVecThreads) cg_axpy_kernel(
     rv.x = fma(-a, av.x, rv.x); rv.y = fma(-a, av.y, rv.y);
     x[i] = xv;
     r[i] = rv;
-    acc += double(rv.x) * rv.x + double(rv.y) * rv.y;
+    acc = fma(rv.x, rv.x, acc);
+    acc = fma(rv.y, rv.y, acc);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     cgd->alpha = alpha;
     cgd->k_axpy = k;
   }
-  double v[1] = {acc};
-  block_reduce_store<1>(v, rr_part, gridDim.x);
+  block_reduce_total(double(acc), rr_part, &cgd->ticket[1], &cgd->rr_next);
 }
 
-// rr_new = sum(rr partials); done if rr_new <= tol2 bb; beta = rr_new / rr_old;
+// rr_new = cgd->rr_next; done if rr_new <= tol2 bb; beta = rr_new / rr_old;
 // p = r + beta p (also on the converging iteration, so that a reliable update
 // that finds the true residual still too large can simply continue).
 // Block 0 publishes rr[k&1], the history entry, iter = k (also to the host
@@ -331,11 +402,10 @@ __global__ void __launch_bounds__(kVecThreads) cg_axpy_kernel(
 template <typename R>
 __global__ void __launch_bounds__(kVecThreads) cg_xpay_kernel(
     typename Vec2<R>::T* __restrict__ p, const typename Vec2<R>::T* __restrict__ r,
-    const double* __restrict__ rr_part, int nrr, CgDev* __restrict__ cgd,
-    double* __restrict__ hist, int* __restrict__ iter_out, int maxiter, int n) {
+    CgDev* __restrict__ cgd, double* __restrict__ hist, int* __restrict__ iter_out, int maxiter, int n) {
   if (cgd->done) return;
   const int k = cgd->k_axpy;
-  const double rr_new = block_sum_partials(rr_part, nrr);
+  const double rr_new = cgd->rr_next;
   const double rr_old = cgd->rr[(k - 1) & 1];
   const bool conv = rr_new <= cgd->tol2bb;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -393,6 +463,54 @@ __global__ void __launch_bounds__(kVecThreads) ru_residual_kernel(const double2*
   }
   double v[1] = {acc};
   block_reduce_store<1>(v, part, gridDim.x);
+}
+
+// Double-float reliable update (FP32 inner solver), first half:
+// x += x_s in double-float; x_s = 0.
+__global__ void __launch_bounds__(kVecThreads) ru_accumulate_df_kernel(float4* __restrict__ x,
+                                                                       float2* __restrict__ xs, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float2 v = xs[i];
+    float4 a = x[i];
+    const DF re = df_add_f(DF(a.x, a.y), v.x), im = df_add_f(DF(a.z, a.w), v.y);
+    x[i] = make_float4(re.hi, re.lo, im.hi, im.lo);
+    xs[i] = make_float2(0.0f, 0.0f);
+  }
+}
+
+// Second half: r = b - Ax in double-float, r_s = (float) r, |r|^2 from the
+// rounded r_s (a thread's entries in FP32, blocks in FP64).
+__global__ void __launch_bounds__(kVecThreads) ru_residual_df_kernel(const float4* __restrict__ b,
+                                                                     const float4* __restrict__ ax,
+                                                                     float2* __restrict__ rs,
+                                                                     double* __restrict__ part, int n) {
+  float acc = 0.0f;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float4 bv = b[i], av = ax[i];
+    const DF re = DF(bv.x, bv.y) - DF(av.x, av.y), im = DF(bv.z, bv.w) - DF(av.z, av.w);
+    rs[i] = make_float2(re.hi, im.hi);
+    acc = fmaf(re.hi, re.hi, acc);
+    acc = fmaf(im.hi, im.hi, acc);
+  }
+  double v[1] = {double(acc)};
+  block_reduce_store<1>(v, part, gridDim.x);
+}
+
+// FP64 <-> double-float vectors (n complex entries).
+__global__ void __launch_bounds__(kVecThreads) df_from_double_kernel(float4* __restrict__ dst,
+                                                                     const double2* __restrict__ src, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double2 v = src[i];
+    const DF re(v.x), im(v.y);
+    dst[i] = make_float4(re.hi, re.lo, im.hi, im.lo);
+  }
+}
+__global__ void __launch_bounds__(kVecThreads) df_to_double_kernel(double2* __restrict__ dst,
+                                                                   const float4* __restrict__ src, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float4 v = src[i];
+    dst[i] = make_double2(double(DF(v.x, v.y)), double(DF(v.z, v.w)));
+  }
 }
 
 // Publishes a reliable-update residual after iteration k = iter:
@@ -531,7 +649,7 @@ int dslash_blocks(int Vh) { return (Vh + kDslashThreads - 1) / kDslashThreads; }
 template <typename RL, int NC, typename RS>
 cudaError_t launch_dslash(const GeomH& gh, void* out, const void* in, const void* x, const void* pdot,
                           const void* U, int out_par, int dag, int mode, double b, double* partial,
-                          const int* done, cudaStream_t st) {
+                          CgDev* cgd, cudaStream_t st) {
   Gauge<RL, NC> u;
   u.p = const_cast<void*>(U);
   u.V = gh.V;
@@ -540,7 +658,7 @@ cudaError_t launch_dslash(const GeomH& gh, void* out, const void* in, const void
 #define FG_DS(D, M)                                                                                     \
   dslash_kernel<RL, NC, RS, D, M><<<nb, kDslashThreads, 0, st>>>(v2<RS>(out), cv2<RS>(in), cv2<RS>(x),   \
                                                                  cv2<RS>(pdot), u, g, out_par, RS(b),   \
-                                                                 partial, done)
+                                                                 partial, cgd)
   if (dag) {
     if (mode == 0) FG_DS(1, 0); else if (mode == 1) FG_DS(1, 1); else FG_DS(1, 2);
   } else {
@@ -565,17 +683,16 @@ cudaError_t launch_fermion_force(const GeomH& gh, const void* U, const void* Xe,
 }
 
 template <typename R>
-cudaError_t launch_cg_axpy(void* x, void* r, const void* p, const void* ap, const double* pap_part, int npap,
-                           CgDev* cgd, double* rr_part, int n, cudaStream_t st) {
-  cg_axpy_kernel<R><<<vec_blocks(n), kVecThreads, 0, st>>>(v2<R>(x), v2<R>(r), cv2<R>(p), cv2<R>(ap), pap_part,
-                                                           npap, cgd, rr_part, n);
+cudaError_t launch_cg_axpy(void* x, void* r, const void* p, const void* ap, CgDev* cgd, double* rr_part, int n,
+                           cudaStream_t st) {
+  cg_axpy_kernel<R><<<vec_blocks(n), kVecThreads, 0, st>>>(v2<R>(x), v2<R>(r), cv2<R>(p), cv2<R>(ap), cgd,
+                                                           rr_part, n);
   return cudaGetLastError();
 }
 template <typename R>
-cudaError_t launch_cg_xpay(void* p, const void* r, const double* rr_part, int nrr, CgDev* cgd, double* hist,
-                           int* iter_out, int maxiter, int n, cudaStream_t st) {
-  cg_xpay_kernel<R><<<vec_blocks(n), kVecThreads, 0, st>>>(v2<R>(p), cv2<R>(r), rr_part, nrr, cgd, hist,
-                                                           iter_out, maxiter, n);
+cudaError_t launch_cg_xpay(void* p, const void* r, CgDev* cgd, double* hist, int* iter_out, int maxiter, int n,
+                           cudaStream_t st) {
+  cg_xpay_kernel<R><<<vec_blocks(n), kVecThreads, 0, st>>>(v2<R>(p), cv2<R>(r), cgd, hist, iter_out, maxiter, n);
   return cudaGetLastError();
 }
 template <typename RI>
@@ -608,6 +725,24 @@ cudaError_t launch_convert(void* dst, const void* src, double* part, int n, cuda
   convert_kernel<RO, RI><<<vec_blocks(n), kVecThreads, 0, st>>>(v2<RO>(dst), cv2<RI>(src), part, n);
   return cudaGetLastError();
 }
+cudaError_t launch_ru_accumulate_df(void* xdf, void* xs, int n, cudaStream_t st) {
+  ru_accumulate_df_kernel<<<vec_blocks(n), kVecThreads, 0, st>>>((float4*)xdf, (float2*)xs, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_ru_residual_df(const void* bdf, const void* axdf, void* rs, double* part, int n,
+                                  cudaStream_t st) {
+  ru_residual_df_kernel<<<vec_blocks(n), kVecThreads, 0, st>>>((const float4*)bdf, (const float4*)axdf,
+                                                                (float2*)rs, part, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_df_from_double(void* dst, const void* src, int n, cudaStream_t st) {
+  df_from_double_kernel<<<vec_blocks(n), kVecThreads, 0, st>>>((float4*)dst, (const double2*)src, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_df_to_double(void* dst, const void* src, int n, cudaStream_t st) {
+  df_to_double_kernel<<<vec_blocks(n), kVecThreads, 0, st>>>((double2*)dst, (const float4*)src, n);
+  return cudaGetLastError();
+}
 cudaError_t launch_dot64(const void* a, const void* b, double* part, int n, cudaStream_t st) {
   dot64_kernel<<<vec_blocks(n), kVecThreads, 0, st>>>((const double2*)a, (const double2*)b, part, n);
   return cudaGetLastError();
@@ -631,7 +766,7 @@ cudaError_t launch_spinor_to_canon(const void* f, double* canon, int Vh, cudaStr
 
 #define FG_INST_F(RL, NC, RS)                                                                                  \
   template cudaError_t launch_dslash<RL, NC, RS>(const GeomH&, void*, const void*, const void*, const void*,  \
-                                                 const void*, int, int, int, double, double*, const int*,     \
+                                                 const void*, int, int, int, double, double*, CgDev*,        \
                                                  cudaStream_t);                                               \
   template cudaError_t launch_fermion_force<RL, NC, RS>(const GeomH&, const void*, const void*, const void*,  \
                                                         const void*, const void*, void*, double, int,         \
@@ -642,15 +777,17 @@ FG_INST_F(float, 9, float)
 FG_INST_F(float, 6, float)
 FG_INST_F(float, 9, double)
 FG_INST_F(float, 6, double)
+template cudaError_t launch_dslash<float, 9, DF>(const GeomH&, void*, const void*, const void*, const void*,
+                                                 const void*, int, int, int, double, double*, CgDev*, cudaStream_t);
+template cudaError_t launch_dslash<float, 6, DF>(const GeomH&, void*, const void*, const void*, const void*,
+                                                 const void*, int, int, int, double, double*, CgDev*, cudaStream_t);
 
-template cudaError_t launch_cg_axpy<double>(void*, void*, const void*, const void*, const double*, int, CgDev*,
-                                            double*, int, cudaStream_t);
-template cudaError_t launch_cg_axpy<float>(void*, void*, const void*, const void*, const double*, int, CgDev*,
-                                           double*, int, cudaStream_t);
-template cudaError_t launch_cg_xpay<double>(void*, const void*, const double*, int, CgDev*, double*, int*, int,
-                                            int, cudaStream_t);
-template cudaError_t launch_cg_xpay<float>(void*, const void*, const double*, int, CgDev*, double*, int*, int, int,
+template cudaError_t launch_cg_axpy<double>(void*, void*, const void*, const void*, CgDev*, double*, int,
+                                            cudaStream_t);
+template cudaError_t launch_cg_axpy<float>(void*, void*, const void*, const void*, CgDev*, double*, int,
                                            cudaStream_t);
+template cudaError_t launch_cg_xpay<double>(void*, const void*, CgDev*, double*, int*, int, int, cudaStream_t);
+template cudaError_t launch_cg_xpay<float>(void*, const void*, CgDev*, double*, int*, int, int, cudaStream_t);
 template cudaError_t launch_cg_restart<double>(void*, const void*, const CgDev*, int, cudaStream_t);
 template cudaError_t launch_cg_restart<float>(void*, const void*, const CgDev*, int, cudaStream_t);
 template cudaError_t launch_ru_accumulate<double>(void*, void*, int, cudaStream_t);

@@ -520,4 +520,47 @@ __device__ __forceinline__ void block_reduce_store(double v[NV], double* __restr
   }
 }
 
+// block_reduce_store<1> followed by a grand total: the last block to finish
+// (counted on *ticket, which it resets to 0 for the next launch) sums the
+// partials in block order and writes *total, so the sum is deterministic and
+// the next kernel reads one scalar.  Every block of the launch must call it.
+__device__ __forceinline__ void block_reduce_total(double v, double* __restrict__ partial,
+                                                   unsigned* __restrict__ ticket, double* __restrict__ total) {
+  double vv[1] = {v};
+  block_reduce_store<1>(vv, partial, gridDim.x);
+  __shared__ int last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  // each thread's partials in block order; four loads in flight at a time
+  double x = 0.0;
+  const int n = gridDim.x, bd = blockDim.x;
+  int i = threadIdx.x;
+  for (; i + 3 * bd < n; i += 4 * bd) {
+    const double a = __ldcg(partial + i), b = __ldcg(partial + i + bd);
+    const double c = __ldcg(partial + i + 2 * bd), d = __ldcg(partial + i + 3 * bd);
+    x += a;
+    x += b;
+    x += c;
+    x += d;
+  }
+  for (; i < n; i += bd) x += __ldcg(partial + i);
+  __shared__ double sh[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) sh[warp] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) t += sh[w];
+    *total = t;
+    *ticket = 0u;
+  }
+}
+
 }  // namespace fg

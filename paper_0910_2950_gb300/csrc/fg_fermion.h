@@ -22,20 +22,26 @@ struct CgDev {
   int iter;     // last completed iteration (written by xpay's block 0)
   int k_axpy;   // iteration in progress (written by axpy's block 0)
   int restart;  // set by a reliable update whose true residual left the recursion far behind
+  double pap;       // <p, Ap> of the iteration in progress (grand total of the Dslash partials)
+  double rr_next;   // |r|^2 after the iteration in progress (grand total of the axpy partials)
+  unsigned ticket[2];  // blocks finished, for the two grand totals; the last block resets it to 0
 };
 
 int vec_blocks(int n);
 int dslash_blocks(int Vh);
 
-// out = b D in (mode 0); out = x + b D in (mode 1); mode 2 also writes block
-// partials of Re <pdot, out>.  D hops from parity 1-out_par to out_par;
-// dag = 1 applies g5 D g5.  Links stored as RL with NC complex entries,
-// spinors and arithmetic in RS.  If `done` is non-null and *done != 0 the
-// kernel returns at once (converged CG).
+// RS = DF (df64.cuh) evaluates the hop in double-float arithmetic on FP32
+// links; it is instantiated for RL = float, modes 0 and 1 only.
+// out = b D in (mode 0); out = x + b D in (mode 1); mode 2 (CG only) also
+// sums Re <pdot, out> into cgd->pap through the block partials `partial`.
+// D hops from parity 1-out_par to out_par; dag = 1 applies g5 D g5.  Links
+// stored as RL with NC complex entries, spinors and arithmetic in RS.  If
+// `cgd` is non-null and cgd->done != 0 the kernel returns at once (converged
+// CG).
 template <typename RL, int NC, typename RS>
 cudaError_t launch_dslash(const GeomH& g, void* out, const void* in, const void* x, const void* pdot,
                           const void* U, int out_par, int dag, int mode, double b, double* partial,
-                          const int* done, cudaStream_t st);
+                          CgDev* cgd, cudaStream_t st);
 
 // Pseudofermion force (8 Gell-Mann components per link) into FF (momentum
 // layout, precision RL); accumulate != 0 adds to FF.
@@ -43,18 +49,29 @@ template <typename RL, int NC, typename RS>
 cudaError_t launch_fermion_force(const GeomH& g, const void* U, const void* Xe, const void* Xo, const void* Ye,
                                  const void* Yo, void* FF, double kappa2, int accumulate, cudaStream_t st);
 
+// x += alpha p, r -= alpha Ap with alpha = rr / cgd->pap; |r|^2 into
+// cgd->rr_next through the block partials rr_part.
 template <typename R>
-cudaError_t launch_cg_axpy(void* x, void* r, const void* p, const void* ap, const double* pap_part, int npap,
-                           CgDev* cgd, double* rr_part, int n, cudaStream_t st);
-// hist[k] receives |r_k|^2 for k <= maxiter and *iter_out the iteration k.
+cudaError_t launch_cg_axpy(void* x, void* r, const void* p, const void* ap, CgDev* cgd, double* rr_part, int n,
+                           cudaStream_t st);
+// p = r + beta p with beta = cgd->rr_next / rr; hist[k] receives |r_k|^2 for
+// k <= maxiter and *iter_out the iteration k.
 template <typename R>
-cudaError_t launch_cg_xpay(void* p, const void* r, const double* rr_part, int nrr, CgDev* cgd, double* hist,
-                           int* iter_out, int maxiter, int n, cudaStream_t st);
+cudaError_t launch_cg_xpay(void* p, const void* r, CgDev* cgd, double* hist, int* iter_out, int maxiter, int n,
+                           cudaStream_t st);
 template <typename RI>
 cudaError_t launch_ru_accumulate(void* x64, void* xs, int n, cudaStream_t st);
 template <typename RI>
 cudaError_t launch_ru_residual(const void* b64, const void* ax64, void* r64, void* rs, double* part, int n,
                                cudaStream_t st);
+// Double-float reliable update for the FP32 solver (vectors of float4 =
+// one complex double-float, x_s and r_s float2): x += x_s, x_s = 0;
+// r_s = (float)(b - Ax) with partials of |r_s|^2; conversions to and from FP64.
+cudaError_t launch_ru_accumulate_df(void* xdf, void* xs, int n, cudaStream_t st);
+cudaError_t launch_ru_residual_df(const void* bdf, const void* axdf, void* rs, double* part, int n,
+                                  cudaStream_t st);
+cudaError_t launch_df_from_double(void* dst, const void* src, int n, cudaStream_t st);
+cudaError_t launch_df_to_double(void* dst, const void* src, int n, cudaStream_t st);
 cudaError_t launch_ru_publish(const double* part, int n, CgDev* cgd, double* true_rr, cudaStream_t st);
 // p = r when the last reliable update asked for a restart (cgd->restart).
 template <typename R>

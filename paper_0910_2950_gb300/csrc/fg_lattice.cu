@@ -29,7 +29,8 @@
 namespace fg {
 
 const char* kKernelClasses[] = {"gauge_force", "drift", "energy", "reduce", "momenta",
-                                "dslash", "cg_blas", "fermion_force", "convert"};
+                                "dslash", "cg_blas", "fermion_force", "convert", "dslash_fp64",
+                                "dslash_df"};
 
 // ---------------------------------------------------------------------------
 // Integrator sequences (Table 1 and section 3).
@@ -157,7 +158,7 @@ fg_status fg_params_default(fg_params* p) {
   p->cg_tol = 1e-10;
   p->cg_tol_action = 1e-12;
   p->cg_maxiter = 20000;
-  p->cg_delta = 0.1;
+  p->cg_delta = 0.01;
   p->seed = 1;
   p->cuda_stream = nullptr;
   return FG_OK;

@@ -27,9 +27,9 @@ int count_forces(const std::vector<Op>& ops);
 
 enum KernelClass {
   KC_GAUGE_FORCE = 0, KC_DRIFT, KC_ENERGY, KC_REDUCE, KC_MOMENTA,
-  KC_DSLASH, KC_CG_BLAS, KC_FERMION_FORCE, KC_CONVERT
+  KC_DSLASH, KC_CG_BLAS, KC_FERMION_FORCE, KC_CONVERT, KC_DSLASH64, KC_DSLASH_DF
 };
-constexpr int kNumKernelClasses = 9;
+constexpr int kNumKernelClasses = 11;
 extern const char* kKernelClasses[];
 
 // Per-launch CUDA-event timing.  Events come from a pool that grows on

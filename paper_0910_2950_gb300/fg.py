@@ -153,7 +153,7 @@ class Lattice:
     """One lattice handle (``fg_lattice*``)."""
 
     def __init__(self, dims, beta=6.0, kappa=0.0, precision="fp64", link_reals=18, alpha=0.1932,
-                 cg_tol=1e-10, cg_tol_action=1e-12, cg_maxiter=20000, cg_delta=0.1, seed=1,
+                 cg_tol=1e-10, cg_tol_action=1e-12, cg_maxiter=20000, cg_delta=0.01, seed=1,
                  reunitarize=None, stream=None):
         lib = load()
         p = FgParams()

@@ -88,6 +88,31 @@ def test_cg_solve(fgmod, precision, dims):
     assert _rel(x, inputs.pack_even(xo, dims)) < 1e-7
 
 
+def test_fp32_reliable_updates_in_double_float(fgmod):
+    """The FP32 solver's intermediate reliable updates apply Mhat^dag Mhat in
+    double-float arithmetic; only the update that certifies convergence uses
+    the FP64 Dslash, and the certified residual holds against the oracle."""
+    dims = (8, 8, 8, 8)
+    u = inputs.hot_start(dims, 7)
+    b = _rand_even(dims, 9)
+    tol = 1e-10
+    with fgmod.Lattice(dims, BETA, kappa=0.158, precision="fp32", cg_tol=tol) as lat:
+        lat.set_gauge(u)
+        lat.timing(True)
+        lat.timing_reset()
+        x, info = lat.cg_solve(b)
+        _, n_df = lat.kernel_time("dslash_df")
+        _, n64 = lat.kernel_time("dslash_fp64")
+        _, n32 = lat.kernel_time("dslash")
+    assert info["reliable_updates"] >= 3
+    assert n_df > 0 and n64 >= 4 and n64 % 4 == 0
+    assert n_df + n64 == 4 * info["reliable_updates"]
+    assert n32 >= 4 * info["iterations"]
+    uu = u.astype(np.complex64).astype(np.complex128)
+    res = inputs.unpack_even(b, dims) - fe.mdagm(uu, 0.158, inputs.unpack_even(x, dims))
+    assert np.linalg.norm(res) <= 1.01 * tol * np.linalg.norm(b)
+
+
 def test_cg_matches_dense_solve_2x2x2x2(fgmod):
     dims = (2, 2, 2, 2)
     u = inputs.hot_start(dims, 3)
