@@ -182,6 +182,98 @@ __device__ __forceinline__ void reconstruct_add(Spinor<DF>& acc, const Cx<DF> w[
   }
 }
 
+// ---- runtime-direction hop (double-float): one loop body for all eight
+// hops keeps the long double-float code within the instruction cache.
+// The spin structure of each direction is a choice of component and a unit
+// factor in {1, i, -1, -i}, taken with selects.
+__device__ __forceinline__ Cx<DF> unit_mul(const Cx<DF>& x, bool is_i, bool neg) {
+  const float sg = neg ? -1.0f : 1.0f;
+  const DF re = is_i ? -x.im : x.re;
+  const DF im = is_i ? x.re : x.im;
+  return cx<DF>(DF(sg * re.hi, sg * re.lo), DF(sg * im.hi, sg * im.lo));
+}
+__device__ __forceinline__ Cx<DF> pick(bool first, const Cx<DF>& a, const Cx<DF>& b) {
+  return cx<DF>(first ? a.re : b.re, first ? a.im : b.im);
+}
+// h_k = psi_k - S (A_mu psi_down)_k: (A_mu psi_down)_0 = c0 psi_j0,
+// (A_mu psi_down)_1 = c1 psi_(5-j0); j0 = 3 for mu = x, y and 2 for z, t;
+// c0, c1 = (i, i), (-1, 1), (i, -i), (1, 1).
+__device__ __forceinline__ void project_rt(int mu, int S, const Spinor<DF>& p, Cx<DF> h[2][3]) {
+  const bool j3 = mu < 2, is_i = mu == 0 || mu == 2;
+  const bool n0 = (mu == 1) != (S > 0), n1 = (mu == 2) != (S > 0);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    h[0][c] = p.s[0][c] + unit_mul(pick(j3, p.s[3][c], p.s[2][c]), is_i, n0);
+    h[1][c] = p.s[1][c] + unit_mul(pick(j3, p.s[2][c], p.s[3][c]), is_i, n1);
+  }
+}
+// acc_up += sign w; acc_down += sign (-S) A_mu^dagger w with
+// (A_mu^dagger w)_0 = d0 w_k0, (A_mu^dagger w)_1 = d1 w_(1-k0); k0 = 1 for
+// mu = x, y and 0 for z, t; d0, d1 = (-i, -i), (1, -1), (-i, i), (1, 1).
+__device__ __forceinline__ void reconstruct_rt(int mu, int S, float sign, const Cx<DF> w[2][3], Spinor<DF>& acc) {
+  const bool k1 = mu < 2, is_i = mu == 0 || mu == 2;
+  // w0, w1 carry `sign`; unit_mul applies d and the factor -S
+  const bool n0 = is_i != (S > 0), n1 = (mu < 2) != (S > 0);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const Cx<DF> w0 = df_scale_sign(w[0][c], sign), w1 = df_scale_sign(w[1][c], sign);
+    acc.s[0][c] = acc.s[0][c] + w0;
+    acc.s[1][c] = acc.s[1][c] + w1;
+    acc.s[2][c] = acc.s[2][c] + unit_mul(pick(k1, w1, w0), is_i, n0);
+    acc.s[3][c] = acc.s[3][c] + unit_mul(pick(k1, w0, w1), is_i, n1);
+  }
+}
+// w = U h (adj = false) or U^dagger h, FP32 link, compensated double-float sums
+__device__ __forceinline__ void mat_half_rt(const M3<float>& u, bool adj, const Cx<DF> h[2][3], Cx<DF> w[2][3]) {
+  float ur[3][3], ui[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      ur[a][b] = adj ? u.e[b][a].re : u.e[a][b].re;
+      ui[a][b] = adj ? -u.e[b][a].im : u.e[a][b].im;
+    }
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      DfAcc re = {0.0f, 0.0f}, im = {0.0f, 0.0f};
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        dfacc_add(re, h[k][b].re, ur[a][b]);
+        dfacc_add(re, h[k][b].im, -ui[a][b]);
+        dfacc_add(im, h[k][b].im, ur[a][b]);
+        dfacc_add(im, h[k][b].re, ui[a][b]);
+      }
+      w[k][a] = cx<DF>(df_fast_two_sum(re.s, re.c), df_fast_two_sum(im.s, im.c));
+    }
+}
+template <int DAG, int NC>
+__device__ __forceinline__ void hops_rt(Spinor<DF>& acc, const float4* __restrict__ in, const Gauge<float, NC>& U,
+                                        const Geom& g, const int c[4], int s, int in_off) {
+  constexpr int SF = DAG ? -1 : 1;  // forward hop: (1 - g_mu), (1 + g_mu) for the dagger
+#pragma unroll 1
+  for (int hd = 0; hd < 8; ++hd) {
+    const int mu = hd >> 1;
+    const bool fwd = (hd & 1) == 0;
+    const int sn = cb_neighbor_rt(g, c, mu, fwd ? 1 : -1);
+    const Spinor<DF> p = load_spinor<DF>(in, sn - in_off, g.Vh);
+    const int S = fwd ? SF : -SF;
+    Cx<DF> h[2][3], w[2][3];
+    project_rt(mu, S, p, h);
+    const M3<float> u = U.load(mu, fwd ? s : sn);
+    mat_half_rt(u, !fwd, h, w);
+    const bool anti = mu == 3 && (fwd ? c[3] == g.L[3] - 1 : c[3] == 0);
+    reconstruct_rt(mu, S, anti ? -1.0f : 1.0f, w, acc);
+  }
+}
+template <int DAG, typename RL, int NC, typename RS>
+struct Hops {
+  static __device__ __forceinline__ void run(Spinor<RS>& acc, const typename Vec2<RS>::T* __restrict__ in,
+                                             const Gauge<RL, NC>& U, const Geom& g, const int c[4], int s,
+                                             int in_off);
+};
+
 template <int MU, int DAG, typename RL, int NC, typename RS>
 __device__ __forceinline__ void hop_dir(Spinor<RS>& acc, const typename Vec2<RS>::T* __restrict__ in,
                                         const Gauge<RL, NC>& U, const Geom& g, const int c[4], int s,
@@ -209,6 +301,24 @@ __device__ __forceinline__ void hop_dir(Spinor<RS>& acc, const typename Vec2<RS>
     reconstruct_add<MU, SB>(acc, w, sign);
   }
 }
+
+template <int DAG, typename RL, int NC, typename RS>
+__device__ __forceinline__ void Hops<DAG, RL, NC, RS>::run(Spinor<RS>& acc, const typename Vec2<RS>::T* __restrict__ in,
+                                                           const Gauge<RL, NC>& U, const Geom& g, const int c[4],
+                                                           int s, int in_off) {
+  hop_dir<0, DAG>(acc, in, U, g, c, s, in_off);
+  hop_dir<1, DAG>(acc, in, U, g, c, s, in_off);
+  hop_dir<2, DAG>(acc, in, U, g, c, s, in_off);
+  hop_dir<3, DAG>(acc, in, U, g, c, s, in_off);
+}
+template <int DAG, int NC>
+struct Hops<DAG, float, NC, DF> {
+  static __device__ __forceinline__ void run(Spinor<DF>& acc, const float4* __restrict__ in,
+                                             const Gauge<float, NC>& U, const Geom& g, const int c[4], int s,
+                                             int in_off) {
+    hops_rt<DAG, NC>(acc, in, U, g, c, s, in_off);
+  }
+};
 
 constexpr int kDslashThreads = 128;
 
@@ -240,10 +350,7 @@ __global__ void __launch_bounds__(kDslashThreads, DslashMinBlocks<RS>::value) ds
     for (int k = 0; k < 4; ++k)
 #pragma unroll
       for (int cc = 0; cc < 3; ++cc) acc.s[k][cc] = cx<RS>(0, 0);
-    hop_dir<0, DAG>(acc, in, U, g, c, s, in_off);
-    hop_dir<1, DAG>(acc, in, U, g, c, s, in_off);
-    hop_dir<2, DAG>(acc, in, U, g, c, s, in_off);
-    hop_dir<3, DAG>(acc, in, U, g, c, s, in_off);
+    Hops<DAG, RL, NC, RS>::run(acc, in, U, g, c, s, in_off);
     Spinor<RS> o;
     if (MODE == 0) {
 #pragma unroll
