@@ -249,6 +249,11 @@ DSLASH_BYTES_CG_AVG = 8 * 72 + 96 + 96 + (2 * 96 + 96) // 4
 DSLASH_FLOP = 1320
 
 
+def torch_sync():
+    import torch
+    torch.cuda.synchronize()
+
+
 def fermion_measurement(fg, stream, rank, hbm_peak, dims=(16, 16, 16, 32)):
     """CG on the Nf=2 workload (16^3 x 32 by default); returns a dict for the JSON line."""
     dims = tuple(dims)
@@ -283,6 +288,32 @@ def fermion_measurement(fg, stream, rank, hbm_peak, dims=(16, 16, 16, 32)):
     _, info = lat.cg_solve(bs[-1])
     cls = {c: lat.kernel_time(c) for c in ("dslash", "dslash_df", "dslash_fp64", "cg_blas", "reduce", "convert")}
     lat.timing(False)
+    # FG trajectories on the total force (tau = 1, dt = 0.1 and 0.05) from one
+    # start (links, momenta, chi), and the FP64 path's dH for dt = 0.1
+    chi = inputs.gaussian_spinor_even(dims, 21 + rank)
+    p0 = inputs.gaussian_momenta(dims, 22 + rank)
+    trajs = {}
+    for dt in (0.1, 0.05):
+        lat.set_gauge(u)
+        lat.set_momenta(p0)
+        lat.set_pseudofermion(chi)
+        torch_sync()
+        t0 = time.perf_counter()
+        r = lat.trajectory("fg", dt, TAU, refresh=False, u_accept=0.0)
+        ms = 1000 * (time.perf_counter() - t0)
+        trajs[f"fg_dt_{dt}"] = {"dH": r["dH"], "ms": ms, "forces": r["n_force"], "solves": r["n_solves"],
+                                "cg_iterations": r["cg_iters"]}
+    lat64 = fg.Lattice(dims, 5.6, kappa=0.158, precision="fp64", cg_tol=1e-10, seed=400 + rank, stream=stream)
+    lat64.set_gauge(u)
+    lat64.set_momenta(p0)
+    lat64.set_pseudofermion(chi)
+    t0 = time.perf_counter()
+    r64 = lat64.trajectory("fg", 0.1, TAU, refresh=False, u_accept=0.0)
+    ms64 = 1000 * (time.perf_counter() - t0)
+    lat64.close()
+    trajs["fp64_fg_dt_0.1"] = {"dH": r64["dH"], "ms": ms64, "solves": r64["n_solves"],
+                               "cg_iterations": r64["cg_iters"]}
+    trajs["dH_error_fp32_vs_fp64_dt_0.1"] = abs(trajs["fg_dt_0.1"]["dH"] - r64["dH"])
     lat.close()
     ds_ms, ds_n = cls["dslash"]
     avg = ds_ms / 1000.0 / max(ds_n, 1)
@@ -304,7 +335,64 @@ def fermion_measurement(fg, stream, rank, hbm_peak, dims=(16, 16, 16, 32)):
                             "sites_per_launch": vh, "avg_launch_us": avg * 1e6, "launches": ds_n,
                             "gflops": DSLASH_FLOP * vh / avg / 1e9},
         "cg_blas_ms_share": cls["cg_blas"][0] / max(sum(v[0] for v in cls.values()), 1e-9),
+        "trajectories": trajs,
+        "trajectories_note": "one FG trajectory per entry from the same links, momenta and chi; FP32 "
+                             "links/forces with the mixed solver vs the FP64 path; ms is wall clock",
     }
+
+
+def precision_measurement(fg, stream, rank, L=16, n_time=5):
+    """FP64 vs FP32 links/forces and 18- vs 12-real storage on 16^4 (beta 6):
+    dH of one FG (dt 0.25) and one Omelyan (dt 0.125) trajectory from the same
+    thermalised links and momenta, the error against FP64, trajectories/s and
+    the force kernel's algorithmic GB/s."""
+    import torch
+    dims = (L,) * 4
+    base = fg.Lattice(dims, BETA, precision="fp64", seed=500 + rank, stream=stream)
+    base.set_gauge(inputs.hot_start(dims, 11 + rank))
+    for _ in range(THERM_TRAJ):
+        base.trajectory("fg", 0.125, TAU, refresh=True, u_accept=0.0)
+    u = base.get_gauge()
+    base.close()
+    p0 = inputs.gaussian_momenta(dims, 13 + rank)
+    out, ref = {}, {}
+    for name, prec, reals in (("fp64_18", "fp64", 18), ("fp32_18", "fp32", 18), ("fp32_12", "fp32", 12)):
+        lat = fg.Lattice(dims, BETA, precision=prec, link_reals=reals, seed=600 + rank, stream=stream)
+        row = {}
+        for integ, dt in (("fg", 0.25), ("omelyan", 0.125)):
+            lat.set_gauge(u)
+            lat.set_momenta(p0)
+            r = lat.trajectory(integ, dt, TAU, refresh=False, u_accept=0.0)
+            row[f"dH_{integ}_dt_{dt}"] = r["dH"]
+            if prec == "fp64":
+                ref[integ] = r["dH"]
+            else:
+                row[f"dH_error_vs_fp64_{integ}"] = abs(r["dH"] - ref[integ])
+        lat.set_gauge(u)
+        lat.trajectory("fg", 0.25, TAU, refresh=True, u_accept=0.0)
+        st = torch.cuda.ExternalStream(stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(n_time):
+            lat.trajectory("fg", 0.25, TAU, refresh=True, u_accept=0.0)
+        e1.record(st)
+        torch.cuda.synchronize()
+        row["fg_trajectories_per_s"] = n_time / (e0.elapsed_time(e1) / 1000.0)
+        lat.timing(True)
+        lat.timing_reset()
+        lat.trajectory("fg", 0.25, TAU, refresh=True, u_accept=0.0)
+        f_ms, f_n = lat.kernel_time("gauge_force")
+        lat.timing(False)
+        lat.close()
+        esize = 8 if prec == "fp64" else 4
+        link_bytes = reals * esize + 2 * 8 * esize
+        row["force_avg_launch_us"] = 1000.0 * f_ms / max(f_n, 1)
+        row["force_algorithmic_gbs"] = link_bytes * 4 * L ** 4 / (f_ms / 1000.0 / max(f_n, 1)) / 1e9
+        row["force_bytes_per_link"] = link_bytes
+        out[name] = row
+    out["workload"] = (f"pure-gauge {L}^4, beta={BETA}, hot start + {THERM_TRAJ} FP64 FG trajectories; one "
+                       "trajectory per integrator from the same links and momenta")
+    return out
 
 
 def batched_measurement(fg, stream, rank, n_traj=6):
@@ -544,6 +632,9 @@ def run_ours(args):
     if not args.no_fermion:
         ferm = fermion_measurement(fg, stream.cuda_stream, rank, hbm_peak(),
                                    tuple(int(x) for x in args.fermion_dims.split(",")))
+    precision = None
+    if not args.no_compare:
+        precision = precision_measurement(fg, stream.cuda_stream, rank)
     batched = None
     if not args.no_batch:
         batched = batched_measurement(fg, stream.cuda_stream, rank)
@@ -566,6 +657,7 @@ def run_ours(args):
                 "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
                 "config": cfg, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fermion": ferm,
                 "batched_chains": batched, "serving": served, "integrator_comparison": comparison,
+                "precision_comparison": precision,
                 "gpu_launches": launches, "clocks": clk}
         print(json.dumps(line), flush=True)
     lat.close()

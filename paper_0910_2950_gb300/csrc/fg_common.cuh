@@ -249,27 +249,39 @@ template <typename R> __device__ __forceinline__ void rebuild_row2(M3<R>& u) {
   u.e[2][2] = conj(u.e[0][0] * u.e[1][1] - u.e[0][1] * u.e[1][0]);
 }
 
+// Scale a row of squared norm 1 + d to unit norm.  The factor is applied as
+// x += c x with c = (1 + d)^(-1/2) - 1, not as x *= (1 + c): a factor that
+// close to 1 would be rounded on the grid around 1.0, which is twice as
+// coarse above 1 as below, so rows slightly too long would survive more often
+// than rows slightly too short and every link would drift the same way
+// (the Wilson action would move coherently, by an amount proportional to the
+// volume, in each trajectory).
+template <typename R> __device__ __forceinline__ void normalize_row(Cx<R> row[3]) {
+  R d = R(-1);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    d = fma(row[j].re, row[j].re, d);
+    d = fma(row[j].im, row[j].im, d);
+  }
+  // (1 + d)^(-1/2) - 1 = -d/2 + 3 d^2 / 8 - 5 d^3 / 16 + ...
+  const R c = fabs(d) < R(1e-3) ? d * (R(-0.5) + d * (R(0.375) - d * R(0.3125))) : R(1) / sqrt(R(1) + d) - R(1);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    row[j].re = fma(c, row[j].re, row[j].re);
+    row[j].im = fma(c, row[j].im, row[j].im);
+  }
+}
+
 // Gram-Schmidt of rows 0-1 in the link's own precision, then row 2 from the
 // cross product.
 template <typename R> __device__ __forceinline__ void reunitarize(M3<R>& u) {
-  R n0 = 0;
-#pragma unroll
-  for (int j = 0; j < 3; ++j) n0 += u.e[0][j].re * u.e[0][j].re + u.e[0][j].im * u.e[0][j].im;
-  const R in0 = rsqrt(n0);
-#pragma unroll
-  for (int j = 0; j < 3; ++j) u.e[0][j] = in0 * u.e[0][j];
+  normalize_row(u.e[0]);
   Cx<R> pr = cx<R>(0, 0);  // <row0, row1>
 #pragma unroll
   for (int j = 0; j < 3; ++j) cmac_cj(pr, u.e[0][j], u.e[1][j]);
-  R n1 = 0;
 #pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    u.e[1][j] = u.e[1][j] - pr * u.e[0][j];
-    n1 += u.e[1][j].re * u.e[1][j].re + u.e[1][j].im * u.e[1][j].im;
-  }
-  const R in1 = rsqrt(n1);
-#pragma unroll
-  for (int j = 0; j < 3; ++j) u.e[1][j] = in1 * u.e[1][j];
+  for (int j = 0; j < 3; ++j) u.e[1][j] = u.e[1][j] - pr * u.e[0][j];
+  normalize_row(u.e[1]);
   rebuild_row2(u);
 }
 

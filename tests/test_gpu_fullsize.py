@@ -4,6 +4,10 @@
   sampled links against the per-link oracle, the action and kinetic totals
   against the whole-field oracle, gauge covariance of the force (sampled),
   and reversibility of a force-gradient trajectory (a property at any size).
+* 16^4 pure gauge from a thermalised FP64 start: the FP32 path's dH against
+  the FP64 path's (itself pinned to the oracle at 1e-12) for FG and leapfrog
+  trajectories; a one-signed rounding bias in the link normalisation shows
+  up here as an offset proportional to the volume.
 * 16^3 x 32 Nf=2 Wilson, kappa = 0.158, FP32 links with mixed-precision CG:
   Mhat against the whole-field oracle, the CG solution's FP64 true residual
   recomputed by the oracle, and the total force against the oracle's force
@@ -111,6 +115,26 @@ def nf2_case():
     dims = (16, 16, 16, 32)
     u = inputs.hot_start(dims, 2)
     return dims, u, u.astype(np.complex64).astype(np.complex128)
+
+
+@pytest.mark.parametrize("integ,dt", [("fg", 0.25), ("leapfrog", 0.05)])
+def test_fp32_dh_against_fp64_16x4(fgmod, integ, dt):
+    dims = (16, 16, 16, 16)
+    with fgmod.Lattice(dims, BETA, precision="fp64", seed=500) as base:
+        base.set_gauge(inputs.hot_start(dims, 11))
+        for _ in range(10):
+            base.trajectory("fg", 0.125, 1.0, refresh=True, u_accept=0.0)
+        u = base.get_gauge()
+    p = inputs.gaussian_momenta(dims, 13)
+    dh = {}
+    for prec in ("fp64", "fp32"):
+        with fgmod.Lattice(dims, BETA, precision=prec, seed=600) as lat:
+            lat.set_gauge(u)
+            lat.set_momenta(p)
+            dh[prec] = lat.trajectory(integ, dt, 1.0, refresh=False, u_accept=0.0)["dH"]
+    # H ~ 2e6 here; random FP32 rounding of 4.7e6 link and momentum entries per
+    # step moves dH by ~1e-3; a coherent half-ulp bias per link moved it by 0.2
+    assert abs(dh["fp32"] - dh["fp64"]) < 2e-2, dh
 
 
 def test_mhat_16x16x16x32_fp32_links(fgmod, nf2_case):
