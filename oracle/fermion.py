@@ -188,3 +188,20 @@ class FermionSystem:
         self.n_force += 1
         self.n_solve += 1
         return self.gauge.force(u) + fermion_force(u, self.kappa, self.phi, self.tol)
+
+
+class PseudofermionPart:
+    """S_F alone (the outer action of a two-level integrator)."""
+
+    def __init__(self, kappa, phi_e, tol=1e-12):
+        self.kappa = float(kappa)
+        self.phi = phi_e
+        self.tol = tol
+        self.n_force = 0
+
+    def action(self, u):
+        return pseudofermion_action(u, self.kappa, self.phi, self.tol)
+
+    def force(self, u):
+        self.n_force += 1
+        return fermion_force(u, self.kappa, self.phi, self.tol)
