@@ -303,6 +303,17 @@ def fermion_measurement(fg, stream, rank, hbm_peak, dims=(16, 16, 16, 32)):
         ms = 1000 * (time.perf_counter() - t0)
         trajs[f"fg_dt_{dt}"] = {"dH": r["dH"], "ms": ms, "forces": r["n_force"], "solves": r["n_solves"],
                                 "cg_iterations": r["cg_iters"]}
+    # two-level integrators: outer step on S_F at twice the step, gauge inside
+    for outer, inner, m, dt in (("fg", "omelyan", 2, 0.2), ("fg", "fg", 1, 0.2), ("omelyan", "omelyan", 2, 0.1)):
+        lat.set_gauge(u)
+        lat.set_momenta(p0)
+        lat.set_pseudofermion(chi)
+        torch_sync()
+        t0 = time.perf_counter()
+        r = lat.trajectory_nested(outer, inner, m, dt, TAU, refresh=False, u_accept=0.0)
+        ms = 1000 * (time.perf_counter() - t0)
+        trajs[f"nested_{outer}_over_{m}x{inner}_dt_{dt}"] = {"dH": r["dH"], "ms": ms, "solves": r["n_solves"],
+                                                            "cg_iterations": r["cg_iters"]}
     lat64 = fg.Lattice(dims, 5.6, kappa=0.158, precision="fp64", cg_tol=1e-10, seed=400 + rank, stream=stream)
     lat64.set_gauge(u)
     lat64.set_momenta(p0)

@@ -190,6 +190,23 @@ fg_status fg_fg_step(fg_lattice *h, double dt);
 fg_status fg_trajectory(fg_lattice *h, fg_integrator integ, double dt, double tau,
                         int refresh, double u_accept, fg_traj_result *out);
 
+/* Two-level (Sexton-Weingarten) trajectory for Nf = 2: H = T + S_G + S_F is
+ * split as (T + S_G) + S_F.  The outer integrator, with step dt, kicks with
+ * the pseudofermion force alone (its force-gradient kick, for
+ * FG_FORCE_GRADIENT, displaces along and kicks with that force alone); each
+ * of its drifts, of length c dt, is n_inner steps of the inner integrator
+ * with step c dt / n_inner on T + S_G.  Section 3 composes integrators from
+ * exactly integrable flows; this nests that composition, and the outer
+ * force-gradient term {S_F,{S_F,T + S_G}} reduces to {S_F,{S_F,T}} because
+ * S_G and S_F depend on the links only.  Adjacent kicks (gauge and
+ * pseudofermion kicks at the same links) and adjacent drifts are merged.
+ * On a pure-gauge handle the outer kicks vanish and the trajectory is the
+ * inner integrator's.  refresh, u_accept, *out and rejection as for
+ * fg_trajectory; FG_EINVAL if n_inner < 1. */
+fg_status fg_trajectory_nested(fg_lattice *h, fg_integrator outer, fg_integrator inner, int n_inner,
+                               double dt, double tau, int refresh, double u_accept,
+                               fg_traj_result *out);
+
 /* Building blocks for callers and tests (even-site spinors, host layout above). */
 /* out = Mhat in (dagger = 0) or Mhat^dagger in (dagger = 1). */
 fg_status fg_apply_mhat(fg_lattice *h, const double *host_in_even, double *host_out_even,

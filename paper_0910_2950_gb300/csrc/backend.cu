@@ -212,6 +212,19 @@ class Backend final : public IBackend {
 
   fg_status trajectory(int integ, double dt, int nsteps, int refresh, double u_accept,
                        fg_traj_result* r) override {
+    return run_trajectory(trajectory_ops(integ, h_->prm.alpha, nsteps, true), dt, nsteps, refresh, u_accept, r);
+  }
+
+  fg_status trajectory_nested(int outer, int inner, int n_inner, double dt, int nsteps, int refresh,
+                              double u_accept, fg_traj_result* r) override {
+    return run_trajectory(nested_trajectory_ops(outer, inner, h_->prm.alpha, n_inner, dt, nsteps), 1.0, nsteps,
+                          refresh, u_accept, r);
+  }
+
+  // Refresh, H at the start, the op list (coefficients times dt), H at the
+  // end, Metropolis.
+  fg_status run_trajectory(const std::vector<Op>& ops, double dt, int nsteps, int refresh, double u_accept,
+                           fg_traj_result* r) {
     fg_status s;
     solves_ = 0;
     cg_iters_ = 0;
@@ -232,7 +245,6 @@ class Backend final : public IBackend {
     // The start field is never written during the trajectory (see execute),
     // so a rejection only has to point back at it.
     void* const start = U_;
-    std::vector<Op> ops = trajectory_ops(integ, h_->prm.alpha, nsteps, true);
     if ((s = execute(ops, dt, start)) != FG_OK) return s;
     if ((s = energy(1, P_, 3)) != FG_OK) return s;
     if ((s = fetch(6)) != FG_OK) return s;
@@ -398,6 +410,10 @@ class Backend final : public IBackend {
       if (s != FG_OK) return s;
       a.FF = FF_;
     }
+    return gauge_launch(mode, a);
+  }
+  // The fused gauge-force kernel with whatever a.FF holds (no solve).
+  fg_status gauge_launch(int mode, const ForceArgs& a) {
     return run(KC_GAUGE_FORCE, [&] { return launch_gauge_force<R, NC>(g_, mode, a, st_); });
   }
 
@@ -434,6 +450,73 @@ class Backend final : public IBackend {
           if ((s = force_launch(FM_KICK, a)) != FG_OK) return s;
           i += 1;
         }
+      } else if (o.kind == 'K') {
+        // c dt times the gauge force plus d dt times the pseudofermion force
+        const double cg = o.c * dt, cf = ferm_ ? o.d * dt : 0.0;
+        if (cf != 0.0 && (s = fermion_force(U_, h_->prm.cg_tol)) != FG_OK) return s;
+        if (cg == 0.0) {
+          if (cf != 0.0 && (s = run(KC_MOMENTA, [&] { return launch_kick_ff<R>(g_, P_, FF_, cf, st_); })) != FG_OK)
+            return s;
+          i += 1;
+          continue;
+        }
+        ForceArgs a = force_args(U_);
+        a.ckick = cg;
+        a.FF = (cf != 0.0) ? FF_ : nullptr;
+        a.ffw = cf / cg;
+        if (next_q) {
+          void* out = free_buffer(protect);
+          a.cdrift = ops[i + 1].c * dt;
+          a.Ubase = U_;
+          a.Uout = out;
+          if ((s = gauge_launch(FM_KICK_DRIFT, a)) != FG_OK) return s;
+          U_ = out;
+          i += 2;
+        } else {
+          if ((s = gauge_launch(FM_KICK, a)) != FG_OK) return s;
+          i += 1;
+        }
+      } else if (o.kind == 'f') {
+        // force-gradient kick on the pseudofermion force alone: displace along
+        // it (a drift with FF in place of P), evaluate it there, kick
+        if (!ferm_) {
+          i += 1;
+          continue;
+        }
+        if ((s = fermion_force(U_, h_->prm.cg_tol)) != FG_OK) return s;
+        void* disp = free_buffer(protect);
+        const double cdisp = o.d * dt * dt;
+        const void* in = U_;
+        if ((s = run(KC_DRIFT, [&] {
+               return launch_drift<R, NC>(g_, in, FF_, disp, -cdisp, h_->prm.reunitarize, st_);
+             })) != FG_OK)
+          return s;
+        if ((s = fermion_force(disp, h_->prm.cg_tol)) != FG_OK) return s;
+        const double ck = o.c * dt;
+        if ((s = run(KC_MOMENTA, [&] { return launch_kick_ff<R>(g_, P_, FF_, ck, st_); })) != FG_OK) return s;
+        i += 1;
+      } else if (o.kind == 'g') {
+        // force-gradient kick on the gauge force alone
+        void* disp = free_buffer(protect);
+        ForceArgs d = force_args(U_);
+        d.cdisp = o.d * dt * dt;
+        d.Uout = disp;
+        if ((s = gauge_launch(FM_DISPLACE, d)) != FG_OK) return s;
+        ForceArgs a = force_args(disp);
+        a.ckick = o.c * dt;
+        if (next_q) {
+          void* out = (U_ == protect) ? buffer_not(protect, disp) : U_;
+          a.cdrift = ops[i + 1].c * dt;
+          a.Ubase = U_;
+          a.Uout = out;
+          s = gauge_launch(FM_KICK_DRIFT, a);
+          U_ = out;
+          i += 2;
+        } else {
+          s = gauge_launch(FM_KICK, a);
+          i += 1;
+        }
+        if (s != FG_OK) return s;
       } else if (o.kind == 'Q') {
         void* out = (U_ == protect) ? free_buffer(protect) : U_;
         const void* in = U_;

@@ -30,11 +30,16 @@ struct ForceArgs {
   void* Uout;          // output links (FM_KICK_DRIFT, FM_DISPLACE)
   double beta;
   double ckick, cdrift, cdisp;
+  double ffw;          // weight of FF relative to the gauge force (0 is treated as 1)
   int reunit;
 };
 
 template <typename R, int NC>
 cudaError_t launch_gauge_force(const GeomH& g, int mode, const ForceArgs& a, cudaStream_t st);
+
+// P -= c FF on every link (a kick with an externally computed force).
+template <typename R>
+cudaError_t launch_kick_ff(const GeomH& g, void* P, const void* FF, double c, cudaStream_t st);
 
 // U_out = exp(i c P) U_in on every link (U_out may equal U_in).
 template <typename R, int NC>

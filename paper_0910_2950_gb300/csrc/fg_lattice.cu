@@ -80,9 +80,45 @@ std::vector<Op> trajectory_ops(int integ, double alpha, int nsteps, bool merge) 
   return out;
 }
 
+std::vector<Op> nested_trajectory_ops(int outer, int inner, double alpha, int n_inner, double dt, int nsteps) {
+  std::vector<Op> out;
+  auto kick = [&](double cg, double cf) {
+    if (!out.empty() && out.back().kind == 'K') {
+      out.back().c += cg;
+      out.back().d += cf;
+    } else {
+      out.push_back({'K', cg, cf});
+    }
+  };
+  auto drift = [&](double c) {
+    if (!out.empty() && out.back().kind == 'Q') out.back().c += c;
+    else out.push_back({'Q', c, 0});
+  };
+  const std::vector<Op> o_ops = step_ops(outer, alpha), i_ops = step_ops(inner, alpha);
+  for (int n = 0; n < nsteps; ++n) {
+    for (const Op& o : o_ops) {
+      if (o.kind == 'P') {
+        kick(0.0, o.c * dt);
+      } else if (o.kind == 'G') {
+        out.push_back({'f', o.c * dt, o.d * dt * dt});
+      } else {
+        const double h = o.c * dt / n_inner;
+        for (int k = 0; k < n_inner; ++k)
+          for (const Op& i : i_ops) {
+            if (i.kind == 'P') kick(i.c * h, 0.0);
+            else if (i.kind == 'Q') drift(i.c * h);
+            else out.push_back({'g', i.c * h, i.d * h * h});
+          }
+      }
+    }
+  }
+  return out;
+}
+
 int count_forces(const std::vector<Op>& ops) {
   int n = 0;
-  for (const Op& o : ops) n += (o.kind == 'P') ? 1 : (o.kind == 'G' ? 2 : 0);
+  for (const Op& o : ops)
+    n += (o.kind == 'P' || o.kind == 'K') ? 1 : ((o.kind == 'G' || o.kind == 'g' || o.kind == 'f') ? 2 : 0);
   return n;
 }
 
@@ -272,6 +308,22 @@ fg_status fg_trajectory(fg_lattice* h, fg_integrator integ, double dt, double ta
   fg_traj_result r;
   std::memset(&r, 0, sizeof(r));
   fg_status s = h->be->trajectory((int)integ, dt, n, refresh, u_accept, &r);
+  if (out) *out = r;
+  return s;
+}
+fg_status fg_trajectory_nested(fg_lattice* h, fg_integrator outer, fg_integrator inner, int n_inner, double dt,
+                               double tau, int refresh, double u_accept, fg_traj_result* out) {
+  FG_CHECK_HANDLE(h);
+  if ((int)outer < 0 || (int)outer > 4 || (int)inner < 0 || (int)inner > 4)
+    return h->fail(FG_EINVAL, "bad integrator");
+  if (n_inner < 1) return h->fail(FG_EINVAL, "n_inner must be >= 1");
+  if (!(dt > 0.0) || !(tau > 0.0)) return h->fail(FG_EINVAL, "dt and tau must be positive");
+  const int n = (int)std::llround(tau / dt);
+  if (n < 1 || std::fabs(n * dt - tau) > 1e-9 * tau) return h->fail(FG_EINVAL, "tau must be a multiple of dt");
+  if (u_accept >= 1.0) return h->fail(FG_EINVAL, "u_accept must be < 1");
+  fg_traj_result r;
+  std::memset(&r, 0, sizeof(r));
+  fg_status s = h->be->trajectory_nested((int)outer, (int)inner, n_inner, dt, n, refresh, u_accept, &r);
   if (out) *out = r;
   return s;
 }

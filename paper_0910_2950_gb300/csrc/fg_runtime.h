@@ -15,6 +15,14 @@ namespace fg {
 // One sub-step of an integrator: 'P' kick exp(c dt S-hat), 'Q' drift
 // exp(c dt T-hat), 'G' force-gradient kick with coefficient c and the force
 // taken at links displaced by d dt^2 along the force.
+// One operation of an integrator sequence, with coefficients in units of dt
+// (c dt, d dt^2) when the list is run with a step size:
+//   'P' kick with the total force, c;      'Q' drift, c;
+//   'G' force-gradient kick on the total force (kick c, displacement d).
+// Two-level (nested) lists carry absolute coefficients and also use
+//   'K' kick with c times the gauge force plus d times the pseudofermion force;
+//   'g' force-gradient kick on the gauge force alone;
+//   'f' force-gradient kick on the pseudofermion force alone.
 struct Op {
   char kind;
   double c;
@@ -23,6 +31,10 @@ struct Op {
 
 std::vector<Op> step_ops(int integ, double alpha);
 std::vector<Op> trajectory_ops(int integ, double alpha, int nsteps, bool merge);
+// nsteps outer steps of `outer` (step dt) on the pseudofermion action whose
+// drifts are n_inner steps of `inner` on the gauge action; absolute
+// coefficients, adjacent kicks and drifts merged.
+std::vector<Op> nested_trajectory_ops(int outer, int inner, double alpha, int n_inner, double dt, int nsteps);
 int count_forces(const std::vector<Op>& ops);
 
 enum KernelClass {
@@ -66,6 +78,8 @@ struct IBackend {
   virtual fg_status md_step(int integ, double dt) = 0;
   virtual fg_status trajectory(int integ, double dt, int nsteps, int refresh, double u_accept,
                                fg_traj_result* r) = 0;
+  virtual fg_status trajectory_nested(int outer, int inner, int n_inner, double dt, int nsteps, int refresh,
+                                      double u_accept, fg_traj_result* r) = 0;
   virtual fg_status apply_mhat(const double* in, double* out, int dagger) = 0;
   virtual fg_status cg_solve(const double* b, double* x, fg_cg_result* r) = 0;
   virtual fg_status reunitarize_all() = 0;

@@ -35,12 +35,13 @@ template <typename R, int NC, int MODE>
 __global__ void __launch_bounds__(256, FG_FORCE_MIN_BLOCKS) gauge_force_kernel(Gauge<R, NC> U, Mom<R> P, Mom<R> F,
                                                           Mom<R> FF, Gauge<R, NC> Ubase,
                                                           Gauge<R, NC> Uout, Geom g, R beta6,
-                                                          R ckick, R cdrift, R cdisp, int reunit) {
+                                                          R ckick, R cdrift, R cdisp, int reunit, R ffw) {
   int s;
   if (!link_site(g, s)) return;
   int c[4], par;
   cb_coords(g, s, c, par);
-  force_link<R, NC, MODE>(U, P, F, FF, Ubase, Uout, g, c, s, (int)threadIdx.y, beta6, ckick, cdrift, cdisp, reunit);
+  force_link<R, NC, MODE>(U, P, F, FF, Ubase, Uout, g, c, s, (int)threadIdx.y, beta6, ckick, cdrift, cdisp, reunit,
+                          ffw);
 }
 
 template <typename R, int NC>
@@ -249,22 +250,23 @@ cudaError_t launch_gauge_force(const GeomH& gh, int mode, const ForceArgs& a, cu
   auto Ub = gauge_of<R, NC>(a.Ubase, V);
   auto Uo = gauge_of<R, NC>(a.Uout, V);
   const R b6 = R(a.beta / 6.0);
+  const R ffw = R(a.ffw == 0.0 ? 1.0 : a.ffw);
   switch (mode) {
     case FM_STORE:
       gauge_force_kernel<R, NC, FM_STORE><<<pair_grid(V), link_block(), 0, st>>>(
-          U, P, F, FF, Ub, Uo, g, b6, R(a.ckick), R(a.cdrift), R(a.cdisp), a.reunit);
+          U, P, F, FF, Ub, Uo, g, b6, R(a.ckick), R(a.cdrift), R(a.cdisp), a.reunit, ffw);
       break;
     case FM_KICK:
       gauge_force_kernel<R, NC, FM_KICK><<<pair_grid(V), link_block(), 0, st>>>(
-          U, P, F, FF, Ub, Uo, g, b6, R(a.ckick), R(a.cdrift), R(a.cdisp), a.reunit);
+          U, P, F, FF, Ub, Uo, g, b6, R(a.ckick), R(a.cdrift), R(a.cdisp), a.reunit, ffw);
       break;
     case FM_KICK_DRIFT:
       gauge_force_kernel<R, NC, FM_KICK_DRIFT><<<pair_grid(V), link_block(), 0, st>>>(
-          U, P, F, FF, Ub, Uo, g, b6, R(a.ckick), R(a.cdrift), R(a.cdisp), a.reunit);
+          U, P, F, FF, Ub, Uo, g, b6, R(a.ckick), R(a.cdrift), R(a.cdisp), a.reunit, ffw);
       break;
     case FM_DISPLACE:
       gauge_force_kernel<R, NC, FM_DISPLACE><<<pair_grid(V), link_block(), 0, st>>>(
-          U, P, F, FF, Ub, Uo, g, b6, R(a.ckick), R(a.cdrift), R(a.cdisp), a.reunit);
+          U, P, F, FF, Ub, Uo, g, b6, R(a.ckick), R(a.cdrift), R(a.cdisp), a.reunit, ffw);
       break;
     default:
       return cudaErrorInvalidValue;
@@ -345,6 +347,29 @@ cudaError_t launch_mom_to_canon(const GeomH& gh, const void* P, double* canon, c
   mom_to_canon_kernel<R><<<(4 * gh.V + 255) / 256, 256, 0, st>>>(mom_of<R>(P, gh.V), canon, to_dev(gh));
   return cudaGetLastError();
 }
+
+// P -= c FF (kick with a force computed elsewhere: the pseudofermion force of
+// a two-level integrator's outer kicks).
+template <typename R>
+__global__ void __launch_bounds__(256) kick_ff_kernel(Mom<R> P, Mom<R> FF, int V, R c) {
+  const int s = blockIdx.x * kSitesPerBlock + threadIdx.x;
+  const int mu = threadIdx.y;
+  if (s >= V) return;
+  R p[8], f[8];
+  P.load(mu, s, p);
+  FF.load(mu, s, f);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) p[k] = fma(-c, f[k], p[k]);
+  P.store(mu, s, p);
+}
+template <typename R>
+cudaError_t launch_kick_ff(const GeomH& gh, void* P, const void* FF, double c, cudaStream_t st) {
+  kick_ff_kernel<R><<<link_grid(gh.V), link_block(), 0, st>>>(mom_of<R>(P, gh.V), mom_of<R>(FF, gh.V), gh.V,
+                                                              R(c));
+  return cudaGetLastError();
+}
+template cudaError_t launch_kick_ff<double>(const GeomH&, void*, const void*, double, cudaStream_t);
+template cudaError_t launch_kick_ff<float>(const GeomH&, void*, const void*, double, cudaStream_t);
 
 #define FG_INST_RNC(R, NC)                                                                          \
   template cudaError_t launch_gauge_force<R, NC>(const GeomH&, int, const ForceArgs&, cudaStream_t); \

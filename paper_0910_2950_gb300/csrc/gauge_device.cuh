@@ -53,7 +53,8 @@ template <typename R, int NC, int MODE>
 __device__ __forceinline__ void force_link(const Gauge<R, NC>& U, const Mom<R>& P, const Mom<R>& F,
                                            const Mom<R>& FF, const Gauge<R, NC>& Ubase,
                                            const Gauge<R, NC>& Uout, const Geom& g, const int c[4], int s,
-                                           int mu, R beta6, R ckick, R cdrift, R cdisp, int reunit) {
+                                           int mu, R beta6, R ckick, R cdrift, R cdisp, int reunit,
+                                           R ffw = R(1)) {
   const M3<R> a = staple_sum(U, g, c, s, mu);
   const M3<R> ul = U.load(mu, s);
   const M3<R> omega = mul(ul, a);
@@ -65,7 +66,7 @@ __device__ __forceinline__ void force_link(const Gauge<R, NC>& U, const Mom<R>& 
     R ff[8];
     FF.load(mu, s, ff);
 #pragma unroll
-    for (int k = 0; k < 8; ++k) f[k] += ff[k];
+    for (int k = 0; k < 8; ++k) f[k] = fma(ffw, ff[k], f[k]);
   }
   if (MODE == FM_STORE) {
     F.store(mu, s, f);

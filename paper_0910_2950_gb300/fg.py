@@ -84,6 +84,7 @@ SIGNATURES = {
     "fg_timing_enable": (_i, [_vp, _i]),
     "fg_timing_reset": (_i, [_vp]),
     "fg_kernel_time": (_i, [_vp, C.c_char_p, _dp, C.POINTER(C.c_longlong)]),
+    "fg_trajectory_nested": (_i, [_vp, _i, _i, _i, _d, _d, _i, _d, C.POINTER(FgTrajResult)]),
     "fg_launch_count": (C.c_longlong, [_vp]),
     "fg_sync": (_i, [_vp]),
     "fg_device_bytes": (C.c_ulonglong, [_vp]),
@@ -257,6 +258,12 @@ class Lattice:
         r = FgTrajResult()
         self._call("fg_trajectory", INTEGRATORS[integrator], float(dt), float(tau), int(bool(refresh)),
                    float(u_accept), C.byref(r))
+        return {k: getattr(r, k) for k, _ in FgTrajResult._fields_}
+
+    def trajectory_nested(self, outer, inner, n_inner, dt, tau=1.0, refresh=True, u_accept=-1.0):
+        r = FgTrajResult()
+        self._call("fg_trajectory_nested", INTEGRATORS[outer], INTEGRATORS[inner], int(n_inner), float(dt),
+                   float(tau), int(bool(refresh)), float(u_accept), C.byref(r))
         return {k: getattr(r, k) for k, _ in FgTrajResult._fields_}
 
     # -- fermion building blocks

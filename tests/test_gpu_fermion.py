@@ -279,3 +279,76 @@ def test_device_pseudofermion_refresh(fgmod):
     # S_F = chi^dagger chi ~ 12 V/2 (one unit per complex component)
     v = inputs.volume(dims)
     assert abs(sf / (12 * v / 2) - 1) < 5 * np.sqrt(1 / (12 * v / 2))
+
+
+# ---------------------------------------------------------------- two-level integrator
+NESTED = [("fg", "omelyan", 2), ("omelyan", "fg", 1), ("fg", "fg", 3), ("leapfrog", "qpq", 2)]
+
+
+@pytest.fixture(scope="module")
+def nested_oracle():
+    dims = (4, 4, 2, 4)
+    u = inputs.hot_start(dims, 21)
+    p = inputs.gaussian_momenta(dims, 22)
+    chi = inputs.gaussian_spinor_even(dims, 23)
+    phi = fe.heatbath_phi(u, KAPPA, inputs.unpack_even(chi, dims))
+    out = {}
+    for outer, inner, m in NESTED:
+        total = fe.FermionSystem(BETA, KAPPA, phi, tol=1e-13)
+        outer_sys = fe.PseudofermionPart(KAPPA, phi, tol=1e-13)
+        u1, p1, h0, h1 = it.nested_trajectory(total, outer_sys, total.gauge, it.Integrator(outer),
+                                              it.Integrator(inner), m, u, p, 0.25, 0.5)
+        out[(outer, inner, m)] = (h1 - h0, h0, u1, p1, outer_sys.n_force)
+    return dims, u, p, chi, out
+
+
+@pytest.mark.parametrize("outer,inner,m", NESTED)
+def test_nested_trajectory_fp64_matches_oracle(fgmod, nested_oracle, outer, inner, m):
+    dims, u, p, chi, ref = nested_oracle
+    with fgmod.Lattice(dims, BETA, kappa=KAPPA, cg_tol=1e-13, cg_tol_action=1e-13) as lat:
+        lat.set_gauge(u)
+        lat.set_pseudofermion(chi)
+        lat.set_momenta(p)
+        r = lat.trajectory_nested(outer, inner, m, 0.25, 0.5, refresh=False, u_accept=0.0)
+        ug = lat.get_gauge()
+        pg = lat.get_momenta()
+    dh_o, h0_o, u1_o, p1_o, n_outer = ref[(outer, inner, m)]
+    assert abs(r["H0"] - h0_o) < 1e-9 * abs(h0_o)
+    assert abs(r["dH"] - dh_o) < 1e-6, (r["dH"], dh_o)
+    assert _rel(ug, u1_o) < 1e-10
+    assert _rel(pg, p1_o) < 1e-9
+    # outer kicks of neighbouring steps share one solve; the outer FG kick
+    # takes two; plus the action solve at the end
+    n_steps = 2
+    per_step = {"fg": 3, "omelyan": 2, "leapfrog": 1}[outer]
+    assert r["n_solves"] == per_step * n_steps + 1 + 1
+
+
+def test_nested_pure_gauge_is_the_inner_integrator(fgmod):
+    """Without fermions the outer kicks vanish: the nested trajectory is the
+    inner integrator's at step (drift weight) x dt / n_inner, op for op."""
+    dims = (6, 4, 4, 6)
+    u = inputs.hot_start(dims, 3)
+    p = inputs.gaussian_momenta(dims, 4)
+    res = []
+    for nested in (True, False):
+        with fgmod.Lattice(dims, 6.0) as lat:
+            lat.set_gauge(u)
+            lat.set_momenta(p)
+            if nested:
+                r = lat.trajectory_nested("leapfrog", "omelyan", 3, 0.25, 1.0, refresh=False, u_accept=0.0)
+            else:
+                r = lat.trajectory("omelyan", 0.25 / 3, 1.0, refresh=False, u_accept=0.0)
+            res.append((r["dH"], lat.get_gauge(), lat.get_momenta()))
+    assert res[0][0] == res[1][0]
+    assert np.array_equal(res[0][1], res[1][1]) and np.array_equal(res[0][2], res[1][2])
+
+
+def test_nested_fp32_mixed(fgmod, nested_oracle):
+    dims, u, p, chi, ref = nested_oracle
+    with fgmod.Lattice(dims, BETA, kappa=KAPPA, precision="fp32", cg_tol=1e-10, cg_tol_action=1e-11) as lat:
+        lat.set_gauge(u)
+        lat.set_pseudofermion(chi)
+        lat.set_momenta(p)
+        r = lat.trajectory_nested("fg", "omelyan", 2, 0.25, 0.5, refresh=False, u_accept=0.0)
+    assert abs(r["dH"] - ref[("fg", "omelyan", 2)][0]) < 2e-3
