@@ -82,7 +82,8 @@ def footprint_bytes(spec: ChainSpec, precision: str = "fp32", link_reals: int = 
     """Device bytes a chain holds, from the library's allocation plan: three
     link buffers, momenta and force, per-site energies and partial sums, the
     FP64 host-layout staging buffer, and for fermions 8 FP64 and 10 working
-    half-lattice spinors plus the fermion force."""
+    half-lattice spinors (plus 2 double-float ones for the FP32 solver's
+    reliable updates) and the fermion force."""
     v = int(np.prod(spec.dims))
     r = 4 if precision == "fp32" else 8
     gauge = 4 * v * link_reals * r
@@ -90,7 +91,7 @@ def footprint_bytes(spec: ChainSpec, precision: str = "fp32", link_reals: int = 
     total = 3 * gauge + 2 * mom + 8 * v + 16 * (v // 256 + 2) + 4 * v * 18 * 8
     if spec.kappa > 0:
         nvec = 12 * (v // 2)
-        total += 8 * nvec * 16 + 10 * nvec * 2 * r + mom
+        total += (8 + (2 if precision == "fp32" else 0)) * nvec * 16 + 10 * nvec * 2 * r + mom
     return total
 
 

@@ -65,3 +65,19 @@ def test_alone_and_in_the_mix_gpu(fgmod):
         assert np.array_equal(l1[k], l4[k]) and np.array_equal(l1[k], l3[k])
     # fermion requests did CG solves; pure-gauge ones did not
     assert all((r.n_solves > 0) == (r.chain == 3) for r in seq)
+
+
+@pytest.mark.parametrize("spec", [serve.ChainSpec((8, 8, 8, 8), 6.0, 0.0, 1),
+                                  serve.ChainSpec((8, 8, 8, 16), 5.6, 0.157, 2),
+                                  serve.ChainSpec((6, 6, 6, 12), 5.6, 0.155, 3)])
+def test_footprint_bounds_the_library_allocation(fgmod, spec):
+    """Admission by HBM footprint is only safe if the estimate is an upper
+    bound of what a chain's handle holds after a trajectory (all lazy
+    buffers allocated), and it should not waste much of the budget."""
+    with fgmod.Lattice(spec.dims, spec.beta, kappa=spec.kappa, precision="fp32", seed=spec.seed) as lat:
+        lat.random_gauge()
+        lat.trajectory("fg", 0.25, 1.0, refresh=True, u_accept=0.0)
+        lat.get_gauge()
+        held = lat.device_bytes()
+    est = serve.footprint_bytes(spec, "fp32")
+    assert held <= est <= 1.15 * held, (held, est)
