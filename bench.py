@@ -304,7 +304,8 @@ def fermion_measurement(fg, stream, rank, hbm_peak, dims=(16, 16, 16, 32)):
         trajs[f"fg_dt_{dt}"] = {"dH": r["dH"], "ms": ms, "forces": r["n_force"], "solves": r["n_solves"],
                                 "cg_iterations": r["cg_iters"]}
     # two-level integrators: outer step on S_F at twice the step, gauge inside
-    for outer, inner, m, dt in (("fg", "omelyan", 2, 0.2), ("fg", "fg", 1, 0.2), ("omelyan", "omelyan", 2, 0.1)):
+    for outer, inner, m, dt in (("fg", "fg", 1, 0.2), ("fg", "fg", 2, 0.2), ("fg", "omelyan", 2, 0.2),
+                                ("fg", "omelyan", 4, 0.2), ("omelyan", "omelyan", 4, 0.1)):
         lat.set_gauge(u)
         lat.set_momenta(p0)
         lat.set_pseudofermion(chi)

@@ -80,19 +80,25 @@ class Result:
 
 def footprint_bytes(spec: ChainSpec, precision: str = "fp32", link_reals: int = 18) -> int:
     """Device bytes a chain holds, from the library's allocation plan: three
-    link buffers, momenta and force, per-site energies and partial sums, the
-    FP64 host-layout staging buffer, and for fermions 8 FP64 and 10 working
-    half-lattice spinors (plus 2 double-float ones for the FP32 solver's
-    reliable updates) and the fermion force."""
+    link buffers, momenta and force, per-site energies, block partials and
+    result scalars, the FP64 host-layout staging buffer, and for fermions 8
+    FP64 and 10 working half-lattice spinors (plus 2 double-float ones for the
+    FP32 solver's reliable updates), the pseudofermion force, the CG scalars
+    and the Dslash / vector block partials.  4 KiB are added for allocator
+    rounding of the small buffers."""
     v = int(np.prod(spec.dims))
     r = 4 if precision == "fp32" else 8
     gauge = 4 * v * link_reals * r
     mom = 4 * v * 8 * r
-    total = 3 * gauge + 2 * mom + 8 * v + 16 * (v // 256 + 2) + 4 * v * 18 * 8
+    total = 3 * gauge + 2 * mom + 8 * v + 4 * 8 * ((v + 255) // 256 + 1) + 32 * 8 + 4 * v * 18 * 8
     if spec.kappa > 0:
-        nvec = 12 * (v // 2)
-        total += (8 + (2 if precision == "fp32" else 0)) * nvec * 16 + 10 * nvec * 2 * r + mom
-    return total
+        vh = v // 2
+        nvec = 12 * vh
+        n64 = 8 + (2 if precision == "fp32" else 0)
+        dslash_blocks = (vh + 127) // 128
+        vec_blocks = min((nvec + 255) // 256, 152 * 8)
+        total += n64 * nvec * 16 + 10 * nvec * 2 * r + mom + 128 + 8 * (dslash_blocks + vec_blocks + 2)
+    return total + 4096
 
 
 class _Chain:
