@@ -149,6 +149,13 @@ def fermion_force(u, kappa, phi_e, tol=1e-12, x=None):
     y = mhat(u, kappa, x)
     xt = x + hop(u, x)
     yt = y + spin_mul(GAMMA5, hop(u, spin_mul(GAMMA5, y)))
+    return _force_form(u, kappa, xt, yt)
+
+
+def _force_form(u, kappa, xt, yt):
+    """2 kappa^2 Re <Ytilde, e_a(D) Xtilde> per link: real-linear in each of
+    the links (U enters each hop term once, as U or U^dagger), Xtilde and
+    Ytilde."""
     f = np.empty(u.shape[:5] + (8,))
     for mu in range(4):
         u_mu = u[..., mu, :, :]
@@ -166,6 +173,45 @@ def fermion_force(u, kappa, phi_e, tol=1e-12, x=None):
                            spin_mul(EYE4 + GAMMA[mu], q))
             f[..., mu, a] = 2.0 * kappa * kappa * np.real(t1 + t2)
     return f
+
+
+def mhat_tangent(u, du, kappa, psi_e):
+    """d/ds Mhat psi_e along U -> U + s dU: -kappa^2 (D(dU) D(U) + D(U) D(dU)) psi_e
+    (the hop is linear in the links, its backward terms in U^dagger)."""
+    return -kappa * kappa * (hop(du, hop(u, psi_e)) + hop(u, hop(du, psi_e)))
+
+
+def mhat_dag_tangent(u, du, kappa, psi_e):
+    return spin_mul(GAMMA5, mhat_tangent(u, du, kappa, spin_mul(GAMMA5, psi_e)))
+
+
+def mdagm_tangent(u, du, kappa, x):
+    """F(calM) X of section 4 for the direction dU: dMhat^dag Mhat X + Mhat^dag dMhat X."""
+    return mhat_dag_tangent(u, du, kappa, mhat(u, kappa, x)) + mhat_dag(u, kappa, mhat_tangent(u, du, kappa, x))
+
+
+def fermion_force_tangent(u, du, kappa, phi_e, tol=1e-12, x=None):
+    """Directional derivative of ``fermion_force`` along the link tangent dU.
+
+    Section 4: with X = calM^{-1} phi, its derivative is Y = -calM^{-1} F(calM) X
+    (one more solve); the force -X^dag e_i(calM) X then changes by
+    Y^dag e_i(calM) X + X^dag F(e_i(calM)) X + X^dag e_i(calM) Y.  Here the same
+    sum is taken through the bilinear form of ``fermion_force``: the links,
+    Xtilde and Ytilde each move in turn.  With dU = i F U (F the total force)
+    this is the fermion part of the force gradient G.
+    """
+    if x is None:
+        x, _ = cg(u, kappa, phi_e, tol)
+    z, _ = cg(u, kappa, mdagm_tangent(u, du, kappa, x), tol)
+    dx = -z
+    y = mhat(u, kappa, x)
+    dy = mhat_tangent(u, du, kappa, x) + mhat(u, kappa, dx)
+    xt = x + hop(u, x)
+    dxt = dx + hop(du, x) + hop(u, dx)
+    yt = y + spin_mul(GAMMA5, hop(u, spin_mul(GAMMA5, y)))
+    dyt = (dy + spin_mul(GAMMA5, hop(du, spin_mul(GAMMA5, y)))
+           + spin_mul(GAMMA5, hop(u, spin_mul(GAMMA5, dy))))
+    return _force_form(du, kappa, xt, yt) + _force_form(u, kappa, dxt, yt) + _force_form(u, kappa, xt, dyt)
 
 
 class FermionSystem:
@@ -189,6 +235,10 @@ class FermionSystem:
         self.n_solve += 1
         return self.gauge.force(u) + fermion_force(u, self.kappa, self.phi, self.tol)
 
+    def force_tangent(self, u, du):
+        self.n_solve += 2
+        return self.gauge.force_tangent(u, du) + fermion_force_tangent(u, du, self.kappa, self.phi, self.tol)
+
 
 class PseudofermionPart:
     """S_F alone (the outer action of a two-level integrator)."""
@@ -205,3 +255,6 @@ class PseudofermionPart:
     def force(self, u):
         self.n_force += 1
         return fermion_force(u, self.kappa, self.phi, self.tol)
+
+    def force_tangent(self, u, du):
+        return fermion_force_tangent(u, du, self.kappa, self.phi, self.tol)

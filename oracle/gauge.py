@@ -68,6 +68,47 @@ def staple_sum(u: np.ndarray, mu: int) -> np.ndarray:
     return a
 
 
+def _product_tangent(factors, tangents):
+    """d/ds of factors[0] @ factors[1] @ ... with factor k -> factor k + s tangents[k]."""
+    out = None
+    for k in range(len(factors)):
+        term = None
+        for j, f in enumerate(factors):
+            m = tangents[j] if j == k else f
+            term = m if term is None else term @ m
+        out = term if out is None else out + term
+    return out
+
+
+def staple_sum_tangent(u: np.ndarray, du: np.ndarray, mu: int) -> np.ndarray:
+    """d/ds A_mu(x) along U -> U + s dU (every link moves; daggered links
+    move by dU^dagger), term by term from ``staple_sum``."""
+    a = np.zeros(u.shape[:4] + (3, 3), dtype=np.complex128)
+    for nu in range(4):
+        if nu == mu:
+            continue
+        u_mu, u_nu = u[..., mu, :, :], u[..., nu, :, :]
+        d_mu, d_nu = du[..., mu, :, :], du[..., nu, :, :]
+        a += _product_tangent([shift(u_nu, mu, 1), dag(shift(u_mu, nu, 1)), dag(u_nu)],
+                              [shift(d_nu, mu, 1), dag(shift(d_mu, nu, 1)), dag(d_nu)])
+        u_nu_m, d_nu_m = shift(u_nu, nu, -1), shift(d_nu, nu, -1)
+        a += _product_tangent([dag(shift(u_nu_m, mu, 1)), dag(shift(u_mu, nu, -1)), u_nu_m],
+                              [dag(shift(d_nu_m, mu, 1)), dag(shift(d_mu, nu, -1)), d_nu_m])
+    return a
+
+
+def gauge_force_tangent(u: np.ndarray, du: np.ndarray, beta: float) -> np.ndarray:
+    """Directional derivative of ``gauge_force`` along the link tangent dU:
+    (beta/6) Im Tr(lambda^a (dU_mu A_mu + U_mu dA_mu)).  With dU = i F U it is
+    the force gradient G of section 4 (the derivative of the force along the
+    vector field e^j(S) e_j)."""
+    f = np.empty(u.shape[:5] + (8,))
+    for mu in range(4):
+        omega = du[..., mu, :, :] @ staple_sum(u, mu) + u[..., mu, :, :] @ staple_sum_tangent(u, du, mu)
+        f[..., mu, :] = (beta / 6.0) * im_tr_gellmann(omega)
+    return f
+
+
 def gauge_force(u: np.ndarray, beta: float) -> np.ndarray:
     """F^a_mu(x) = dS_G/d eps^a = (beta/6) Im Tr(lambda^a U_mu(x) A_mu(x)).
 
