@@ -293,16 +293,16 @@ def fermion_measurement(fg, stream, rank, hbm_peak, dims=(16, 16, 16, 32)):
     chi = inputs.gaussian_spinor_even(dims, 21 + rank)
     p0 = inputs.gaussian_momenta(dims, 22 + rank)
     trajs = {}
-    for dt in (0.1, 0.05):
+    for integ, dt in (("fg", 0.1), ("fg", 0.05), ("fg_analytic", 0.1), ("omelyan", 0.1), ("omelyan", 0.05)):
         lat.set_gauge(u)
         lat.set_momenta(p0)
         lat.set_pseudofermion(chi)
         torch_sync()
         t0 = time.perf_counter()
-        r = lat.trajectory("fg", dt, TAU, refresh=False, u_accept=0.0)
+        r = lat.trajectory(integ, dt, TAU, refresh=False, u_accept=0.0)
         ms = 1000 * (time.perf_counter() - t0)
-        trajs[f"fg_dt_{dt}"] = {"dH": r["dH"], "ms": ms, "forces": r["n_force"], "solves": r["n_solves"],
-                                "cg_iterations": r["cg_iters"]}
+        trajs[f"{integ}_dt_{dt}"] = {"dH": r["dH"], "ms": ms, "forces": r["n_force"], "solves": r["n_solves"],
+                                     "cg_iterations": r["cg_iters"]}
     # two-level integrators: outer step on S_F at twice the step, gauge inside
     for outer, inner, m, dt in (("fg", "fg", 1, 0.2), ("fg", "fg", 2, 0.2), ("fg", "omelyan", 2, 0.2),
                                 ("fg", "omelyan", 4, 0.2), ("omelyan", "omelyan", 4, 0.1)):
@@ -599,6 +599,8 @@ def run_ours(args):
     if not args.no_compare:
         comparison = {}
         for name, integ, dt in [("fg_dt_0.25", "fg", 0.25), ("fg_dt_0.125", "fg", 0.125),
+                                ("fg_analytic_dt_0.25", "fg_analytic", 0.25),
+                                ("fg_analytic_dt_0.125", "fg_analytic", 0.125),
                                 ("omelyan_dt_0.125", "omelyan", 0.125), ("omelyan_dt_0.0625", "omelyan", 0.0625)]:
             for _ in range(2):
                 lat.trajectory(integ, dt, TAU, refresh=True, u_accept=-1.0)

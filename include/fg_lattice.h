@@ -75,13 +75,22 @@ typedef enum {
  *   FG_CAMPOSTRINI     drift w1/2, kick w1, drift (w1+w0)/2, kick w0, drift
  *                      (w1+w0)/2, kick w1, drift w1/2; w1 = 1/(2-2^(1/3)), w0 = 1-2 w1
  *   FG_QPQ             drift 1/2, kick 1, drift 1/2
- * (kick c means exp(c dt S-hat), drift c means exp(c dt T-hat)). */
+ *   FG_FORCE_GRADIENT_ANALYTIC  the FG_FORCE_GRADIENT step with G in closed form
+ * (kick c means exp(c dt S-hat), drift c means exp(c dt T-hat)).  The
+ * force-gradient kick of Table 1 is a kick with F - (dt^2/24) G, G the
+ * derivative of the force F along the vector field e^j(S) e_j (section 4).
+ * FG_FORCE_GRADIENT evaluates it as the force at links displaced along the
+ * force, F(exp(-i (dt^2/24) F) U) (one extra force evaluation, equal to
+ * O(dt^4)); FG_FORCE_GRADIENT_ANALYTIC computes G itself, through the
+ * staples by the product rule and, with fermions, with the second solve
+ * Y = -calM^{-1} F(calM) X of section 4 (one extra solve, the same count). */
 typedef enum {
   FG_LEAPFROG = 0,
   FG_OMELYAN = 1,
   FG_FORCE_GRADIENT = 2,
   FG_CAMPOSTRINI = 3,
-  FG_QPQ = 4
+  FG_QPQ = 4,
+  FG_FORCE_GRADIENT_ANALYTIC = 5
 } fg_integrator;
 
 /* Arithmetic of the bulk fields (links, momenta, forces, CG inner vectors).

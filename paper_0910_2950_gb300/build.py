@@ -21,7 +21,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libfg_lattice.so")
-SOURCES = ["fg_lattice.cu", "backend.cu", "gauge.cu", "fermion.cu", "batch.cu", "noalloc.cu"]
+SOURCES = ["fg_lattice.cu", "backend.cu", "gauge.cu", "fermion.cu", "batch.cu", "noalloc.cu", "forcegrad.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -306,6 +306,12 @@ class Backend final : public IBackend {
   // fermions
   void *chi64_ = nullptr, *phi64_ = nullptr, *b64_ = nullptr, *x64_ = nullptr, *r64_ = nullptr;
   void *ax64_ = nullptr, *te64_ = nullptr, *to64_ = nullptr;
+  // closed-form force gradient: tangent links (NC = 9), force, gradient and
+  // pseudofermion-gradient momenta-layout fields, derivative spinors and
+  // temporaries (allocated at the first analytic FG step)
+  void *dU_ = nullptr, *Fa_ = nullptr, *G_ = nullptr, *FFt_ = nullptr;
+  void *dXe_ = nullptr, *dXo_ = nullptr, *dYe_ = nullptr, *dYo_ = nullptr;
+  void *Te1_ = nullptr, *Te2_ = nullptr, *To1_ = nullptr, *To2_ = nullptr;
   // double-float solution and source of the FP32 solver's reliable updates
   // (its Dslash temporaries reuse ax64_, te64_, to64_, which have the same size)
   void *xdf_ = nullptr, *bdf_ = nullptr;
@@ -417,6 +423,114 @@ class Backend final : public IBackend {
     return run(KC_GAUGE_FORCE, [&] { return launch_gauge_force<R, NC>(g_, mode, a, st_); });
   }
 
+  fg_status ensure_fg_buffers() {
+    if (dU_ != nullptr) return FG_OK;
+    fg_status s;
+    const size_t mom_bytes = (size_t)4 * 4 * g_.V * sizeof(C2);
+    // NC = 9 layout: four pairs and a tail entry per link, 36 complex per site
+    if ((s = alloc(&dU_, (size_t)4 * 9 * g_.V * sizeof(C2))) != FG_OK) return s;
+    void** m[] = {&Fa_, &G_, &FFt_};
+    for (void** q : m)
+      if ((s = alloc(q, mom_bytes)) != FG_OK) return s;
+    if (ferm_) {
+      void** v[] = {&dXe_, &dXo_, &dYe_, &dYo_, &Te1_, &Te2_, &To1_, &To2_};
+      for (void** q : v)
+        if ((s = alloc(q, (size_t)nvec() * sizeof(C2))) != FG_OK) return s;
+    }
+    return FG_OK;
+  }
+
+  // Derivative of the pseudofermion force along the tangent links dU_ into
+  // FFt_ (section 4).  Needs the state of the fermion_force(U) call just
+  // before it: X_e (Xe_, and x64_), X_o = D_oe X_e, Y_e = Mhat X_e,
+  // Y_o = D_oe^dag Y_e.  With X = calM^{-1} phi its derivative is
+  // -calM^{-1} F(calM) X (one more solve); X~ = (X_e, X_o) and
+  // Y~ = (Y_e, Y_o) move with it and with the links, and the force's
+  // bilinear form is differentiated in each argument in turn.
+  fg_status fermion_force_tangent(const void* U, double tol) {
+    const int n = nvec();
+    const double k2 = h_->prm.kappa * h_->prm.kappa;
+    fg_status s;
+    auto ds = [&](void* out, const void* in, const void* x, const void* links, bool tangent, int out_par, int dag,
+                  int mode, double b) {
+      return run(KC_DSLASH, [&] {
+        return tangent ? launch_dslash<R, 9, R>(g_, out, in, x, nullptr, links, out_par, dag, mode, b, nullptr,
+                                                nullptr, st_)
+                       : launch_dslash<R, NC, R>(g_, out, in, x, nullptr, links, out_par, dag, mode, b, nullptr,
+                                                 nullptr, st_);
+      });
+    };
+    auto lc = [&](auto launch) { return run(KC_CG_BLAS, launch); };
+    // dMhat X_e = -k2 (dD_eo X_o + D_eo dD_oe X_e)
+    if ((s = ds(To1_, Xe_, nullptr, dU_, true, 1, 0, 0, 1.0)) != FG_OK) return s;
+    if ((s = ds(Te1_, Xo_, nullptr, dU_, true, 0, 0, 0, -k2)) != FG_OK) return s;
+    if ((s = ds(dYe_, To1_, Te1_, U, false, 0, 0, 1, -k2)) != FG_OK) return s;
+    // dMhat^dag Y_e = -k2 (dD^dag_eo Y_o + D^dag_eo dD^dag_oe Y_e); dD^dag_oe Y_e kept in dYo_
+    if ((s = ds(dYo_, Ye_, nullptr, dU_, true, 1, 1, 0, 1.0)) != FG_OK) return s;
+    if ((s = ds(Te1_, Yo_, nullptr, dU_, true, 0, 1, 0, -k2)) != FG_OK) return s;
+    if ((s = ds(Te2_, dYo_, Te1_, U, false, 0, 1, 1, -k2)) != FG_OK) return s;
+    // Mhat^dag (dMhat X_e)
+    if ((s = ds(To2_, dYe_, nullptr, U, false, 1, 1, 0, 1.0)) != FG_OK) return s;
+    if ((s = ds(Te1_, To2_, dYe_, U, false, 0, 1, 1, -k2)) != FG_OK) return s;
+    // F(calM) X = dMhat^dag Y_e + Mhat^dag dMhat X_e, in FP64, and the solve
+    if ((s = lc([&] { return launch_lincomb<double, R, R>(b64_, 1.0, Te1_, 1.0, Te2_, n, st_); })) != FG_OK) return s;
+    CgStats cs;
+    if ((s = cg(U, b64_, tol, &cs)) != FG_OK) return s;
+    // dX_e = -calM^{-1} F(calM) X; dX_o = dD_oe X_e + D_oe dX_e
+    if ((s = lc([&] { return launch_lincomb<R, double, double>(dXe_, -1.0, x64_, 0.0, nullptr, n, st_); })) != FG_OK)
+      return s;
+    if ((s = ds(To2_, dXe_, nullptr, U, false, 1, 0, 0, 1.0)) != FG_OK) return s;
+    if ((s = lc([&] { return launch_lincomb<R, R, R>(dXo_, 1.0, To1_, 1.0, To2_, n, st_); })) != FG_OK) return s;
+    // dY_e = dMhat X_e + Mhat dX_e; dY_o = dD^dag_oe Y_e + D^dag_oe dY_e
+    if ((s = ds(Te1_, To2_, dXe_, U, false, 0, 0, 1, -k2)) != FG_OK) return s;
+    if ((s = lc([&] { return launch_lincomb<R, R, R>(dYe_, 1.0, dYe_, 1.0, Te1_, n, st_); })) != FG_OK) return s;
+    if ((s = ds(dYo_, dYe_, dYo_, U, false, 1, 1, 1, 1.0)) != FG_OK) return s;
+    // the bilinear force form with the links, X~ and Y~ moved in turn
+    auto ff = [&](const void* links, bool tangent, const void* xe, const void* xo, const void* ye, const void* yo,
+                  int acc) {
+      return run(KC_FERMION_FORCE, [&] {
+        return tangent ? launch_fermion_force<R, 9, R>(g_, links, xe, xo, ye, yo, FFt_, k2, acc, st_)
+                       : launch_fermion_force<R, NC, R>(g_, links, xe, xo, ye, yo, FFt_, k2, acc, st_);
+      });
+    };
+    if ((s = ff(dU_, true, Xe_, Xo_, Ye_, Yo_, 0)) != FG_OK) return s;
+    if ((s = ff(U, false, dXe_, dXo_, Ye_, Yo_, 1)) != FG_OK) return s;
+    return ff(U, false, Xe_, Xo_, dYe_, dYo_, 1);
+  }
+
+  // Closed-form force-gradient kick P -= c (F - shift G), G the derivative of
+  // the force along i F U; the force is the gauge part, the pseudofermion
+  // part, or both.
+  fg_status analytic_fg_kick(double c, double shift, bool gauge, bool ferm) {
+    fg_status s;
+    if ((s = ensure_fg_buffers()) != FG_OK) return s;
+    ferm = ferm && ferm_;
+    if (!gauge && !ferm) return FG_OK;
+    if (ferm && (s = fermion_force(U_, h_->prm.cg_tol)) != FG_OK) return s;
+    const void* F = FF_;
+    if (gauge) {
+      ForceArgs a = force_args(U_);
+      a.F = Fa_;
+      a.FF = ferm ? FF_ : nullptr;
+      if ((s = gauge_launch(FM_STORE, a)) != FG_OK) return s;
+      F = Fa_;
+    }
+    const void* Ucur = U_;
+    if ((s = run(KC_GAUGE_FORCE, [&] { return launch_tangent_links<R, NC>(g_, Ucur, F, dU_, st_); })) != FG_OK)
+      return s;
+    if (ferm && (s = fermion_force_tangent(U_, h_->prm.cg_tol)) != FG_OK) return s;
+    const void* G = FFt_;
+    if (gauge) {
+      const void* fft = ferm ? FFt_ : nullptr;
+      if ((s = run(KC_GAUGE_FORCE, [&] {
+             return launch_force_tangent<R, NC>(g_, Ucur, dU_, G_, fft, h_->prm.beta, st_);
+           })) != FG_OK)
+        return s;
+      G = G_;
+    }
+    return run(KC_MOMENTA, [&] { return launch_kick_fg<R>(g_, P_, F, G, c, shift, st_); });
+  }
+
   // One of the three link buffers that is neither the current field nor the
   // protected one.
   void* free_buffer(const void* protect) const { return buffer_not(U_, protect); }
@@ -517,6 +631,11 @@ class Backend final : public IBackend {
           i += 1;
         }
         if (s != FG_OK) return s;
+      } else if (o.kind == 'A' || o.kind == 'a' || o.kind == 'h') {
+        // closed-form force-gradient kick: total ('A'), pseudofermion ('a')
+        // or gauge ('h') force
+        if ((s = analytic_fg_kick(o.c * dt, o.d * dt * dt, o.kind != 'a', o.kind != 'h')) != FG_OK) return s;
+        i += 1;
       } else if (o.kind == 'Q') {
         void* out = (U_ == protect) ? free_buffer(protect) : U_;
         const void* in = U_;

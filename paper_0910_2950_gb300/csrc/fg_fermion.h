@@ -80,6 +80,9 @@ cudaError_t launch_cg_init(const double* part, int n, CgDev* cgd, double tol2, d
 // dst = (RO) src, with block partials of |src|^2 if part != nullptr.
 template <typename RO, typename RI>
 cudaError_t launch_convert(void* dst, const void* src, double* part, int n, cudaStream_t st);
+// out = a x + b y (y may be null) on n complex entries, arithmetic in FP64.
+template <typename RO, typename RX, typename RY>
+cudaError_t launch_lincomb(void* out, double a, const void* x, double b, const void* y, int n, cudaStream_t st);
 // Block partials of Re <a, b> for FP64 vectors.
 cudaError_t launch_dot64(const void* a, const void* b, double* part, int n, cudaStream_t st);
 template <typename R>

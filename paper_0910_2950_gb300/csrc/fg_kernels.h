@@ -41,6 +41,18 @@ cudaError_t launch_gauge_force(const GeomH& g, int mode, const ForceArgs& a, cud
 template <typename R>
 cudaError_t launch_kick_ff(const GeomH& g, void* P, const void* FF, double c, cudaStream_t st);
 
+// Closed-form force gradient (forcegrad.cu): dU = i F U on every link
+// (dU stored with NC = 9); G = derivative of the gauge force along dU, plus
+// FFt if not null; P -= c (F - shift G).
+template <typename R, int NC>
+cudaError_t launch_tangent_links(const GeomH& g, const void* U, const void* F, void* dU, cudaStream_t st);
+template <typename R, int NC>
+cudaError_t launch_force_tangent(const GeomH& g, const void* U, const void* dU, void* G, const void* FFt,
+                                 double beta, cudaStream_t st);
+template <typename R>
+cudaError_t launch_kick_fg(const GeomH& g, void* P, const void* F, const void* G, double c, double shift,
+                           cudaStream_t st);
+
 // U_out = exp(i c P) U_in on every link (U_out may equal U_in).
 template <typename R, int NC>
 cudaError_t launch_drift(const GeomH& g, const void* Uin, const void* P, void* Uout, double c,

@@ -52,6 +52,11 @@ std::vector<Op> step_ops(int integ, double alpha) {
       v = {{'P', 1.0 / 6.0, 0}, {'Q', 0.5, 0}, {'G', 2.0 / 3.0, 1.0 / 24.0}, {'Q', 0.5, 0},
            {'P', 1.0 / 6.0, 0}};
       break;
+    case FG_FORCE_GRADIENT_ANALYTIC:
+      // the same step with G in closed form: kick with F - (dt^2/24) G
+      v = {{'P', 1.0 / 6.0, 0}, {'Q', 0.5, 0}, {'A', 2.0 / 3.0, 1.0 / 24.0}, {'Q', 0.5, 0},
+           {'P', 1.0 / 6.0, 0}};
+      break;
     case FG_CAMPOSTRINI: {
       const double w1 = 1.0 / (2.0 - std::cbrt(2.0));
       const double w0 = 1.0 - 2.0 * w1;
@@ -70,7 +75,7 @@ std::vector<Op> trajectory_ops(int integ, double alpha, int nsteps, bool merge) 
   const std::vector<Op> one = step_ops(integ, alpha);
   for (int n = 0; n < nsteps; ++n) {
     for (const Op& o : one) {
-      if (merge && !out.empty() && out.back().kind == o.kind && o.kind != 'G') {
+      if (merge && !out.empty() && out.back().kind == o.kind && (o.kind == 'P' || o.kind == 'Q')) {
         out.back().c += o.c;
       } else {
         out.push_back(o);
@@ -99,15 +104,15 @@ std::vector<Op> nested_trajectory_ops(int outer, int inner, double alpha, int n_
     for (const Op& o : o_ops) {
       if (o.kind == 'P') {
         kick(0.0, o.c * dt);
-      } else if (o.kind == 'G') {
-        out.push_back({'f', o.c * dt, o.d * dt * dt});
+      } else if (o.kind == 'G' || o.kind == 'A') {
+        out.push_back({o.kind == 'G' ? 'f' : 'a', o.c * dt, o.d * dt * dt});
       } else {
         const double h = o.c * dt / n_inner;
         for (int k = 0; k < n_inner; ++k)
           for (const Op& i : i_ops) {
             if (i.kind == 'P') kick(i.c * h, 0.0);
             else if (i.kind == 'Q') drift(i.c * h);
-            else out.push_back({'g', i.c * h, i.d * h * h});
+            else out.push_back({i.kind == 'G' ? 'g' : 'h', i.c * h, i.d * h * h});
           }
       }
     }
@@ -118,7 +123,7 @@ std::vector<Op> nested_trajectory_ops(int outer, int inner, double alpha, int n_
 int count_forces(const std::vector<Op>& ops) {
   int n = 0;
   for (const Op& o : ops)
-    n += (o.kind == 'P' || o.kind == 'K') ? 1 : ((o.kind == 'G' || o.kind == 'g' || o.kind == 'f') ? 2 : 0);
+    n += (o.kind == 'P' || o.kind == 'K') ? 1 : ((o.kind == 'Q') ? 0 : 2);
   return n;
 }
 
@@ -291,7 +296,7 @@ fg_status fg_plaquette(fg_lattice* h, double* plaq) {
 }
 fg_status fg_md_step(fg_lattice* h, fg_integrator integ, double dt) {
   FG_CHECK_HANDLE(h);
-  if ((int)integ < 0 || (int)integ > 4 || !std::isfinite(dt)) return h->fail(FG_EINVAL, "bad integrator or dt");
+  if ((int)integ < 0 || (int)integ > 5 || !std::isfinite(dt)) return h->fail(FG_EINVAL, "bad integrator or dt");
   return h->be->md_step((int)integ, dt);
 }
 fg_status fg_fg_step(fg_lattice* h, double dt) { return fg_md_step(h, FG_FORCE_GRADIENT, dt); }
@@ -299,7 +304,7 @@ fg_status fg_fg_step(fg_lattice* h, double dt) { return fg_md_step(h, FG_FORCE_G
 fg_status fg_trajectory(fg_lattice* h, fg_integrator integ, double dt, double tau, int refresh,
                         double u_accept, fg_traj_result* out) {
   FG_CHECK_HANDLE(h);
-  if ((int)integ < 0 || (int)integ > 4) return h->fail(FG_EINVAL, "bad integrator");
+  if ((int)integ < 0 || (int)integ > 5) return h->fail(FG_EINVAL, "bad integrator");
   if (!(dt > 0.0) || !(tau > 0.0)) return h->fail(FG_EINVAL, "dt and tau must be positive");
   const double ns = tau / dt;
   const int n = (int)std::llround(ns);
@@ -314,7 +319,7 @@ fg_status fg_trajectory(fg_lattice* h, fg_integrator integ, double dt, double ta
 fg_status fg_trajectory_nested(fg_lattice* h, fg_integrator outer, fg_integrator inner, int n_inner, double dt,
                                double tau, int refresh, double u_accept, fg_traj_result* out) {
   FG_CHECK_HANDLE(h);
-  if ((int)outer < 0 || (int)outer > 4 || (int)inner < 0 || (int)inner > 4)
+  if ((int)outer < 0 || (int)outer > 5 || (int)inner < 0 || (int)inner > 5)
     return h->fail(FG_EINVAL, "bad integrator");
   if (n_inner < 1) return h->fail(FG_EINVAL, "n_inner must be >= 1");
   if (!(dt > 0.0) || !(tau > 0.0)) return h->fail(FG_EINVAL, "dt and tau must be positive");

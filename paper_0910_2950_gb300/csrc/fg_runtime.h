@@ -23,6 +23,9 @@ namespace fg {
 //   'K' kick with c times the gauge force plus d times the pseudofermion force;
 //   'g' force-gradient kick on the gauge force alone;
 //   'f' force-gradient kick on the pseudofermion force alone.
+// 'A', 'a', 'h' are the closed-form versions of 'G', 'f', 'g' (the kick uses
+// F - d G with G the derivative of the force along i F U, instead of the
+// force at links displaced by d along the force).
 struct Op {
   char kind;
   double c;

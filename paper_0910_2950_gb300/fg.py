@@ -22,7 +22,8 @@ LIB_PATH = os.environ.get("FG_LATTICE_LIB", os.path.join(_PKG, "libfg_lattice.so
 FG_OK, FG_EINVAL, FG_ENOMEM, FG_ECUDA, FG_ENOCONV, FG_ETIMEOUT, FG_ESTATE = range(7)
 STATUS_NAMES = {0: "FG_OK", 1: "FG_EINVAL", 2: "FG_ENOMEM", 3: "FG_ECUDA", 4: "FG_ENOCONV",
                 5: "FG_ETIMEOUT", 6: "FG_ESTATE"}
-INTEGRATORS = {"leapfrog": 0, "omelyan": 1, "fg": 2, "force_gradient": 2, "campostrini": 3, "qpq": 4}
+INTEGRATORS = {"leapfrog": 0, "omelyan": 1, "fg": 2, "force_gradient": 2, "campostrini": 3, "qpq": 4,
+               "fg_analytic": 5}
 PRECISIONS = {"fp64": 0, "fp32": 1}
 
 # Every function the header declares, with its ctypes signature.

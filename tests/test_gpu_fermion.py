@@ -352,3 +352,87 @@ def test_nested_fp32_mixed(fgmod, nested_oracle):
         lat.set_momenta(p)
         r = lat.trajectory_nested("fg", "omelyan", 2, 0.25, 0.5, refresh=False, u_accept=0.0)
     assert abs(r["dH"] - ref[("fg", "omelyan", 2)][0]) < 2e-3
+
+
+# ---------------------------------------------------------------- closed-form force gradient
+def test_analytic_fg_step_pure_gauge_fp64_matches_oracle(fgmod):
+    dims = (6, 4, 2, 4)
+    u = inputs.hot_start(dims, 31)
+    p = inputs.gaussian_momenta(dims, 32)
+    u1, p1 = it.md_step(it.GaugeSystem(6.0), it.Integrator("fg_analytic"), u, p, 0.2)
+    with fgmod.Lattice(dims, 6.0) as lat:
+        lat.set_gauge(u)
+        lat.set_momenta(p)
+        lat.md_step("fg_analytic", 0.2)
+        ug, pg = lat.get_gauge(), lat.get_momenta()
+    assert _rel(ug, u1) < 1e-12
+    assert _rel(pg, p1) < 1e-12
+    # and it is not the displaced-force step
+    u2, p2 = it.md_step(it.GaugeSystem(6.0), it.Integrator("fg"), u, p, 0.2)
+    assert _rel(pg, p2) > 1e-8
+
+
+@pytest.mark.parametrize("link_reals", [18, 12])
+def test_analytic_fg_step_fermions_fp64_matches_oracle(fgmod, link_reals):
+    dims = (4, 4, 2, 4)
+    u = inputs.hot_start(dims, 33)
+    p = inputs.gaussian_momenta(dims, 34)
+    chi = inputs.gaussian_spinor_even(dims, 35)
+    phi = fe.heatbath_phi(u, KAPPA, inputs.unpack_even(chi, dims))
+    system = fe.FermionSystem(BETA, KAPPA, phi, tol=1e-14)
+    u1, p1 = it.md_step(system, it.Integrator("fg_analytic"), u, p, 0.2)
+    with fgmod.Lattice(dims, BETA, kappa=KAPPA, link_reals=link_reals, cg_tol=1e-13,
+                       cg_tol_action=1e-13) as lat:
+        lat.set_gauge(u)
+        lat.set_pseudofermion(chi)
+        lat.set_momenta(p)
+        lat.md_step("fg_analytic", 0.2)
+        ug, pg = lat.get_gauge(), lat.get_momenta()
+    assert _rel(ug, u1) < 1e-10
+    assert _rel(pg, p1) < 1e-9
+
+
+def test_analytic_fg_trajectory_fermions(fgmod):
+    dims = (4, 4, 2, 4)
+    u = inputs.hot_start(dims, 36)
+    p = inputs.gaussian_momenta(dims, 37)
+    chi = inputs.gaussian_spinor_even(dims, 38)
+    phi = fe.heatbath_phi(u, KAPPA, inputs.unpack_even(chi, dims))
+    system = fe.FermionSystem(BETA, KAPPA, phi, tol=1e-13)
+    _, _, h0, h1 = it.trajectory(system, it.Integrator("fg_analytic"), u, p, 0.25, 1.0)
+    res = {}
+    for prec in ("fp64", "fp32"):
+        with fgmod.Lattice(dims, BETA, kappa=KAPPA, precision=prec, cg_tol=1e-13 if prec == "fp64" else 1e-10,
+                           cg_tol_action=1e-13 if prec == "fp64" else 1e-11) as lat:
+            lat.set_gauge(u)
+            lat.set_pseudofermion(chi)
+            lat.set_momenta(p)
+            res[prec] = lat.trajectory("fg_analytic", 0.25, 1.0, refresh=False, u_accept=0.0)
+    assert abs(res["fp64"]["dH"] - (h1 - h0)) < 1e-6, (res["fp64"]["dH"], h1 - h0)
+    assert abs(res["fp32"]["dH"] - (h1 - h0)) < 2e-3
+    # section 4: the closed form costs one extra solve per FG kick, as the
+    # displaced force does: 3n + 1 force solves plus the action solve
+    n = res["fp64"]["n_steps"]
+    assert res["fp64"]["n_solves"] == 3 * n + 1 + 1
+
+
+@pytest.mark.parametrize("outer,inner", [("fg_analytic", "omelyan"), ("fg", "fg_analytic"),
+                                         ("fg_analytic", "fg_analytic")])
+def test_nested_analytic_fp64_matches_oracle(fgmod, outer, inner):
+    dims = (4, 4, 2, 4)
+    u = inputs.hot_start(dims, 41)
+    p = inputs.gaussian_momenta(dims, 42)
+    chi = inputs.gaussian_spinor_even(dims, 43)
+    phi = fe.heatbath_phi(u, KAPPA, inputs.unpack_even(chi, dims))
+    total = fe.FermionSystem(BETA, KAPPA, phi, tol=1e-13)
+    outer_sys = fe.PseudofermionPart(KAPPA, phi, tol=1e-13)
+    u1, p1, h0, h1 = it.nested_trajectory(total, outer_sys, total.gauge, it.Integrator(outer), it.Integrator(inner),
+                                          2, u, p, 0.25, 0.5)
+    with fgmod.Lattice(dims, BETA, kappa=KAPPA, cg_tol=1e-13, cg_tol_action=1e-13) as lat:
+        lat.set_gauge(u)
+        lat.set_pseudofermion(chi)
+        lat.set_momenta(p)
+        r = lat.trajectory_nested(outer, inner, 2, 0.25, 0.5, refresh=False, u_accept=0.0)
+        ug = lat.get_gauge()
+    assert abs(r["dH"] - (h1 - h0)) < 1e-6
+    assert _rel(ug, u1) < 1e-10
