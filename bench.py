@@ -315,6 +315,40 @@ def fermion_measurement(fg, stream, rank, hbm_peak, dims=(16, 16, 16, 32)):
         ms = 1000 * (time.perf_counter() - t0)
         trajs[f"nested_{outer}_over_{m}x{inner}_dt_{dt}"] = {"dH": r["dH"], "ms": ms, "solves": r["n_solves"],
                                                             "cg_iterations": r["cg_iters"]}
+    # the same solves and one FG trajectory with half-precision links in the inner solver
+    half = {}
+    lat16 = fg.Lattice(dims, 5.6, kappa=0.158, precision="fp32_fp16cg", cg_tol=1e-10, seed=400 + rank,
+                       stream=stream)
+    lat16.set_gauge(u)
+    lat16.cg_solve(bs[0])
+    its16, ru16, res16 = 0, 0, 0.0
+    t0 = time.perf_counter()
+    for k in range(solves):
+        _, info = lat16.cg_solve(bs[1 + k])
+        its16 += info["iterations"]
+        ru16 += info["reliable_updates"]
+        res16 = max(res16, info["true_residual"])
+    half["ms_per_solve"] = 1000 * (time.perf_counter() - t0) / solves
+    half["cg_iterations_per_solve"] = its16 / solves
+    half["reliable_updates_per_solve"] = ru16 / solves
+    half["true_residual_max"] = res16
+    lat16.timing(True)
+    lat16.timing_reset()
+    lat16.cg_solve(bs[-1])
+    half["device_ms_per_solve_by_class"] = {c: lat16.kernel_time(c)[0]
+                                            for c in ("dslash", "dslash_df", "dslash_fp64", "cg_blas", "convert")}
+    d16_ms, d16_n = lat16.kernel_time("dslash")
+    half["dslash_avg_launch_us"] = 1000.0 * d16_ms / max(d16_n, 1)
+    lat16.timing(False)
+    lat16.set_gauge(u)
+    lat16.set_momenta(p0)
+    lat16.set_pseudofermion(chi)
+    torch_sync()
+    t0 = time.perf_counter()
+    r = lat16.trajectory("fg", 0.1, TAU, refresh=False, u_accept=0.0)
+    half["fg_dt_0.1"] = {"dH": r["dH"], "ms": 1000 * (time.perf_counter() - t0), "solves": r["n_solves"],
+                         "cg_iterations": r["cg_iters"]}
+    lat16.close()
     lat64 = fg.Lattice(dims, 5.6, kappa=0.158, precision="fp64", cg_tol=1e-10, seed=400 + rank, stream=stream)
     lat64.set_gauge(u)
     lat64.set_momenta(p0)
@@ -348,6 +382,7 @@ def fermion_measurement(fg, stream, rank, hbm_peak, dims=(16, 16, 16, 32)):
                             "gflops": DSLASH_FLOP * vh / avg / 1e9},
         "cg_blas_ms_share": cls["cg_blas"][0] / max(sum(v[0] for v in cls.values()), 1e-9),
         "trajectories": trajs,
+        "half_precision_links_in_cg": half,
         "trajectories_note": "one FG trajectory per entry from the same links, momenta and chi; FP32 "
                              "links/forces with the mixed solver vs the FP64 path; ms is wall clock",
     }

@@ -94,10 +94,16 @@ typedef enum {
 } fg_integrator;
 
 /* Arithmetic of the bulk fields (links, momenta, forces, CG inner vectors).
- * Action, kinetic and dH sums and the CG outer residual are FP64 always. */
+ * Action, kinetic and dH sums and the CG outer residual are FP64 always.
+ * FG_FP32_FP16CG is FG_FP32 whose inner CG iterations read a half-precision
+ * copy of the links (made at the start of every solve; entries of SU(3)
+ * matrices lie in [-1, 1], so no scale is needed): the dominant link bytes
+ * of the inner Dslash halve, and the reliable updates, which use the FP32
+ * links, correct the ~5e-4 relative error of the inner operator. */
 typedef enum {
   FG_FP64 = 0,
-  FG_FP32 = 1
+  FG_FP32 = 1,
+  FG_FP32_FP16CG = 2
 } fg_precision;
 
 typedef struct {

@@ -316,6 +316,9 @@ class Backend final : public IBackend {
   // (its Dslash temporaries reuse ax64_, te64_, to64_, which have the same size)
   void *xdf_ = nullptr, *bdf_ = nullptr;
   static constexpr bool kMixed = sizeof(R) < sizeof(double);
+  // inner CG Dslash on a half-precision copy of the links (FG_FP32_FP16CG)
+  void* U16_ = nullptr;
+  const bool half_links_ = kMixed && h_->prm.precision == FG_FP32_FP16CG;
   void *xs_ = nullptr, *rs_ = nullptr, *p_ = nullptr, *ap_ = nullptr, *te_ = nullptr, *to_ = nullptr;
   void *Xe_ = nullptr, *Xo_ = nullptr, *Ye_ = nullptr, *Yo_ = nullptr, *FF_ = nullptr;
   CgDev* cgd_ = nullptr;
@@ -693,6 +696,8 @@ class Backend final : public IBackend {
       if ((s = alloc(&xdf_, b64)) != FG_OK) return s;
       if ((s = alloc(&bdf_, b64)) != FG_OK) return s;
     }
+    // two bytes per real, NC complex entries per link
+    if (half_links_ && (s = alloc(&U16_, (size_t)4 * NC * g_.V * 4)) != FG_OK) return s;
     void** dR[] = {&xs_, &rs_, &p_, &ap_, &te_, &to_, &Xe_, &Xo_, &Ye_, &Yo_};
     for (void** p : dR)
       if ((s = alloc(p, bR)) != FG_OK) return s;
@@ -824,6 +829,17 @@ class Backend final : public IBackend {
     });
   }
 
+  // Dslash of the inner iterations: on the FP32 links, or with
+  // FG_FP32_FP16CG on their half-precision copy (then U is that copy).
+  cudaError_t inner_dslash(void* out, const void* in, const void* x, const void* pdot, const void* U, int out_par,
+                           int dag, int mode, double b, double* partial) {
+    if constexpr (kMixed) {
+      if (half_links_)
+        return launch_dslash<Half16, NC, R>(g_, out, in, x, pdot, U, out_par, dag, mode, b, partial, cgd_, st_);
+    }
+    return launch_dslash<R, NC, R>(g_, out, in, x, pdot, U, out_par, dag, mode, b, partial, cgd_, st_);
+  }
+
   // One CG iteration in the inner precision R: 4 Dslash + 2 vector kernels,
   // which all return at once after convergence (cgd_->done).  Raw launches,
   // usable inside stream capture.
@@ -831,14 +847,10 @@ class Backend final : public IBackend {
     const double k2 = h_->prm.kappa * h_->prm.kappa;
     const int n = nvec();
     cudaError_t e;
-    if ((e = launch_dslash<R, NC, R>(g_, to_, p_, nullptr, nullptr, U, 1, 0, 0, 1.0, nullptr, cgd_, st_)) != cudaSuccess)
-      return e;
-    if ((e = launch_dslash<R, NC, R>(g_, te_, to_, p_, nullptr, U, 0, 0, 1, -k2, nullptr, cgd_, st_)) != cudaSuccess)
-      return e;
-    if ((e = launch_dslash<R, NC, R>(g_, to_, te_, nullptr, nullptr, U, 1, 1, 0, 1.0, nullptr, cgd_, st_)) != cudaSuccess)
-      return e;
-    if ((e = launch_dslash<R, NC, R>(g_, ap_, to_, te_, p_, U, 0, 1, 2, -k2, part_pap_, cgd_, st_)) != cudaSuccess)
-      return e;
+    if ((e = inner_dslash(to_, p_, nullptr, nullptr, U, 1, 0, 0, 1.0, nullptr)) != cudaSuccess) return e;
+    if ((e = inner_dslash(te_, to_, p_, nullptr, U, 0, 0, 1, -k2, nullptr)) != cudaSuccess) return e;
+    if ((e = inner_dslash(to_, te_, nullptr, nullptr, U, 1, 1, 0, 1.0, nullptr)) != cudaSuccess) return e;
+    if ((e = inner_dslash(ap_, to_, te_, p_, U, 0, 1, 2, -k2, part_pap_)) != cudaSuccess) return e;
     if ((e = launch_cg_axpy<R>(xs_, rs_, p_, ap_, cgd_, part_rr_, n, st_)) !=
         cudaSuccess)
       return e;
@@ -852,18 +864,16 @@ class Backend final : public IBackend {
     const double k2 = h_->prm.kappa * h_->prm.kappa;
     const int n = nvec();
     fg_status s;
-    if ((s = run(KC_DSLASH, [&] {
-           return launch_dslash<R, NC, R>(g_, to_, p_, nullptr, nullptr, U, 1, 0, 0, 1.0, nullptr, cgd_, st_);
-         })) != FG_OK) return s;
-    if ((s = run(KC_DSLASH, [&] {
-           return launch_dslash<R, NC, R>(g_, te_, to_, p_, nullptr, U, 0, 0, 1, -k2, nullptr, cgd_, st_);
-         })) != FG_OK) return s;
-    if ((s = run(KC_DSLASH, [&] {
-           return launch_dslash<R, NC, R>(g_, to_, te_, nullptr, nullptr, U, 1, 1, 0, 1.0, nullptr, cgd_, st_);
-         })) != FG_OK) return s;
-    if ((s = run(KC_DSLASH, [&] {
-           return launch_dslash<R, NC, R>(g_, ap_, to_, te_, p_, U, 0, 1, 2, -k2, part_pap_, cgd_, st_);
-         })) != FG_OK) return s;
+    if ((s = run(KC_DSLASH, [&] { return inner_dslash(to_, p_, nullptr, nullptr, U, 1, 0, 0, 1.0, nullptr); })) !=
+        FG_OK)
+      return s;
+    if ((s = run(KC_DSLASH, [&] { return inner_dslash(te_, to_, p_, nullptr, U, 0, 0, 1, -k2, nullptr); })) != FG_OK)
+      return s;
+    if ((s = run(KC_DSLASH, [&] { return inner_dslash(to_, te_, nullptr, nullptr, U, 1, 1, 0, 1.0, nullptr); })) !=
+        FG_OK)
+      return s;
+    if ((s = run(KC_DSLASH, [&] { return inner_dslash(ap_, to_, te_, p_, U, 0, 1, 2, -k2, part_pap_); })) != FG_OK)
+      return s;
     if ((s = run(KC_CG_BLAS, [&] {
            return launch_cg_axpy<R>(xs_, rs_, p_, ap_, cgd_, part_rr_, n, st_);
          })) != FG_OK) return s;
@@ -997,6 +1007,12 @@ class Backend final : public IBackend {
     if ((s = run(KC_REDUCE, [&] { return launch_cg_init(part_rr_, nbv, cgd_, tol * tol, bbp, st_); })) != FG_OK) return s;
     if (cudaMemcpyAsync(p_, rs_, (size_t)n * sizeof(C2), cudaMemcpyDeviceToDevice, st_) != cudaSuccess)
       return cuda_fail("cg setup");
+    // the inner iterations' links: the FP32 field, or its half-precision copy
+    const void* Uin = U;
+    if (half_links_) {
+      if ((s = run(KC_CONVERT, [&] { return launch_links_to_half<NC>(g_, U, U16_, st_); })) != FG_OK) return s;
+      Uin = U16_;
+    }
     st->iters = 0;
     st->nru = 0;
     st->true_res = 0.0;
@@ -1043,7 +1059,7 @@ class Backend final : public IBackend {
           nb = per_delta >= 16.0 ? 8 : (per_delta >= 8.0 ? 4 : (per_delta >= 4.0 ? 2 : 1));
         }
         nb = std::min(nb, maxiter - queued);
-        if ((s = cg_batch(U, nb)) != FG_OK) return s;
+        if ((s = cg_batch(Uin, nb)) != FG_OK) return s;
         queued += nb;
         const int slot = (pending + 1) & 1;
         if (cudaEventRecord(ev_[slot], st_) != cudaSuccess) return cuda_fail("event");

@@ -884,6 +884,34 @@ FG_INST_F(float, 9, float)
 FG_INST_F(float, 6, float)
 FG_INST_F(float, 9, double)
 FG_INST_F(float, 6, double)
+template cudaError_t launch_dslash<Half16, 9, float>(const GeomH&, void*, const void*, const void*,
+                                                     const void*, const void*, int, int, int, double, double*,
+                                                     CgDev*, cudaStream_t);
+template cudaError_t launch_dslash<Half16, 6, float>(const GeomH&, void*, const void*, const void*,
+                                                     const void*, const void*, int, int, int, double, double*,
+                                                     CgDev*, cudaStream_t);
+
+template <int NC>
+__global__ void __launch_bounds__(256) links_to_half_kernel(Gauge<float, NC> in, Gauge<Half16, NC> out, int V) {
+  const int s = blockIdx.x * 64 + threadIdx.x;
+  const int mu = threadIdx.y;
+  if (s >= V) return;
+  out.store(mu, s, in.load(mu, s));
+}
+template <int NC>
+cudaError_t launch_links_to_half(const GeomH& gh, const void* U32, void* U16, cudaStream_t st) {
+  Gauge<float, NC> a;
+  a.p = const_cast<void*>(U32);
+  a.V = gh.V;
+  Gauge<Half16, NC> b;
+  b.p = U16;
+  b.V = gh.V;
+  links_to_half_kernel<NC><<<(gh.V + 63) / 64, dim3(64, 4), 0, st>>>(a, b, gh.V);
+  return cudaGetLastError();
+}
+template cudaError_t launch_links_to_half<9>(const GeomH&, const void*, void*, cudaStream_t);
+template cudaError_t launch_links_to_half<6>(const GeomH&, const void*, void*, cudaStream_t);
+
 template cudaError_t launch_dslash<float, 9, DF>(const GeomH&, void*, const void*, const void*, const void*,
                                                  const void*, int, int, int, double, double*, CgDev*, cudaStream_t);
 template cudaError_t launch_dslash<float, 6, DF>(const GeomH&, void*, const void*, const void*, const void*,

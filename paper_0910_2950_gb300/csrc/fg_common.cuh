@@ -12,6 +12,7 @@
 //   spinor  Pair[6][Vh]         entries spin * 3 + colour, two per pair, one parity
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -479,6 +480,52 @@ template <typename R, int NC> struct Gauge {
       v.x = m.e[2][2].re;
       v.y = m.e[2][2].im;
       tail[(size_t)mu * V + s] = v;
+    }
+  }
+};
+
+// Links stored in IEEE half precision for the inner Dslash of the solver
+// (entries of an SU(3) matrix lie in [-1, 1], so half keeps ~5e-4 relative
+// precision and needs no scale).  Same layout as Gauge<float, NC> with two
+// bytes per real: a pair of entries is 8 bytes, the NC = 9 tail 4 bytes.
+// Loads return FP32 matrices.
+struct Half16 {};
+template <int NC> struct Gauge<Half16, NC> {
+  static constexpr int NP = NC / 2;
+  void* __restrict__ p;
+  int V;
+  static __device__ __forceinline__ Cx<float> cx_of(unsigned int w) {
+    const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w));
+    return cx<float>(f.x, f.y);
+  }
+  static __device__ __forceinline__ unsigned int word_of(const Cx<float>& c) {
+    const __half2 h = __floats2half2_rn(c.re, c.im);
+    return *reinterpret_cast<const unsigned int*>(&h);
+  }
+  __device__ __forceinline__ M3<float> load(int mu, int s) const {
+    M3<float> m;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      const uint2 v = __ldg((const uint2*)p + ((size_t)mu * NP + q) * V + s);
+      m.e[(2 * q) / 3][(2 * q) % 3] = cx_of(v.x);
+      m.e[(2 * q + 1) / 3][(2 * q + 1) % 3] = cx_of(v.y);
+    }
+    if (NC == 9) {
+      const unsigned int* tail = (const unsigned int*)((const char*)p + (size_t)4 * NP * V * 8);
+      m.e[2][2] = cx_of(__ldg(tail + (size_t)mu * V + s));
+    } else {
+      rebuild_row2(m);
+    }
+    return m;
+  }
+  __device__ __forceinline__ void store(int mu, int s, const M3<float>& m) const {
+#pragma unroll
+    for (int q = 0; q < NP; ++q)
+      ((uint2*)p)[((size_t)mu * NP + q) * V + s] =
+          make_uint2(word_of(m.e[(2 * q) / 3][(2 * q) % 3]), word_of(m.e[(2 * q + 1) / 3][(2 * q + 1) % 3]));
+    if (NC == 9) {
+      unsigned int* tail = (unsigned int*)((char*)p + (size_t)4 * NP * V * 8);
+      tail[(size_t)mu * V + s] = word_of(m.e[2][2]);
     }
   }
 };

@@ -43,6 +43,10 @@ cudaError_t launch_dslash(const GeomH& g, void* out, const void* in, const void*
                           const void* U, int out_par, int dag, int mode, double b, double* partial,
                           CgDev* cgd, cudaStream_t st);
 
+// Half-precision copy of FP32 links (NC entries per link) for the inner Dslash.
+template <int NC>
+cudaError_t launch_links_to_half(const GeomH& g, const void* U32, void* U16, cudaStream_t st);
+
 // Pseudofermion force (8 Gell-Mann components per link) into FF (momentum
 // layout, precision RL); accumulate != 0 adds to FF.
 template <typename RL, int NC, typename RS>

@@ -85,19 +85,22 @@ def footprint_bytes(spec: ChainSpec, precision: str = "fp32", link_reals: int = 
     FP64 and 10 working half-lattice spinors (plus 2 double-float ones for the
     FP32 solver's reliable updates), the pseudofermion force, the CG scalars
     and the Dslash / vector block partials.  4 KiB are added for allocator
-    rounding of the small buffers."""
+    rounding of the small buffers.  (The closed-form force gradient's
+    buffers are not included: the server does not offer that integrator.)"""
     v = int(np.prod(spec.dims))
-    r = 4 if precision == "fp32" else 8
+    r = 8 if precision == "fp64" else 4
     gauge = 4 * v * link_reals * r
     mom = 4 * v * 8 * r
     total = 3 * gauge + 2 * mom + 8 * v + 4 * 8 * ((v + 255) // 256 + 1) + 32 * 8 + 4 * v * 18 * 8
     if spec.kappa > 0:
         vh = v // 2
         nvec = 12 * vh
-        n64 = 8 + (2 if precision == "fp32" else 0)
+        n64 = 8 + (2 if precision != "fp64" else 0)
         dslash_blocks = (vh + 127) // 128
         vec_blocks = min((nvec + 255) // 256, 152 * 8)
         total += n64 * nvec * 16 + 10 * nvec * 2 * r + mom + 128 + 8 * (dslash_blocks + vec_blocks + 2)
+        if precision == "fp32_fp16cg":
+            total += 4 * v * link_reals * 2      # half-precision links of the inner solver
     return total + 4096
 
 

@@ -67,7 +67,7 @@ def test_apply_mhat_fp32_links_in_fp64_arithmetic(fgmod):
     assert _rel(out, ref) < 1e-13
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_fp16cg"])
 @pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 2, 6)])
 def test_cg_solve(fgmod, precision, dims):
     u = inputs.hot_start(dims, 5)
@@ -78,9 +78,9 @@ def test_cg_solve(fgmod, precision, dims):
         x, info = lat.cg_solve(b)
     assert info["true_residual"] <= tol
     assert info["iterations"] > 0
-    if precision == "fp32":
+    if precision != "fp64":
         assert info["reliable_updates"] >= 1
-    uu = u.astype(np.complex64).astype(np.complex128) if precision == "fp32" else u
+    uu = u.astype(np.complex64).astype(np.complex128) if precision != "fp64" else u
     full_x = inputs.unpack_even(x, dims)
     res = inputs.unpack_even(b, dims) - fe.mdagm(uu, 0.158, full_x)
     assert np.linalg.norm(res) <= 1.01 * tol * np.linalg.norm(b)
@@ -258,9 +258,10 @@ def test_fermion_fg_trajectory_dh_fp64(fgmod, fermion_traj_oracle, dt):
     assert r["cg_iters"] > 0
 
 
-def test_fermion_fg_trajectory_fp32_mixed(fgmod, fermion_traj_oracle):
+@pytest.mark.parametrize("precision", ["fp32", "fp32_fp16cg"])
+def test_fermion_fg_trajectory_fp32_mixed(fgmod, fermion_traj_oracle, precision):
     dims, u, p, chi, ref = fermion_traj_oracle
-    with fgmod.Lattice(dims, BETA, kappa=KAPPA, precision="fp32", cg_tol=1e-10,
+    with fgmod.Lattice(dims, BETA, kappa=KAPPA, precision=precision, cg_tol=1e-10,
                        cg_tol_action=1e-12) as lat:
         lat.set_gauge(u)
         lat.set_pseudofermion(chi)

@@ -151,12 +151,13 @@ def test_mhat_16x16x16x32_fp32_links(fgmod, nf2_case):
     assert np.max(np.abs(outd - refd)) < 1e-13 * np.max(np.abs(refd))
 
 
-def test_cg_and_force_16x16x16x32(fgmod, nf2_case):
+@pytest.mark.parametrize("precision", ["fp32", "fp32_fp16cg"])
+def test_cg_and_force_16x16x16x32(fgmod, nf2_case, precision):
     dims, u, u32 = nf2_case
     kappa, tol = 0.158, 1e-10
     chi = inputs.gaussian_spinor_even(dims, 4)
     phi = fe.heatbath_phi(u32, kappa, inputs.unpack_even(chi, dims))
-    with fgmod.Lattice(dims, 5.6, kappa=kappa, precision="fp32", cg_tol=tol) as lat:
+    with fgmod.Lattice(dims, 5.6, kappa=kappa, precision=precision, cg_tol=tol) as lat:
         lat.set_gauge(u)
         lat.set_pseudofermion(chi)
         x, info = lat.cg_solve(inputs.pack_even(phi, dims))

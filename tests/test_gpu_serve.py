@@ -70,14 +70,15 @@ def test_alone_and_in_the_mix_gpu(fgmod):
 @pytest.mark.parametrize("spec", [serve.ChainSpec((8, 8, 8, 8), 6.0, 0.0, 1),
                                   serve.ChainSpec((8, 8, 8, 16), 5.6, 0.157, 2),
                                   serve.ChainSpec((6, 6, 6, 12), 5.6, 0.155, 3)])
-def test_footprint_bounds_the_library_allocation(fgmod, spec):
+@pytest.mark.parametrize("precision", ["fp32", "fp32_fp16cg", "fp64"])
+def test_footprint_bounds_the_library_allocation(fgmod, spec, precision):
     """Admission by HBM footprint is only safe if the estimate is an upper
     bound of what a chain's handle holds after a trajectory (all lazy
     buffers allocated), and it should not waste much of the budget."""
-    with fgmod.Lattice(spec.dims, spec.beta, kappa=spec.kappa, precision="fp32", seed=spec.seed) as lat:
+    with fgmod.Lattice(spec.dims, spec.beta, kappa=spec.kappa, precision=precision, seed=spec.seed) as lat:
         lat.random_gauge()
         lat.trajectory("fg", 0.25, 1.0, refresh=True, u_accept=0.0)
         lat.get_gauge()
         held = lat.device_bytes()
-    est = serve.footprint_bytes(spec, "fp32")
+    est = serve.footprint_bytes(spec, precision)
     assert held <= est <= 1.15 * held, (held, est)
