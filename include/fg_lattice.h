@@ -99,7 +99,8 @@ typedef enum {
  * copy of the links (made at the start of every solve; entries of SU(3)
  * matrices lie in [-1, 1], so no scale is needed): the dominant link bytes
  * of the inner Dslash halve, and the reliable updates, which use the FP32
- * links, correct the ~5e-4 relative error of the inner operator. */
+ * links, correct the ~5e-4 relative error of the inner operator (at least
+ * every factor 0.1 of residual reduction, whatever cg_delta says). */
 typedef enum {
   FG_FP64 = 0,
   FG_FP32 = 1,
