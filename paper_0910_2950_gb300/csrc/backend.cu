@@ -65,6 +65,8 @@ class Backend final : public IBackend {
     if ((s = alloc(&P_, mom_bytes)) != FG_OK) return s;
     if ((s = alloc(&F_, mom_bytes)) != FG_OK) return s;
     if ((s = alloc((void**)&h0_, V * sizeof(double))) != FG_OK) return s;
+    for (int k = 0; k < 2; ++k)
+      if ((s = alloc((void**)&sgc_[k], V * sizeof(double))) != FG_OK) return s;
     const size_t nb = (V + 255) / 256 + 1;
     if ((s = alloc((void**)&partial_, 4 * nb * sizeof(double))) != FG_OK) return s;
     if ((s = alloc((void**)&dout_, 32 * sizeof(double))) != FG_OK) return s;
@@ -89,6 +91,7 @@ class Backend final : public IBackend {
     s = run(KC_CONVERT, [&] { return launch_gauge_to_device<R, NC>(g_, canon_, U_, st_); });
     if (s != FG_OK) return s;
     sf0_valid_ = false;
+    sgc_valid_ = false;
     return sync();
   }
   fg_status get_gauge(double* host) override {
@@ -184,6 +187,7 @@ class Backend final : public IBackend {
     fg_status s = run(KC_DRIFT, [&] { return launch_reunitarize<R, NC>(g_, U_, st_); });
     if (s != FG_OK) return s;
     sf0_valid_ = false;
+    sgc_valid_ = false;
     return sync();
   }
 
@@ -192,6 +196,7 @@ class Backend final : public IBackend {
     fg_status s = run(KC_CONVERT, [&] { return launch_random_links<R, NC>(g_, U_, h_->prm.seed, d, st_); });
     if (s != FG_OK) return s;
     sf0_valid_ = false;
+    sgc_valid_ = false;
     return sync();
   }
   fg_status set_rng_position(unsigned long long pos) override {
@@ -207,6 +212,7 @@ class Backend final : public IBackend {
     fg_status s = execute(ops, dt, nullptr);
     if (s != FG_OK) return s;
     sf0_valid_ = false;
+    sgc_valid_ = false;
     return sync();
   }
 
@@ -240,13 +246,18 @@ class Backend final : public IBackend {
       }
       sf0 = sf0_;
     }
-    // H at the start: per-site energies kept for the site-by-site dH sum
-    if ((s = energy(0, P_, 0)) != FG_OK) return s;
+    // H at the start: per-site energies kept for the site-by-site dH sum.
+    // The per-site gauge action of these links was stored at the end of the
+    // previous trajectory unless the links changed since; then only the
+    // kinetic term is new.
+    if ((s = energy(0, P_, 0, sgc_valid_ ? sgc_[sgc_cur_] : nullptr, sgc_valid_ ? nullptr : sgc_[sgc_cur_])) !=
+        FG_OK)
+      return s;
     // The start field is never written during the trajectory (see execute),
     // so a rejection only has to point back at it.
     void* const start = U_;
     if ((s = execute(ops, dt, start)) != FG_OK) return s;
-    if ((s = energy(1, P_, 3)) != FG_OK) return s;
+    if ((s = energy(1, P_, 3, nullptr, sgc_[1 - sgc_cur_])) != FG_OK) return s;
     if ((s = fetch(6)) != FG_OK) return s;
     double o[6];
     std::memcpy(o, host_out_, sizeof(o));
@@ -267,6 +278,9 @@ class Backend final : public IBackend {
     r->cg_iters = cg_iters_;
     const double u = (u_accept < 0.0) ? host_uniform() : u_accept;
     r->accepted = std::isfinite(r->dH) && (r->dH <= 0.0 || u < std::exp(-r->dH));
+    // the stored per-site gauge action follows the links kept
+    if (r->accepted) sgc_cur_ = 1 - sgc_cur_;
+    sgc_valid_ = true;
     if (!r->accepted) {
       U_ = start;
       sf0_ = sf0;             // phi unchanged and the links are back: S_F is S_F0 again
@@ -295,6 +309,12 @@ class Backend final : public IBackend {
   void* P_ = nullptr;
   void* F_ = nullptr;
   double* h0_ = nullptr;
+  // per-site gauge action of the current links (sgc_[sgc_cur_]) and of the
+  // end of the running trajectory (the other one); valid while only
+  // trajectories have moved the links
+  double* sgc_[2] = {nullptr, nullptr};
+  int sgc_cur_ = 0;
+  bool sgc_valid_ = false;
   double* partial_ = nullptr;
   double* dout_ = nullptr;
   double* canon_ = nullptr;
@@ -385,10 +405,10 @@ class Backend final : public IBackend {
   }
 
   // energy kernel + fixed-order reduction into dout_[off .. off+2]
-  fg_status energy(int mode, const void* P, int off) {
+  fg_status energy(int mode, const void* P, int off, const double* sg_in = nullptr, double* sg_out = nullptr) {
     int nb = 0;
     fg_status s = run(KC_ENERGY, [&] {
-      return launch_energy<R, NC>(g_, U_, P, h_->prm.beta, mode, h0_, partial_, &nb, st_);
+      return launch_energy<R, NC>(g_, U_, P, h_->prm.beta, mode, h0_, partial_, &nb, st_, sg_in, sg_out);
     });
     if (s != FG_OK) return s;
     return run(KC_REDUCE, [&] { return launch_reduce(partial_, nb, 3, dout_ + off, 0, st_); });

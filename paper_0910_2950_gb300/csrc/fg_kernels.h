@@ -72,9 +72,12 @@ cudaError_t launch_reunitarize(const GeomH& g, void* U, cudaStream_t st);
 // Per-site energy h(x) = T(x) + S_G(x) (T = 0 if P is null).  mode 0: also
 // store h0[x] = h(x); mode 1: also sum h(x) - h0[x]; mode 2: sums only.  Writes per-block partial sums of
 // (S_G, T, dh) into partial[3][nblocks]; returns nblocks in *nblocks.
+// sg_in (optional): per-site S_G of these links stored earlier, used instead
+// of the plaquettes; sg_out (optional): per-site S_G stored for later.
 template <typename R, int NC>
 cudaError_t launch_energy(const GeomH& g, const void* U, const void* P, double beta, int mode,
-                          double* h0, double* partial, int* nblocks, cudaStream_t st);
+                          double* h0, double* partial, int* nblocks, cudaStream_t st,
+                          const double* sg_in = nullptr, double* sg_out = nullptr);
 
 // out[k] += sum_b partial[k][b] for k < nv (fixed order, one block).  If
 // `accumulate` is 0 the sums overwrite out[k].

@@ -111,10 +111,12 @@ template <typename R, int NC>
 __global__ void __launch_bounds__(kEnergyThreads) energy_kernel(Gauge<R, NC> U, Mom<R> P, Geom g,
                                                                 double beta, int mode,
                                                                 double* __restrict__ h0,
-                                                                double* __restrict__ partial) {
+                                                                double* __restrict__ partial,
+                                                                const double* __restrict__ sg_in,
+                                                                double* __restrict__ sg_out) {
   int s;
   double v[3] = {0.0, 0.0, 0.0};  // S_G, T, dh
-  if (pair_site<kEnergyThreads / 2>(g, s)) site_energy(U, P, g, s, beta, mode, h0, v);
+  if (pair_site<kEnergyThreads / 2>(g, s)) site_energy(U, P, g, s, beta, mode, h0, v, sg_in, sg_out);
   block_reduce_store<3>(v, partial, gridDim.x);
 }
 
@@ -303,11 +305,12 @@ cudaError_t launch_reunitarize(const GeomH& gh, void* U, cudaStream_t st) {
 
 template <typename R, int NC>
 cudaError_t launch_energy(const GeomH& gh, const void* U, const void* P, double beta, int mode,
-                          double* h0, double* partial, int* nblocks, cudaStream_t st) {
+                          double* h0, double* partial, int* nblocks, cudaStream_t st, const double* sg_in,
+                          double* sg_out) {
   const int nb = (gh.Vh + kEnergyThreads / 2 - 1) / (kEnergyThreads / 2);
   *nblocks = nb;
   energy_kernel<R, NC><<<nb, kEnergyThreads, 0, st>>>(gauge_of<R, NC>(U, gh.V), mom_of<R>(P, gh.V),
-                                                      to_dev(gh), beta, mode, h0, partial);
+                                                      to_dev(gh), beta, mode, h0, partial, sg_in, sg_out);
   return cudaGetLastError();
 }
 
@@ -379,7 +382,8 @@ template cudaError_t launch_kick_ff<float>(const GeomH&, void*, const void*, dou
   template cudaError_t launch_unit_links<R, NC>(const GeomH&, void*, cudaStream_t);                 \
   template cudaError_t launch_random_links<R, NC>(const GeomH&, void*, uint64_t, uint32_t, cudaStream_t); \
   template cudaError_t launch_energy<R, NC>(const GeomH&, const void*, const void*, double, int,    \
-                                            double*, double*, int*, cudaStream_t);                  \
+                                            double*, double*, int*, cudaStream_t, const double*,    \
+                                            double*);                                               \
   template cudaError_t launch_gauge_to_device<R, NC>(const GeomH&, const double*, void*,            \
                                                      cudaStream_t);                                 \
   template cudaError_t launch_gauge_to_canon<R, NC>(const GeomH&, const void*, double*, cudaStream_t);

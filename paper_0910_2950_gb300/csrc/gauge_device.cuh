@@ -3,6 +3,7 @@
 // (batch.cu), so that a chain in a batch runs the same arithmetic.
 #pragma once
 
+#include "df64.cuh"
 #include "fg_common.cuh"
 #include "fg_kernels.h"
 
@@ -111,34 +112,60 @@ __device__ __forceinline__ void drift_link(const Gauge<R, NC>& Uin, const Mom<R>
 
 // Per-site energy h(x) = T(x) + S_G(x) in FP64 (T = 0 if P is null): v[0] = S_G(x),
 // v[1] = T(x); mode 0 stores h0[s] = h(x), mode 1 sets v[2] = h(x) - h0[s].
+// If sg_in is given, S_G(x) is read from it instead of recomputed (the links
+// have not changed since it was stored); if sg_out is given, S_G(x) is stored.
 template <typename R, int NC>
 __device__ __forceinline__ void site_energy(const Gauge<R, NC>& U, const Mom<R>& P, const Geom& g, int s,
-                                            double beta, int mode, double* __restrict__ h0, double v[3]) {
+                                            double beta, int mode, double* __restrict__ h0, double v[3],
+                                            const double* __restrict__ sg_in = nullptr,
+                                            double* __restrict__ sg_out = nullptr) {
   int c[4], par;
   cb_coords(g, s, c, par);
+  // Sums of FP32 terms are taken in double-float (each p^2 split exactly by
+  // an FMA, each plaquette trace added with two_sum): as accurate as FP64
+  // sums to ~1e-14 relative, without GB300's slow FP64 unit; FP64 fields
+  // keep FP64 sums.
+  constexpr bool kDF = sizeof(R) == sizeof(float);
   double t = 0.0;
   if (P.p != nullptr) {
+    DF tdf(0.0f);
 #pragma unroll 1
     for (int mu = 0; mu < 4; ++mu) {
       R p[8];
       P.load(mu, s, p);
 #pragma unroll
-      for (int k = 0; k < 8; ++k) t += double(p[k]) * double(p[k]);
+      for (int k = 0; k < 8; ++k) {
+        if constexpr (kDF) {
+          const float sq = __fmul_rn(p[k], p[k]);
+          tdf = tdf + DF(sq, __fmaf_rn(p[k], p[k], -sq));
+        } else {
+          t += double(p[k]) * double(p[k]);
+        }
+      }
     }
+    if constexpr (kDF) t = double(tdf);
     t *= 0.5;
   }
   double sg = 0.0;
+  if (sg_in != nullptr) {
+    sg = sg_in[s];
+  } else {
+    DF trdf(0.0f);
 #pragma unroll
-  for (int mu = 0; mu < 4; ++mu) {
-    const M3<R> umu = U.load(mu, s);
+    for (int mu = 0; mu < 4; ++mu) {
+      const M3<R> umu = U.load(mu, s);
 #pragma unroll
-    for (int nu = mu + 1; nu < 4; ++nu) {
-      const M3<R> a = mul(umu, U.load(nu, cb_neighbor(g, c, mu, +1)));
-      const M3<R> b = mul(U.load(nu, s), U.load(mu, cb_neighbor(g, c, nu, +1)));
-      sg += 1.0 - double(re_tr_mul_nd(a, b)) * (1.0 / 3.0);
+      for (int nu = mu + 1; nu < 4; ++nu) {
+        const M3<R> a = mul(umu, U.load(nu, cb_neighbor(g, c, mu, +1)));
+        const M3<R> b = mul(U.load(nu, s), U.load(mu, cb_neighbor(g, c, nu, +1)));
+        if constexpr (kDF) trdf = trdf + DF(float(re_tr_mul_nd(a, b)));
+        else sg += 1.0 - double(re_tr_mul_nd(a, b)) * (1.0 / 3.0);
+      }
     }
+    if constexpr (kDF) sg = 6.0 - double(trdf) * (1.0 / 3.0);
+    sg *= beta;
   }
-  sg *= beta;
+  if (sg_out != nullptr) sg_out[s] = sg;
   v[0] = sg;
   v[1] = t;
   const double h = sg + t;

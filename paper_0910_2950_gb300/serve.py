@@ -80,7 +80,8 @@ class Result:
 
 def footprint_bytes(spec: ChainSpec, precision: str = "fp32", link_reals: int = 18) -> int:
     """Device bytes a chain holds, from the library's allocation plan: three
-    link buffers, momenta and force, per-site energies, block partials and
+    link buffers, momenta and force, per-site energies and the stored per-site
+    gauge actions, block partials and
     result scalars, the FP64 host-layout staging buffer, and for fermions 8
     FP64 and 10 working half-lattice spinors (plus 2 double-float ones for the
     FP32 solver's reliable updates), the pseudofermion force, the CG scalars
@@ -91,7 +92,7 @@ def footprint_bytes(spec: ChainSpec, precision: str = "fp32", link_reals: int = 
     r = 8 if precision == "fp64" else 4
     gauge = 4 * v * link_reals * r
     mom = 4 * v * 8 * r
-    total = 3 * gauge + 2 * mom + 8 * v + 4 * 8 * ((v + 255) // 256 + 1) + 32 * 8 + 4 * v * 18 * 8
+    total = 3 * gauge + 2 * mom + 3 * 8 * v + 4 * 8 * ((v + 255) // 256 + 1) + 32 * 8 + 4 * v * 18 * 8
     if spec.kappa > 0:
         vh = v // 2
         nvec = 12 * vh

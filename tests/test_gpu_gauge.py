@@ -235,3 +235,29 @@ def test_timing_and_launch_count(fgmod):
         assert n == 13 and ms > 0
         assert n1 - n0 >= 13 + 1 + 2
         assert lat.device_bytes() > 0
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_stored_site_action_matches_recomputation(fgmod, precision):
+    """A trajectory takes the per-site gauge action of its start links from
+    the end of the previous trajectory (accepted or rejected) unless the links
+    changed in between.  A second lattice that re-uploads its links before
+    every trajectory (which drops the stored values) must see the same H0
+    and dH bit for bit, through accepts and rejects."""
+    dims = (6, 4, 4, 6)
+    u = inputs.hot_start(dims, 51)
+    ps = [inputs.gaussian_momenta(dims, 60 + k) for k in range(6)]
+    out = []
+    for reupload in (False, True):
+        rows = []
+        with fgmod.Lattice(dims, BETA, precision=precision) as lat:
+            lat.set_gauge(u)
+            for k, p in enumerate(ps):
+                if reupload:
+                    lat.set_gauge(lat.get_gauge())
+                lat.set_momenta(p)
+                r = lat.trajectory("fg", 0.5, 1.0, refresh=False, u_accept=0.9 if k % 2 else 0.0)
+                rows.append((r["H0"], r["dH"], r["accepted"]))
+        out.append(rows)
+    assert out[0] == out[1]
+    assert any(not a for _, _, a in out[0]) and any(a for _, _, a in out[0])
