@@ -324,9 +324,16 @@ constexpr int kDslashThreads = 128;
 
 // out = b D in (MODE 0), out = x + b D in (MODE 1), and MODE 2 also writes the
 // block partial sum of Re <pdot, out>.  `in` has parity 1 - out_par.
-// Resident blocks asked of the register allocator: the double-float hop is
-// latency-bound, so it is held to 128 registers for four blocks per SM.
+// Resident blocks asked of the register allocator.  The FP32 hop is bound by
+// memory latency: six blocks of 128 (80 registers, 24 warps per SM) beat the
+// unconstrained five (90 registers) by 8% at 16^3 x 32 and 24^3 x 48.  The
+// double-float hop is latency-bound in arithmetic, so it is held to 128
+// registers for four blocks per SM.
+#ifndef FG_DSLASH_MIN_BLOCKS
+#define FG_DSLASH_MIN_BLOCKS 6
+#endif
 template <typename RS> struct DslashMinBlocks { static constexpr int value = 1; };
+template <> struct DslashMinBlocks<float> { static constexpr int value = FG_DSLASH_MIN_BLOCKS; };
 #ifndef FG_DSLASH_DF_MIN_BLOCKS
 #define FG_DSLASH_DF_MIN_BLOCKS 4
 #endif
