@@ -288,6 +288,19 @@ def fermion_measurement(fg, stream, rank, hbm_peak, dims=(16, 16, 16, 32)):
     _, info = lat.cg_solve(bs[-1])
     cls = {c: lat.kernel_time(c) for c in ("dslash", "dslash_df", "dslash_fp64", "cg_blas", "reduce", "convert")}
     lat.timing(False)
+    # pseudofermion force kernel: compulsory bytes per link = U (72) + F^a out
+    # (32) + a quarter of the site's Xt and Yt spinors (2 x 96 / 4)
+    lat.set_pseudofermion(inputs.gaussian_spinor_even(dims, 20 + rank))
+    lat.timing(True)
+    lat.timing_reset()
+    lat.force()
+    ffk_ms, ffk_n = lat.kernel_time("fermion_force")
+    lat.timing(False)
+    ffk_s = ffk_ms / 1000.0 / max(ffk_n, 1)
+    ff_roof = {"bound": "hbm", "bytes_per_link": 152, "links_per_launch": 4 * 2 * vh,
+               "avg_launch_us": ffk_s * 1e6, "launches": ffk_n,
+               "achieved": 152 * 4 * 2 * vh / ffk_s / 1e9, "peak": hbm_peak, "unit": "GB/s"}
+    ff_roof["frac"] = ff_roof["achieved"] / hbm_peak
     # FG trajectories on the total force (tau = 1, dt = 0.1 and 0.05) from one
     # start (links, momenta, chi), and the FP64 path's dH for dt = 0.1
     chi = inputs.gaussian_spinor_even(dims, 21 + rank)
@@ -381,6 +394,7 @@ def fermion_measurement(fg, stream, rank, hbm_peak, dims=(16, 16, 16, 32)):
                             "sites_per_launch": vh, "avg_launch_us": avg * 1e6, "launches": ds_n,
                             "gflops": DSLASH_FLOP * vh / avg / 1e9},
         "cg_blas_ms_share": cls["cg_blas"][0] / max(sum(v[0] for v in cls.values()), 1e-9),
+        "fermion_force_roofline": ff_roof,
         "trajectories": trajs,
         "half_precision_links_in_cg": half,
         "trajectories_note": "one FG trajectory per entry from the same links, momenta and chi; FP32 "
