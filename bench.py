@@ -240,6 +240,9 @@ class ClockSampler:
 # ----------------------------------------------------------------------------- our arm
 # Dslash algorithmic bytes per output site (FP32, 18-real links): 8 neighbour
 # spinors (96 B) + 8 links (72 B) read, one spinor (96 B) written.
+# dram__bytes_read + write of the fused force kernel per link, FP32 18-real,
+# averaged over an FG trajectory's launch mix (ncu capture at 28^4)
+FORCE_TRAFFIC_BYTES_PER_LINK = 203
 DSLASH_BYTES_FP32_18 = 8 * 96 + 8 * 72 + 96
 # Compulsory bytes per output site of one FP32 Dslash (each of the 4V links is
 # read once per half-lattice hop, input and output spinors once): 8 * 72 + 96
@@ -633,9 +636,15 @@ def run_ours(args):
     esize = 4 if args.precision == "fp32" else 8
     bytes_per_launch = links * (args.link_reals * esize + 2 * 8 * esize)
     peak = FP32_PEAK_TFLOPS if args.precision == "fp32" else FP64_PEAK_TFLOPS
+    # DRAM bytes per link of the FP32 18-real FG mix from one ncu capture at
+    # 28^4 (profiles/gauge_force_fp32_28x4.md), scaled to this lattice
+    traffic = (FORCE_TRAFFIC_BYTES_PER_LINK * links
+               if (args.precision, args.link_reals, args.integrator) == ("fp32", 18, "fg") else None)
     roof = {"bound": "alu", "achieved": achieved, "peak": peak,
             "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None,
+            "traffic": traffic,
+            "traffic_note": "bytes per launch: 203 B/link measured by ncu at 28^4, scaled by links" if traffic
+            else None,
             "kernel": "gauge_force (fused staple force + kick/drift/displace)",
             "launches": force_n, "avg_launch_us": avg_launch_s * 1e6,
             "algorithmic_gbs": bytes_per_launch / avg_launch_s / 1e9,
