@@ -95,12 +95,15 @@ typedef enum {
 
 /* Arithmetic of the bulk fields (links, momenta, forces, CG inner vectors).
  * Action, kinetic and dH sums and the CG outer residual are FP64 always.
- * FG_FP32_FP16CG is FG_FP32 whose inner CG iterations read a half-precision
- * copy of the links (made at the start of every solve; entries of SU(3)
- * matrices lie in [-1, 1], so no scale is needed): the dominant link bytes
- * of the inner Dslash halve, and the reliable updates, which use the FP32
- * links, correct the ~5e-4 relative error of the inner operator (at least
- * every factor 0.1 of residual reduction, whatever cg_delta says). */
+ * FG_FP32_FP16CG is FG_FP32 whose inner CG iterates in half precision: the
+ * Dslash reads a half-precision copy of the links (made at the start of
+ * every solve; entries of SU(3) matrices lie in [-1, 1], so no scale is
+ * needed), and the residual, search direction and Dslash temporaries are
+ * stored as half precision scaled by 1/sigma, sigma^2 = |r|^2 / n reset at
+ * every reliable update (the solution increment stays FP32, arithmetic is
+ * FP32).  The reliable updates, on the FP32 links in double-float and FP64,
+ * correct the ~5e-4 relative error of the inner operator; they come at least
+ * every factor 0.1 of residual reduction, whatever cg_delta says. */
 typedef enum {
   FG_FP64 = 0,
   FG_FP32 = 1,

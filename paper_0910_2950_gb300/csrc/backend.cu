@@ -850,12 +850,13 @@ class Backend final : public IBackend {
   }
 
   // Dslash of the inner iterations: on the FP32 links, or with
-  // FG_FP32_FP16CG on their half-precision copy (then U is that copy).
+  // FG_FP32_FP16CG on their half-precision copy (then U is that copy) and
+  // half-precision spinors.
   cudaError_t inner_dslash(void* out, const void* in, const void* x, const void* pdot, const void* U, int out_par,
                            int dag, int mode, double b, double* partial) {
     if constexpr (kMixed) {
       if (half_links_)
-        return launch_dslash<Half16, NC, R>(g_, out, in, x, pdot, U, out_par, dag, mode, b, partial, cgd_, st_);
+        return launch_dslash_h16<Half16, NC>(g_, out, in, x, pdot, U, out_par, dag, mode, b, partial, cgd_, st_);
     }
     return launch_dslash<R, NC, R>(g_, out, in, x, pdot, U, out_par, dag, mode, b, partial, cgd_, st_);
   }
@@ -871,6 +872,10 @@ class Backend final : public IBackend {
     if ((e = inner_dslash(te_, to_, p_, nullptr, U, 0, 0, 1, -k2, nullptr)) != cudaSuccess) return e;
     if ((e = inner_dslash(to_, te_, nullptr, nullptr, U, 1, 1, 0, 1.0, nullptr)) != cudaSuccess) return e;
     if ((e = inner_dslash(ap_, to_, te_, p_, U, 0, 1, 2, -k2, part_pap_)) != cudaSuccess) return e;
+    if (half_links_) {
+      if ((e = launch_cg_axpy_h16(xs_, rs_, p_, ap_, cgd_, part_rr_, n, st_)) != cudaSuccess) return e;
+      return launch_cg_xpay_h16(p_, rs_, cgd_, mapped_->hist, &mapped_->dev_iter, h_->prm.cg_maxiter, n, st_);
+    }
     if ((e = launch_cg_axpy<R>(xs_, rs_, p_, ap_, cgd_, part_rr_, n, st_)) !=
         cudaSuccess)
       return e;
@@ -894,6 +899,14 @@ class Backend final : public IBackend {
       return s;
     if ((s = run(KC_DSLASH, [&] { return inner_dslash(ap_, to_, te_, p_, U, 0, 1, 2, -k2, part_pap_); })) != FG_OK)
       return s;
+    if (half_links_) {
+      if ((s = run(KC_CG_BLAS, [&] { return launch_cg_axpy_h16(xs_, rs_, p_, ap_, cgd_, part_rr_, n, st_); })) !=
+          FG_OK)
+        return s;
+      return run(KC_CG_BLAS, [&] {
+        return launch_cg_xpay_h16(p_, rs_, cgd_, mapped_->hist, &mapped_->dev_iter, h_->prm.cg_maxiter, n, st_);
+      });
+    }
     if ((s = run(KC_CG_BLAS, [&] {
            return launch_cg_axpy<R>(xs_, rs_, p_, ap_, cgd_, part_rr_, n, st_);
          })) != FG_OK) return s;
@@ -973,6 +986,7 @@ class Backend final : public IBackend {
   fg_status reliable_update(const void* U, const void* b64, bool final) {
     const int n = nvec();
     fg_status s;
+    if (half_links_) return reliable_update_h16(U, b64, final);
     if (kMixed) {
       if ((s = run(KC_CG_BLAS, [&] { return launch_ru_accumulate_df(xdf_, xs_, n, st_); })) != FG_OK) return s;
       if (!final) {
@@ -996,6 +1010,33 @@ class Backend final : public IBackend {
     if ((s = run(KC_REDUCE, [&] { return launch_ru_publish(part_rr_, vec_blocks(n), cgd_, tr, st_); })) != FG_OK)
       return s;
     return run(KC_CG_BLAS, [&] { return launch_cg_restart<R>(p_, rs_, cgd_, n, st_); });
+  }
+
+  // The same for half-precision inner vectors: x += sigma x_s; the true
+  // residual is kept in double-float (or FP64 for the certifying update),
+  // sigma is reset from it, and r_s = r / sigma, p = rho p (or r_s).
+  fg_status reliable_update_h16(const void* U, const void* b64, bool final) {
+    const int n = nvec();
+    const int nbv = vec_blocks(n);
+    double* tr = &mapped_->true_rr;
+    fg_status s;
+    if ((s = run(KC_CG_BLAS, [&] { return launch_ru_accumulate_df_scaled(xdf_, xs_, cgd_, n, st_); })) != FG_OK)
+      return s;
+    if (!final) {
+      if ((s = apply_mdagm_df(ax64_, xdf_, U)) != FG_OK) return s;
+      if ((s = run(KC_CG_BLAS, [&] { return launch_ru_residual_df_keep(bdf_, ax64_, part_rr_, n, st_); })) != FG_OK)
+        return s;
+      if ((s = run(KC_REDUCE, [&] { return launch_ru_publish_h16(part_rr_, nbv, cgd_, tr, n, st_); })) != FG_OK)
+        return s;
+      return run(KC_CG_BLAS, [&] { return launch_ru_rescale_df_h16(ax64_, rs_, p_, cgd_, n, st_); });
+    }
+    if ((s = run(KC_CG_BLAS, [&] { return launch_df_to_double(x64_, xdf_, n, st_); })) != FG_OK) return s;
+    if ((s = apply_mdagm64(ax64_, x64_, U)) != FG_OK) return s;
+    if ((s = run(KC_CG_BLAS, [&] { return launch_ru_residual64_keep(b64, ax64_, r64_, part_rr_, n, st_); })) != FG_OK)
+      return s;
+    if ((s = run(KC_REDUCE, [&] { return launch_ru_publish_h16(part_rr_, nbv, cgd_, tr, n, st_); })) != FG_OK)
+      return s;
+    return run(KC_CG_BLAS, [&] { return launch_ru_rescale64_h16(r64_, rs_, p_, cgd_, n, st_); });
   }
 
   // Conjugate gradient on Mhat^dagger Mhat x = b (b FP64 on the device), x0 = 0,
@@ -1026,11 +1067,24 @@ class Backend final : public IBackend {
     if (kMixed && (cudaMemsetAsync(xdf_, 0, (size_t)n * sizeof(double2), st_) != cudaSuccess ||
                    run(KC_CG_BLAS, [&] { return launch_df_from_double(bdf_, b64, n, st_); }) != FG_OK))
       return cuda_fail("cg setup");
-    if ((s = run(KC_CG_BLAS, [&] { return launch_convert<R, double>(rs_, b64, part_rr_, n, st_); })) != FG_OK) return s;
     double* bbp = &mapped_->bb;
-    if ((s = run(KC_REDUCE, [&] { return launch_cg_init(part_rr_, nbv, cgd_, tol * tol, bbp, st_); })) != FG_OK) return s;
-    if (cudaMemcpyAsync(p_, rs_, (size_t)n * sizeof(C2), cudaMemcpyDeviceToDevice, st_) != cudaSuccess)
-      return cuda_fail("cg setup");
+    if (half_links_) {
+      // half-precision inner vectors: r_s = b / sigma with sigma^2 = |b|^2 / n
+      if ((s = run(KC_CG_BLAS, [&] { return launch_dot64(b64, b64, part_rr_, n, st_); })) != FG_OK) return s;
+      if ((s = run(KC_REDUCE, [&] { return launch_cg_init_h16(part_rr_, nbv, cgd_, tol * tol, bbp, n, st_); })) !=
+          FG_OK)
+        return s;
+      if ((s = run(KC_CG_BLAS, [&] { return launch_scale_to_h16(rs_, b64, cgd_, n, st_); })) != FG_OK) return s;
+      if (cudaMemcpyAsync(p_, rs_, (size_t)n * sizeof(__half2), cudaMemcpyDeviceToDevice, st_) != cudaSuccess)
+        return cuda_fail("cg setup");
+    } else {
+      if ((s = run(KC_CG_BLAS, [&] { return launch_convert<R, double>(rs_, b64, part_rr_, n, st_); })) != FG_OK)
+        return s;
+      if ((s = run(KC_REDUCE, [&] { return launch_cg_init(part_rr_, nbv, cgd_, tol * tol, bbp, st_); })) != FG_OK)
+        return s;
+      if (cudaMemcpyAsync(p_, rs_, (size_t)n * sizeof(C2), cudaMemcpyDeviceToDevice, st_) != cudaSuccess)
+        return cuda_fail("cg setup");
+    }
     // the inner iterations' links: the FP32 field, or its half-precision copy
     const void* Uin = U;
     if (half_links_) {

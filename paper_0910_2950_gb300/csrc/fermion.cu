@@ -15,6 +15,8 @@
 // spin blocks with A_x = [[0, i], [i, 0]], A_y = [[0, -1], [1, 0]],
 // A_z = diag(i, -i), A_t = 1, so g5 = diag(1, 1, -1, -1) and
 // (1 - s g_mu) psi = (h, -s A_mu^dagger h) with h = psi_up - s A_mu psi_down.
+#include <type_traits>
+
 #include "df64.cuh"
 #include "fg_common.cuh"
 #include "fg_fermion.h"
@@ -36,24 +38,26 @@ template <typename R> struct Spinor {
   Cx<R> s[4][3];
 };
 
-// Spinor entry k = spin * 3 + colour sits in pair k / 2, slot k % 2.
-template <typename R>
-__device__ __forceinline__ Spinor<R> load_spinor(const typename Vec2<R>::T* __restrict__ f, int i, int Vh) {
+// Spinor entry k = spin * 3 + colour sits in pair k / 2, slot k % 2.  ST is
+// the storage type (the arithmetic type R, or Half16 for R = float).
+template <typename R, typename ST = R>
+__device__ __forceinline__ Spinor<R> load_spinor(const typename Vec2<ST>::T* __restrict__ f, int i, int Vh) {
   Spinor<R> x;
 #pragma unroll
   for (int q = 0; q < 6; ++q) {
     Cx<R> a, b;
-    Quad<R>::load(f, (size_t)q * Vh + i, a, b);
+    Quad<ST>::load(f, (size_t)q * Vh + i, a, b);
     x.s[(2 * q) / 3][(2 * q) % 3] = a;
     x.s[(2 * q + 1) / 3][(2 * q + 1) % 3] = b;
   }
   return x;
 }
-template <typename R>
-__device__ __forceinline__ void store_spinor(typename Vec2<R>::T* __restrict__ f, int i, int Vh, const Spinor<R>& x) {
+template <typename R, typename ST = R>
+__device__ __forceinline__ void store_spinor(typename Vec2<ST>::T* __restrict__ f, int i, int Vh,
+                                             const Spinor<R>& x) {
 #pragma unroll
   for (int q = 0; q < 6; ++q)
-    Quad<R>::store(f, (size_t)q * Vh + i, x.s[(2 * q) / 3][(2 * q) % 3], x.s[(2 * q + 1) / 3][(2 * q + 1) % 3]);
+    Quad<ST>::store(f, (size_t)q * Vh + i, x.s[(2 * q) / 3][(2 * q) % 3], x.s[(2 * q + 1) / 3][(2 * q + 1) % 3]);
 }
 
 template <typename RO, typename RI>
@@ -267,22 +271,22 @@ __device__ __forceinline__ void hops_rt(Spinor<DF>& acc, const float4* __restric
     reconstruct_rt(mu, S, anti ? -1.0f : 1.0f, w, acc);
   }
 }
-template <int DAG, typename RL, int NC, typename RS>
+template <int DAG, typename RL, int NC, typename RS, typename ST = RS>
 struct Hops {
-  static __device__ __forceinline__ void run(Spinor<RS>& acc, const typename Vec2<RS>::T* __restrict__ in,
+  static __device__ __forceinline__ void run(Spinor<RS>& acc, const typename Vec2<ST>::T* __restrict__ in,
                                              const Gauge<RL, NC>& U, const Geom& g, const int c[4], int s,
                                              int in_off);
 };
 
-template <int MU, int DAG, typename RL, int NC, typename RS>
-__device__ __forceinline__ void hop_dir(Spinor<RS>& acc, const typename Vec2<RS>::T* __restrict__ in,
+template <int MU, int DAG, typename RL, int NC, typename RS, typename ST = RS>
+__device__ __forceinline__ void hop_dir(Spinor<RS>& acc, const typename Vec2<ST>::T* __restrict__ in,
                                         const Gauge<RL, NC>& U, const Geom& g, const int c[4], int s,
                                         int in_off) {
   constexpr int SF = DAG ? -1 : 1;   // forward hop: (1 - g_mu), (1 + g_mu) for the dagger
   constexpr int SB = -SF;
   {
     const int sn = cb_neighbor(g, c, MU, +1);
-    const Spinor<RS> p = load_spinor<RS>(in, sn - in_off, g.Vh);
+    const Spinor<RS> p = load_spinor<RS, ST>(in, sn - in_off, g.Vh);
     Cx<RS> h[2][3], w[2][3];
     project<MU, SF>(p, h);
     const M3<RS> u = convert<RS>(U.load(MU, s));
@@ -292,7 +296,7 @@ __device__ __forceinline__ void hop_dir(Spinor<RS>& acc, const typename Vec2<RS>
   }
   {
     const int sn = cb_neighbor(g, c, MU, -1);
-    const Spinor<RS> p = load_spinor<RS>(in, sn - in_off, g.Vh);
+    const Spinor<RS> p = load_spinor<RS, ST>(in, sn - in_off, g.Vh);
     Cx<RS> h[2][3], w[2][3];
     project<MU, SB>(p, h);
     const M3<RS> u = convert<RS>(U.load(MU, sn));
@@ -302,17 +306,18 @@ __device__ __forceinline__ void hop_dir(Spinor<RS>& acc, const typename Vec2<RS>
   }
 }
 
-template <int DAG, typename RL, int NC, typename RS>
-__device__ __forceinline__ void Hops<DAG, RL, NC, RS>::run(Spinor<RS>& acc, const typename Vec2<RS>::T* __restrict__ in,
-                                                           const Gauge<RL, NC>& U, const Geom& g, const int c[4],
-                                                           int s, int in_off) {
-  hop_dir<0, DAG>(acc, in, U, g, c, s, in_off);
-  hop_dir<1, DAG>(acc, in, U, g, c, s, in_off);
-  hop_dir<2, DAG>(acc, in, U, g, c, s, in_off);
-  hop_dir<3, DAG>(acc, in, U, g, c, s, in_off);
+template <int DAG, typename RL, int NC, typename RS, typename ST>
+__device__ __forceinline__ void Hops<DAG, RL, NC, RS, ST>::run(Spinor<RS>& acc,
+                                                               const typename Vec2<ST>::T* __restrict__ in,
+                                                               const Gauge<RL, NC>& U, const Geom& g,
+                                                               const int c[4], int s, int in_off) {
+  hop_dir<0, DAG, RL, NC, RS, ST>(acc, in, U, g, c, s, in_off);
+  hop_dir<1, DAG, RL, NC, RS, ST>(acc, in, U, g, c, s, in_off);
+  hop_dir<2, DAG, RL, NC, RS, ST>(acc, in, U, g, c, s, in_off);
+  hop_dir<3, DAG, RL, NC, RS, ST>(acc, in, U, g, c, s, in_off);
 }
 template <int DAG, int NC>
-struct Hops<DAG, float, NC, DF> {
+struct Hops<DAG, float, NC, DF, DF> {
   static __device__ __forceinline__ void run(Spinor<DF>& acc, const float4* __restrict__ in,
                                              const Gauge<float, NC>& U, const Geom& g, const int c[4], int s,
                                              int in_off) {
@@ -339,10 +344,10 @@ template <> struct DslashMinBlocks<float> { static constexpr int value = FG_DSLA
 #endif
 template <> struct DslashMinBlocks<DF> { static constexpr int value = FG_DSLASH_DF_MIN_BLOCKS; };
 
-template <typename RL, int NC, typename RS, int DAG, int MODE>
+template <typename RL, int NC, typename RS, int DAG, int MODE, typename ST = RS>
 __global__ void __launch_bounds__(kDslashThreads, DslashMinBlocks<RS>::value) dslash_kernel(
-    typename Vec2<RS>::T* __restrict__ out, const typename Vec2<RS>::T* __restrict__ in,
-    const typename Vec2<RS>::T* __restrict__ x, const typename Vec2<RS>::T* __restrict__ pdot,
+    typename Vec2<ST>::T* __restrict__ out, const typename Vec2<ST>::T* __restrict__ in,
+    const typename Vec2<ST>::T* __restrict__ x, const typename Vec2<ST>::T* __restrict__ pdot,
     Gauge<RL, NC> U, Geom g, int out_par, RS b, double* __restrict__ partial, CgDev* __restrict__ cgd) {
   if (cgd != nullptr && cgd->done) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -357,7 +362,7 @@ __global__ void __launch_bounds__(kDslashThreads, DslashMinBlocks<RS>::value) ds
     for (int k = 0; k < 4; ++k)
 #pragma unroll
       for (int cc = 0; cc < 3; ++cc) acc.s[k][cc] = cx<RS>(0, 0);
-    Hops<DAG, RL, NC, RS>::run(acc, in, U, g, c, s, in_off);
+    Hops<DAG, RL, NC, RS, ST>::run(acc, in, U, g, c, s, in_off);
     Spinor<RS> o;
     if (MODE == 0) {
 #pragma unroll
@@ -365,13 +370,13 @@ __global__ void __launch_bounds__(kDslashThreads, DslashMinBlocks<RS>::value) ds
 #pragma unroll
         for (int cc = 0; cc < 3; ++cc) o.s[k][cc] = b * acc.s[k][cc];
     } else {
-      const Spinor<RS> xv = load_spinor<RS>(x, i, g.Vh);
+      const Spinor<RS> xv = load_spinor<RS, ST>(x, i, g.Vh);
 #pragma unroll
       for (int k = 0; k < 4; ++k)
 #pragma unroll
         for (int cc = 0; cc < 3; ++cc) o.s[k][cc] = xv.s[k][cc] + b * acc.s[k][cc];
       if (MODE == 2) {
-        const Spinor<RS> pv = load_spinor<RS>(pdot, i, g.Vh);
+        const Spinor<RS> pv = load_spinor<RS, ST>(pdot, i, g.Vh);
 #pragma unroll
         for (int k = 0; k < 4; ++k)
 #pragma unroll
@@ -379,7 +384,7 @@ __global__ void __launch_bounds__(kDslashThreads, DslashMinBlocks<RS>::value) ds
             dot += pv.s[k][cc].re * o.s[k][cc].re + pv.s[k][cc].im * o.s[k][cc].im;
       }
     }
-    store_spinor<RS>(out, i, g.Vh, o);
+    store_spinor<RS, ST>(out, i, g.Vh, o);
   }
   if (MODE == 2) block_reduce_total(double(dot), partial, &cgd->ticket[0], &cgd->pap);
 }
@@ -627,6 +632,187 @@ __global__ void __launch_bounds__(kVecThreads) df_to_double_kernel(double2* __re
   }
 }
 
+// ---------------------------------------------------------------------------
+// Half-precision inner vectors.  The solver iterates on r / sigma: CG is
+// invariant under a common scale of r and p, and keeping |r / sigma|^2 = n
+// after every reliable update keeps the entries O(1), far from the ends of
+// the half range.  Scalars (rr, pAp, alpha, beta) are in the scaled units;
+// the history and the convergence test use rr sigma^2.
+__global__ void __launch_bounds__(kVecThreads) cg_axpy_h16_kernel(float2* __restrict__ x, __half2* __restrict__ r,
+                                                                  const __half2* __restrict__ p,
+                                                                  const __half2* __restrict__ ap,
+                                                                  CgDev* __restrict__ cgd, double* __restrict__ rr_part,
+                                                                  int n) {
+  if (cgd->done) return;
+  const int k = cgd->iter + 1;
+  const double pap = cgd->pap;
+  const double rr = cgd->rr[(k - 1) & 1];
+  const double alpha = pap > 0.0 ? rr / pap : 0.0;
+  const float a = float(alpha);
+  float acc = 0.0f;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    float2 xv = x[i];
+    float2 rv = __half22float2(r[i]);
+    const float2 pv = __half22float2(p[i]), av = __half22float2(ap[i]);
+    xv.x = fmaf(a, pv.x, xv.x); xv.y = fmaf(a, pv.y, xv.y);
+    rv.x = fmaf(-a, av.x, rv.x); rv.y = fmaf(-a, av.y, rv.y);
+    x[i] = xv;
+    const __half2 rh = __float22half2_rn(rv);
+    r[i] = rh;
+    const float2 rq = __half22float2(rh);   // |r|^2 of the stored residual
+    acc = fmaf(rq.x, rq.x, acc);
+    acc = fmaf(rq.y, rq.y, acc);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    cgd->alpha = alpha;
+    cgd->k_axpy = k;
+  }
+  block_reduce_total(double(acc), rr_part, &cgd->ticket[1], &cgd->rr_next);
+}
+
+__global__ void __launch_bounds__(kVecThreads) cg_xpay_h16_kernel(__half2* __restrict__ p,
+                                                                  const __half2* __restrict__ r,
+                                                                  CgDev* __restrict__ cgd, double* __restrict__ hist,
+                                                                  int* __restrict__ iter_out, int maxiter, int n) {
+  if (cgd->done) return;
+  const int k = cgd->k_axpy;
+  const double rr_new = cgd->rr_next;
+  const double rr_old = cgd->rr[(k - 1) & 1];
+  const double rr_true = rr_new * cgd->sigma2;
+  const bool conv = rr_true <= cgd->tol2bb;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    cgd->rr[k & 1] = rr_new;
+    if (k <= maxiter) hist[k] = rr_true;
+    cgd->iter = k;
+    *iter_out = k;
+    if (conv) cgd->done = 1;
+  }
+  const float beta = float(rr_old > 0.0 ? rr_new / rr_old : 0.0);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    float2 pv = __half22float2(p[i]);
+    const float2 rv = __half22float2(r[i]);
+    pv.x = fmaf(beta, pv.x, rv.x);
+    pv.y = fmaf(beta, pv.y, rv.y);
+    p[i] = __float22half2_rn(pv);
+  }
+}
+
+__global__ void cg_init_h16_kernel(const double* __restrict__ part, int nparts, CgDev* __restrict__ cgd, double tol2,
+                                   double* __restrict__ bb_out, int n) {
+  const double bb = block_sum_partials(part, nparts);
+  if (threadIdx.x == 0) {
+    const double s2 = bb > 0.0 ? bb / n : 1.0;
+    cgd->bb = bb;
+    cgd->tol2bb = tol2 * bb;
+    cgd->sigma2 = s2;
+    cgd->rho = 1.0;
+    cgd->rr[0] = cgd->rr[1] = bb / s2;
+    cgd->done = bb == 0.0 ? 1 : 0;
+    cgd->iter = 0;
+    cgd->k_axpy = 0;
+    cgd->restart = 0;
+    *bb_out = bb;
+  }
+}
+
+__global__ void __launch_bounds__(kVecThreads) scale_to_h16_kernel(__half2* __restrict__ rs,
+                                                                   const double2* __restrict__ b,
+                                                                   const CgDev* __restrict__ cgd, int n) {
+  const double inv = 1.0 / sqrt(cgd->sigma2);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double2 v = b[i];
+    rs[i] = __floats2half2_rn(float(v.x * inv), float(v.y * inv));
+  }
+}
+
+__global__ void __launch_bounds__(kVecThreads) ru_accumulate_df_scaled_kernel(float4* __restrict__ x,
+                                                                              float2* __restrict__ xs,
+                                                                              const CgDev* __restrict__ cgd,
+                                                                              int n) {
+  const float sg = float(sqrt(cgd->sigma2));
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float2 v = xs[i];
+    const float4 a = x[i];
+    const DF re = df_add_f(DF(a.x, a.y), sg * v.x), im = df_add_f(DF(a.z, a.w), sg * v.y);
+    x[i] = make_float4(re.hi, re.lo, im.hi, im.lo);
+    xs[i] = make_float2(0.0f, 0.0f);
+  }
+}
+
+__global__ void __launch_bounds__(kVecThreads) ru_residual_df_keep_kernel(const float4* __restrict__ b,
+                                                                          float4* __restrict__ ax,
+                                                                          double* __restrict__ part, int n) {
+  float acc = 0.0f;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float4 bv = b[i], av = ax[i];
+    const DF re = DF(bv.x, bv.y) - DF(av.x, av.y), im = DF(bv.z, bv.w) - DF(av.z, av.w);
+    ax[i] = make_float4(re.hi, re.lo, im.hi, im.lo);
+    acc = fmaf(re.hi, re.hi, acc);
+    acc = fmaf(im.hi, im.hi, acc);
+  }
+  double v[1] = {double(acc)};
+  block_reduce_store<1>(v, part, gridDim.x);
+}
+
+__global__ void __launch_bounds__(kVecThreads) ru_residual64_keep_kernel(const double2* __restrict__ b,
+                                                                         const double2* __restrict__ ax,
+                                                                         double2* __restrict__ r,
+                                                                         double* __restrict__ part, int n) {
+  double acc = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double2 bv = b[i], av = ax[i];
+    const double2 rv = make_double2(bv.x - av.x, bv.y - av.y);
+    r[i] = rv;
+    acc += rv.x * rv.x + rv.y * rv.y;
+  }
+  double v[1] = {acc};
+  block_reduce_store<1>(v, part, gridDim.x);
+}
+
+__global__ void ru_publish_h16_kernel(const double* __restrict__ part, int nparts, CgDev* __restrict__ cgd,
+                                      double* __restrict__ true_rr, int n) {
+  const double rr = block_sum_partials(part, nparts);
+  if (threadIdx.x == 0) {
+    const double rr_iter = cgd->rr[cgd->iter & 1] * cgd->sigma2;
+    const double s2 = rr > 0.0 ? rr / n : cgd->sigma2;
+    cgd->restart = (rr > 2.0 * rr_iter) ? 1 : 0;
+    cgd->rho = sqrt(cgd->sigma2 / s2);
+    cgd->sigma2 = s2;
+    cgd->rr[cgd->iter & 1] = rr / s2;
+    cgd->done = rr <= cgd->tol2bb ? 1 : 0;
+    *true_rr = rr;
+  }
+}
+
+template <typename RV>
+__global__ void __launch_bounds__(kVecThreads) ru_rescale_h16_kernel(const RV* __restrict__ r, __half2* __restrict__ rs,
+                                                                     __half2* __restrict__ p,
+                                                                     const CgDev* __restrict__ cgd, int n) {
+  const double inv = 1.0 / sqrt(cgd->sigma2);
+  const float rho = float(cgd->rho);
+  const bool restart = cgd->restart != 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double re, im;
+    if constexpr (std::is_same<RV, float4>::value) {   // double-float residual
+      const float4 v = ((const float4*)r)[i];
+      re = double(DF(v.x, v.y));
+      im = double(DF(v.z, v.w));
+    } else {
+      const double2 v = ((const double2*)r)[i];
+      re = v.x;
+      im = v.y;
+    }
+    const __half2 h = __floats2half2_rn(float(re * inv), float(im * inv));
+    rs[i] = h;
+    if (restart) {
+      p[i] = h;
+    } else {
+      const float2 pv = __half22float2(p[i]);
+      p[i] = __floats2half2_rn(rho * pv.x, rho * pv.y);
+    }
+  }
+}
+
 // Publishes a reliable-update residual after iteration k = iter:
 // rr[k&1] = |r|^2, done = rr <= tol2 bb.  The search direction is kept (the
 // usual reliable update) while the true |r|^2 is within a factor 2 of the
@@ -855,6 +1041,81 @@ cudaError_t launch_df_from_double(void* dst, const void* src, int n, cudaStream_
 }
 cudaError_t launch_df_to_double(void* dst, const void* src, int n, cudaStream_t st) {
   df_to_double_kernel<<<vec_blocks(n), kVecThreads, 0, st>>>((double2*)dst, (const float4*)src, n);
+  return cudaGetLastError();
+}
+template <typename RL, int NC>
+cudaError_t launch_dslash_h16(const GeomH& gh, void* out, const void* in, const void* x, const void* pdot,
+                              const void* U, int out_par, int dag, int mode, double b, double* partial,
+                              CgDev* cgd, cudaStream_t st) {
+  Gauge<RL, NC> u;
+  u.p = const_cast<void*>(U);
+  u.V = gh.V;
+  const Geom g = to_devg(gh);
+  const int nb = dslash_blocks(gh.Vh);
+#define FG_DH(D, M)                                                                                            \
+  dslash_kernel<RL, NC, float, D, M, Half16><<<nb, kDslashThreads, 0, st>>>(                                  \
+      (__half2*)out, (const __half2*)in, (const __half2*)x, (const __half2*)pdot, u, g, out_par, float(b),     \
+      partial, cgd)
+  if (dag) {
+    if (mode == 0) FG_DH(1, 0); else if (mode == 1) FG_DH(1, 1); else FG_DH(1, 2);
+  } else {
+    if (mode == 0) FG_DH(0, 0); else if (mode == 1) FG_DH(0, 1); else FG_DH(0, 2);
+  }
+#undef FG_DH
+  return cudaGetLastError();
+}
+template cudaError_t launch_dslash_h16<Half16, 9>(const GeomH&, void*, const void*, const void*, const void*,
+                                                  const void*, int, int, int, double, double*, CgDev*, cudaStream_t);
+template cudaError_t launch_dslash_h16<Half16, 6>(const GeomH&, void*, const void*, const void*, const void*,
+                                                  const void*, int, int, int, double, double*, CgDev*, cudaStream_t);
+cudaError_t launch_cg_axpy_h16(void* xs, void* r, const void* p, const void* ap, CgDev* cgd, double* rr_part, int n,
+                               cudaStream_t st) {
+  cg_axpy_h16_kernel<<<vec_blocks(n), kVecThreads, 0, st>>>((float2*)xs, (__half2*)r, (const __half2*)p,
+                                                            (const __half2*)ap, cgd, rr_part, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_cg_xpay_h16(void* p, const void* r, CgDev* cgd, double* hist, int* iter_out, int maxiter, int n,
+                               cudaStream_t st) {
+  cg_xpay_h16_kernel<<<vec_blocks(n), kVecThreads, 0, st>>>((__half2*)p, (const __half2*)r, cgd, hist, iter_out,
+                                                            maxiter, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_cg_init_h16(const double* part, int nparts, CgDev* cgd, double tol2, double* bb_out, int n,
+                               cudaStream_t st) {
+  cg_init_h16_kernel<<<1, 256, 0, st>>>(part, nparts, cgd, tol2, bb_out, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_scale_to_h16(void* rs, const void* b64, const CgDev* cgd, int n, cudaStream_t st) {
+  scale_to_h16_kernel<<<vec_blocks(n), kVecThreads, 0, st>>>((__half2*)rs, (const double2*)b64, cgd, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_ru_accumulate_df_scaled(void* xdf, void* xs, const CgDev* cgd, int n, cudaStream_t st) {
+  ru_accumulate_df_scaled_kernel<<<vec_blocks(n), kVecThreads, 0, st>>>((float4*)xdf, (float2*)xs, cgd, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_ru_residual_df_keep(const void* bdf, void* axdf, double* part, int n, cudaStream_t st) {
+  ru_residual_df_keep_kernel<<<vec_blocks(n), kVecThreads, 0, st>>>((const float4*)bdf, (float4*)axdf, part, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_ru_residual64_keep(const void* b64, const void* ax64, void* r64, double* part, int n,
+                                      cudaStream_t st) {
+  ru_residual64_keep_kernel<<<vec_blocks(n), kVecThreads, 0, st>>>((const double2*)b64, (const double2*)ax64,
+                                                                   (double2*)r64, part, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_ru_publish_h16(const double* part, int nparts, CgDev* cgd, double* true_rr, int n,
+                                  cudaStream_t st) {
+  ru_publish_h16_kernel<<<1, 256, 0, st>>>(part, nparts, cgd, true_rr, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_ru_rescale_df_h16(const void* rdf, void* rs, void* p, const CgDev* cgd, int n, cudaStream_t st) {
+  ru_rescale_h16_kernel<float4><<<vec_blocks(n), kVecThreads, 0, st>>>((const float4*)rdf, (__half2*)rs,
+                                                                       (__half2*)p, cgd, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_ru_rescale64_h16(const void* r64, void* rs, void* p, const CgDev* cgd, int n, cudaStream_t st) {
+  ru_rescale_h16_kernel<double2><<<vec_blocks(n), kVecThreads, 0, st>>>((const double2*)r64, (__half2*)rs,
+                                                                        (__half2*)p, cgd, n);
   return cudaGetLastError();
 }
 cudaError_t launch_dot64(const void* a, const void* b, double* part, int n, cudaStream_t st) {

@@ -444,6 +444,35 @@ template <> struct Quad<double> {
   }
 };
 
+// IEEE half storage (tag Half16) with FP32 arithmetic: links of the inner
+// solver and, with a per-solve-cycle scale, its spinor vectors.  A complex
+// number is one __half2, a pair of entries 8 bytes.
+struct Half16 {};
+template <> struct Vec2<Half16> { typedef __half2 T; };
+__device__ __forceinline__ Cx<float> h2_to_cx(unsigned int w) {
+  const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w));
+  return cx<float>(f.x, f.y);
+}
+__device__ __forceinline__ unsigned int cx_to_h2(const Cx<float>& c) {
+  const __half2 h = __floats2half2_rn(c.re, c.im);
+  return *reinterpret_cast<const unsigned int*>(&h);
+}
+template <> struct Quad<Half16> {
+  static __device__ __forceinline__ void load(const void* base, size_t idx, Cx<float>& a, Cx<float>& b) {
+    const uint2 v = __ldg((const uint2*)base + idx);
+    a = h2_to_cx(v.x);
+    b = h2_to_cx(v.y);
+  }
+  static __device__ __forceinline__ void load_cg(const void* base, size_t idx, Cx<float>& a, Cx<float>& b) {
+    const uint2 v = ((const uint2*)base)[idx];
+    a = h2_to_cx(v.x);
+    b = h2_to_cx(v.y);
+  }
+  static __device__ __forceinline__ void store(void* base, size_t idx, Cx<float> a, Cx<float> b) {
+    ((uint2*)base)[idx] = make_uint2(cx_to_h2(a), cx_to_h2(b));
+  }
+};
+
 // Links: NP = NC / 2 pairs per link in [mu][pair][site] order, then, for
 // NC = 9, the ninth entry of every link in [mu][site] order.
 template <typename R, int NC> struct Gauge {
@@ -489,19 +518,12 @@ template <typename R, int NC> struct Gauge {
 // precision and needs no scale).  Same layout as Gauge<float, NC> with two
 // bytes per real: a pair of entries is 8 bytes, the NC = 9 tail 4 bytes.
 // Loads return FP32 matrices.
-struct Half16 {};
 template <int NC> struct Gauge<Half16, NC> {
   static constexpr int NP = NC / 2;
   void* __restrict__ p;
   int V;
-  static __device__ __forceinline__ Cx<float> cx_of(unsigned int w) {
-    const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w));
-    return cx<float>(f.x, f.y);
-  }
-  static __device__ __forceinline__ unsigned int word_of(const Cx<float>& c) {
-    const __half2 h = __floats2half2_rn(c.re, c.im);
-    return *reinterpret_cast<const unsigned int*>(&h);
-  }
+  static __device__ __forceinline__ Cx<float> cx_of(unsigned int w) { return h2_to_cx(w); }
+  static __device__ __forceinline__ unsigned int word_of(const Cx<float>& c) { return cx_to_h2(c); }
   __device__ __forceinline__ M3<float> load(int mu, int s) const {
     M3<float> m;
 #pragma unroll

@@ -25,6 +25,10 @@ struct CgDev {
   double pap;       // <p, Ap> of the iteration in progress (grand total of the Dslash partials)
   double rr_next;   // |r|^2 after the iteration in progress (grand total of the axpy partials)
   unsigned ticket[2];  // blocks finished, for the two grand totals; the last block resets it to 0
+  // half-precision inner vectors hold r / sigma and p / sigma; sigma^2 is
+  // reset at every reliable update to |r|^2 / n, and rho rescales p then
+  double sigma2;
+  double rho;
 };
 
 int vec_blocks(int n);
@@ -76,6 +80,37 @@ cudaError_t launch_ru_residual_df(const void* bdf, const void* axdf, void* rs, d
                                   cudaStream_t st);
 cudaError_t launch_df_from_double(void* dst, const void* src, int n, cudaStream_t st);
 cudaError_t launch_df_to_double(void* dst, const void* src, int n, cudaStream_t st);
+// ---- half-precision inner vectors (r, p, Ap and the Dslash temporaries as
+// __half2, scaled by 1/sigma; the solution increment x_s stays FP32)
+// Dslash with half-precision spinors, FP32 arithmetic, links RL (float or Half16).
+template <typename RL, int NC>
+cudaError_t launch_dslash_h16(const GeomH& g, void* out, const void* in, const void* x, const void* pdot,
+                              const void* U, int out_par, int dag, int mode, double b, double* partial,
+                              CgDev* cgd, cudaStream_t st);
+cudaError_t launch_cg_axpy_h16(void* xs, void* r, const void* p, const void* ap, CgDev* cgd, double* rr_part, int n,
+                               cudaStream_t st);
+cudaError_t launch_cg_xpay_h16(void* p, const void* r, CgDev* cgd, double* hist, int* iter_out, int maxiter, int n,
+                               cudaStream_t st);
+// Start of a solve: bb from the partials of |b|^2, sigma^2 = bb / n, rr = n, tol2bb, done.
+cudaError_t launch_cg_init_h16(const double* part, int nparts, CgDev* cgd, double tol2, double* bb_out, int n,
+                               cudaStream_t st);
+// rs = b / sigma (b FP64).
+cudaError_t launch_scale_to_h16(void* rs, const void* b64, const CgDev* cgd, int n, cudaStream_t st);
+// x (double-float) += sigma x_s; x_s = 0.
+cudaError_t launch_ru_accumulate_df_scaled(void* xdf, void* xs, const CgDev* cgd, int n, cudaStream_t st);
+// r = b - Ax written over Ax (double-float), partials of |r|^2.
+cudaError_t launch_ru_residual_df_keep(const void* bdf, void* axdf, double* part, int n, cudaStream_t st);
+// r = b - Ax written to r64 (FP64), partials of |r|^2.
+cudaError_t launch_ru_residual64_keep(const void* b64, const void* ax64, void* r64, double* part, int n,
+                                      cudaStream_t st);
+// Publish a true residual for the half-precision solver: rr, restart, new
+// sigma^2 and rho, rr[iter&1] in the new scaling, done.
+cudaError_t launch_ru_publish_h16(const double* part, int nparts, CgDev* cgd, double* true_rr, int n,
+                                  cudaStream_t st);
+// rs = r / sigma (r double-float or FP64); p = restart ? rs : rho p.
+cudaError_t launch_ru_rescale_df_h16(const void* rdf, void* rs, void* p, const CgDev* cgd, int n, cudaStream_t st);
+cudaError_t launch_ru_rescale64_h16(const void* r64, void* rs, void* p, const CgDev* cgd, int n, cudaStream_t st);
+
 cudaError_t launch_ru_publish(const double* part, int n, CgDev* cgd, double* true_rr, cudaStream_t st);
 // p = r when the last reliable update asked for a restart (cgd->restart).
 template <typename R>
