@@ -242,7 +242,7 @@ class ClockSampler:
 # spinors (96 B) + 8 links (72 B) read, one spinor (96 B) written.
 # dram__bytes_read + write of the fused force kernel per link, FP32 18-real,
 # averaged over an FG trajectory's launch mix (ncu capture at 28^4)
-FORCE_TRAFFIC_BYTES_PER_LINK = None   # re-measure after a kernel change (None: not reported)
+FORCE_TRAFFIC_BYTES_PER_LINK = 203   # re-measure after a kernel change (None: not reported)
 DSLASH_BYTES_FP32_18 = 8 * 96 + 8 * 72 + 96
 # Compulsory bytes per output site of one FP32 Dslash (each of the 4V links is
 # read once per half-lattice hop, input and output spinors once): 8 * 72 + 96

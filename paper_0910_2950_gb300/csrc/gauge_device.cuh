@@ -23,17 +23,23 @@ namespace fg {
 // indices are formed with selects, so mu and nu may be run-time values
 // without the coordinate array going to local memory; one copy of the body
 // keeps the kernel small enough for the instruction cache.
-// Change of the half index lex/2 when coordinate nu of c moves by d = +-1
-// (periodic); the parity flips.  Only that coordinate moves, so the change
+// Changes dp, dm of the half index lex/2 when coordinate nu of c moves by
+// +1 and -1 (periodic); the parity flips.  Only that coordinate moves, so the change
 // is (v>>1) - (c>>1) in x and (v - c) times the half stride of nu otherwise,
 // and the changes of two steps in different directions add.
-__device__ __forceinline__ int cb_half_step(const Geom& g, const int c[4], int nu, int d) {
+__device__ __forceinline__ void cb_half_steps(const Geom& g, const int c[4], int nu, int& dp, int& dm) {
   const int cn = sel4(c, nu);
   const int ln = nu == 0 ? g.L[0] : (nu == 1 ? g.L[1] : (nu == 2 ? g.L[2] : g.L[3]));
-  int v = cn + d;
-  v = v < 0 ? v + ln : (v >= ln ? v - ln : v);
-  const int hs = nu == 1 ? g.Lxh : (nu == 2 ? g.Lxh * g.L[1] : g.Lxh * g.L[1] * g.L[2]);
-  return nu == 0 ? (v >> 1) - (cn >> 1) : (v - cn) * hs;
+  const int vp = cn + 1 == ln ? 0 : cn + 1;
+  const int vm = cn == 0 ? ln - 1 : cn - 1;
+  if (nu == 0) {
+    dp = (vp >> 1) - (cn >> 1);
+    dm = (vm >> 1) - (cn >> 1);
+  } else {
+    const int hs = nu == 1 ? g.Lxh : (nu == 2 ? g.Lxh * g.L[1] : g.Lxh * g.L[1] * g.L[2]);
+    dp = (vp - cn) * hs;
+    dm = (vm - cn) * hs;
+  }
 }
 
 template <typename R, int NC>
@@ -44,7 +50,9 @@ __device__ __forceinline__ M3<R> staple_sum(const Gauge<R, NC>& U, const Geom& g
   // x + mu - nu keeps it
   const int par = s >= g.Vh;
   const int other = s + (par ? -g.Vh : g.Vh);
-  const int dmu = cb_half_step(g, c, mu, +1);
+  int dmu, dmu_m;
+  cb_half_steps(g, c, mu, dmu, dmu_m);
+  (void)dmu_m;
   const int s_pmu = other + dmu;
 #if FG_FORCE_UNROLL_NU
 #pragma unroll
@@ -53,10 +61,11 @@ __device__ __forceinline__ M3<R> staple_sum(const Gauge<R, NC>& U, const Geom& g
 #endif
   for (int k = 1; k < 4; ++k) {
     const int nu = (mu + k) & 3;
-    const int dm = cb_half_step(g, c, nu, -1);
+    int dp, dm;
+    cb_half_steps(g, c, nu, dp, dm);
     {
       // upper: U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag
-      const M3<R> t = mul_nd(U.load(nu, s_pmu), U.load(mu, other + cb_half_step(g, c, nu, +1)));
+      const M3<R> t = mul_nd(U.load(nu, s_pmu), U.load(mu, other + dp));
       mac_nd(a, t, U.load(nu, s));
     }
     {
