@@ -359,26 +359,6 @@ __device__ __forceinline__ int cb_neighbor_rt(const Geom& g, const int c[4], int
   }
   return cb_index(g, n);
 }
-__device__ __forceinline__ int cb_neighbor2_rt(const Geom& g, const int c[4], int mu1, int d1, int mu2, int d2) {
-  int n[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    int v = c[k] + (k == mu1 ? d1 : 0) + (k == mu2 ? d2 : 0);
-    v = v < 0 ? v + g.L[k] : (v >= g.L[k] ? v - g.L[k] : v);
-    n[k] = v;
-  }
-  return cb_index(g, n);
-}
-
-// x + d1 * mu1-hat + d2 * mu2-hat
-__device__ __forceinline__ int cb_neighbor2(const Geom& g, const int c[4], int mu1, int d1, int mu2, int d2) {
-  int n[4] = {c[0], c[1], c[2], c[3]};
-  int v = n[mu1] + d1;
-  n[mu1] = v < 0 ? v + g.L[mu1] : (v >= g.L[mu1] ? v - g.L[mu1] : v);
-  v = n[mu2] + d2;
-  n[mu2] = v < 0 ? v + g.L[mu2] : (v >= g.L[mu2] ? v - g.L[mu2] : v);
-  return cb_index(g, n);
-}
 
 // Site of a link thread: a block of (64, 4) threads covers half-site indices
 // [32 b, 32 b + 32) in both parities (warp 0 even, warp 1 odd) and all four

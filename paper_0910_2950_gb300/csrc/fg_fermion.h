@@ -35,7 +35,7 @@ int vec_blocks(int n);
 int dslash_blocks(int Vh);
 
 // RS = DF (df64.cuh) evaluates the hop in double-float arithmetic on FP32
-// links; it is instantiated for RL = float, modes 0 and 1 only.
+// links (instantiated for RL = float; the solver uses modes 0 and 1).
 // out = b D in (mode 0); out = x + b D in (mode 1); mode 2 (CG only) also
 // sums Re <pdot, out> into cgd->pap through the block partials `partial`.
 // D hops from parity 1-out_par to out_par; dag = 1 applies g5 D g5.  Links

@@ -18,6 +18,7 @@
 #include "fg_common.cuh"
 #include "fg_fermion.h"
 #include "fg_kernels.h"
+#include "gauge_device.cuh"
 
 namespace fg {
 
@@ -78,12 +79,20 @@ __device__ __forceinline__ void staple_sum_tangent(const Gauge<R, NC>& U, const 
                                                    const int c[4], int s, int mu, M3<R>& a, M3<R>& da) {
   zero(a);
   zero(da);
-  const int s_pmu = cb_neighbor_rt(g, c, mu, +1);
+  // neighbours as half-index steps from s (see staple_sum)
+  const int par = s >= g.Vh;
+  const int other = s + (par ? -g.Vh : g.Vh);
+  int dmu, dmu_m;
+  cb_half_steps(g, c, mu, dmu, dmu_m);
+  (void)dmu_m;
+  const int s_pmu = other + dmu;
 #pragma unroll 1
   for (int k = 1; k < 4; ++k) {
     const int nu = (mu + k) & 3;
+    int dp, dm;
+    cb_half_steps(g, c, nu, dp, dm);
     {
-      const int s_pnu = cb_neighbor_rt(g, c, nu, +1);
+      const int s_pnu = other + dp;
       const M3<R> A = U.load(nu, s_pmu), B = U.load(mu, s_pnu);
       const M3<R> dA = dU.load(nu, s_pmu), dB = dU.load(mu, s_pnu);
       const M3<R> t = mul_nd(A, B);
@@ -95,8 +104,8 @@ __device__ __forceinline__ void staple_sum_tangent(const Gauge<R, NC>& U, const 
       mac_nd(da, t, dC);
     }
     {
-      const int s_mnu = cb_neighbor_rt(g, c, nu, -1);
-      const int s_pm = cb_neighbor2_rt(g, c, mu, +1, nu, -1);
+      const int s_mnu = other + dm;
+      const int s_pm = s + dm + dmu;
       const M3<R> P = U.load(mu, s_mnu), Q = U.load(nu, s_pm);
       const M3<R> dP = dU.load(mu, s_mnu), dQ = dU.load(nu, s_pm);
       const M3<R> t = mul(P, Q);
