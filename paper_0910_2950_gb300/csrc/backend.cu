@@ -256,9 +256,10 @@ class Backend final : public IBackend {
     // The start field is never written during the trajectory (see execute),
     // so a rejection only has to point back at it.
     void* const start = U_;
-    // until the trajectory completes, the stored per-site action may not
-    // match the current links (an error below leaves them moved)
+    // until the trajectory completes, the stored per-site action and S_F may
+    // not match the current links (an error below leaves them moved)
     sgc_valid_ = false;
+    sf0_valid_ = false;
     if ((s = execute(ops, dt, start)) != FG_OK) return s;
     if ((s = energy(1, P_, 3, nullptr, sgc_[1 - sgc_cur_])) != FG_OK) return s;
     if ((s = fetch(6)) != FG_OK) return s;
