@@ -138,6 +138,32 @@ def oracle_trajectory_rate(sample_l: int, target_l: int, integrator: str, dt: fl
                                 f"FP64 numpy, {secs:.2f} s, scaled by V ratio ({sample_l}/{target_l})^4")
 
 
+def oracle_unit_times(seed: int = 3):
+    """The oracle's per-unit costs on one host core (seconds): a gauge force
+    evaluation on 16^4, and on 8^3 x 16 with kappa = 0.158 a full-lattice
+    hop (the Dslash of both parities), one CG iteration (Mhat^dag Mhat and
+    the vector updates) and a pseudofermion force from a given solution."""
+    from oracle import fermion as fe, gauge
+    out = {}
+    u = inputs.hot_start((16,) * 4, seed)
+    t0 = time.perf_counter()
+    gauge.gauge_force(u, BETA)
+    out["gauge_force_16^4_s"] = time.perf_counter() - t0
+    dims = (8, 8, 8, 16)
+    u = inputs.hot_start(dims, seed)
+    x = inputs.unpack_even(inputs.gaussian_spinor_even(dims, seed), dims)
+    t0 = time.perf_counter()
+    fe.hop(u, x)
+    out["hop_8^3x16_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    _, iters = fe.cg(u, 0.158, x, tol=1e-6)
+    out["cg_iteration_8^3x16_s"] = (time.perf_counter() - t0) / max(iters, 1)
+    t0 = time.perf_counter()
+    fe.fermion_force(u, 0.158, x, x=x)
+    out["fermion_force_8^3x16_s"] = time.perf_counter() - t0
+    return out
+
+
 def cpu_cores_used():
     return 1  # numpy batched 3x3 products and eigh run on one thread
 
@@ -558,7 +584,8 @@ def run_ours(args):
     if rank == 0 and world >= 1 and not args.no_cpu_baseline:
         # oracle first, before this process touches the GPU
         r, s, desc = oracle_trajectory_rate(16, args.lattice, args.integrator, args.dt, 7)
-        cpu = {"value": r, "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle", "sample": desc}
+        cpu = {"value": r, "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle", "sample": desc,
+               "unit_times": oracle_unit_times()}
 
     if world > 1:
         dist.init_process_group("nccl", rank=rank, world_size=world)
