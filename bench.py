@@ -14,8 +14,10 @@ solves to 1e-10 with the even-odd Dslash timed per launch against HBM.
 
 Output: one JSON line (rank 0).  `value` is trajectories per second over all
 ranks with the fields resident in HBM; `e2e` is the same metric through the
-C ABI with host buffers (gauge field and momenta uploaded, gauge field read
-back every trajectory); `roofline` reports the gauge-force kernel against
+C ABI with host buffers (each trajectory's momenta uploaded from pinned host
+memory while the previous trajectory runs, its result read back; beside it
+the same without the overlap, and with the gauge field also uploaded and
+read back every trajectory); `roofline` reports the gauge-force kernel against
 the FP32 FMA peak; `cpu_baseline` times the FP64 CPU oracle on a 16^4 sample.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -710,19 +712,32 @@ def run_ours(args):
         hu[:] = lat.get_gauge().view(np.float64).ravel()
         rng = inputs.make_rng(seeds["e2e_momenta"])
         hp[:] = rng.standard_normal(ncanon_p)
+        hp2 = torch.empty(ncanon_p, dtype=torch.float64, pin_memory=True).numpy()
+        hp2[:] = rng.standard_normal(ncanon_p)
+        moms = [hp if k % 2 == 0 else hp2 for k in range(args.steps)]
         lat.set_gauge(hu)
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
         # (a) the chain stays on the device (as an HMC user runs it): each
-        # trajectory's input, the momenta, comes from pinned host memory and
-        # its result (dH, H, accept) goes back
+        # trajectory's input, the momenta, comes from pinned host memory (two
+        # buffers in turn) and its result (dH, H, accept) goes back; one
+        # fg_trajectories_host_momenta call, which uploads the next momenta
+        # while the current trajectory runs
         t0 = time.perf_counter()
-        for _ in range(args.steps):
-            lat.set_momenta(hp)
-            r = lat.trajectory(args.integrator, args.dt, TAU, refresh=False, u_accept=-1.0)
+        lat.trajectories_host_momenta(args.integrator, args.dt, TAU, moms)
         torch.cuda.synchronize()
         e2e_s = reduce_max(time.perf_counter() - t0, world, "cuda")
+        # (a') the same with one fg_set_momenta + fg_trajectory pair per
+        # trajectory: upload and MD in sequence
+        lat.set_gauge(hu)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            lat.set_momenta(moms[k])
+            r = lat.trajectory(args.integrator, args.dt, TAU, refresh=False, u_accept=-1.0)
+        torch.cuda.synchronize()
+        e2e_seq = reduce_max(time.perf_counter() - t0, world, "cuda")
         # (b) stateless: the whole gauge field goes up and comes back as well
         lat.set_gauge(hu)
         torch.cuda.synchronize()
@@ -737,9 +752,14 @@ def run_ours(args):
         e2e = {"value": whole_job_rate(args.steps, world, e2e_s), "unit": UNIT,
                "h2d_bytes_per_step": ncanon_p * 8,
                "d2h_bytes_per_step": 6 * 8,
-               "note": "per trajectory through fg_set_momenta + fg_trajectory: momenta uploaded from pinned "
-                       "host memory (canonical FP64), trajectory run on the device-resident chain, result "
-                       "(dH, H0, H1 sums, accept) read back",
+               "note": "per trajectory through fg_trajectories_host_momenta: momenta uploaded from pinned "
+                       "host memory (canonical FP64) on a copy stream while the previous trajectory runs, "
+                       "trajectory run on the device-resident chain, result (dH, H0, H1 sums, accept) read "
+                       "back after each trajectory",
+               "sequential": {"value": whole_job_rate(args.steps, world, e2e_seq), "unit": UNIT,
+                              "h2d_bytes_per_step": ncanon_p * 8, "d2h_bytes_per_step": 6 * 8,
+                              "note": "fg_set_momenta then fg_trajectory per trajectory: upload, conversion "
+                                      "and MD in sequence"},
                "stateless": {"value": whole_job_rate(args.steps, world, e2e_sl), "unit": UNIT,
                              "h2d_bytes_per_step": (ncanon_u + ncanon_p) * 8,
                              "d2h_bytes_per_step": ncanon_u * 8 + 6 * 8,

@@ -226,6 +226,26 @@ fg_status fg_trajectory_nested(fg_lattice *h, fg_integrator outer, fg_integrator
                                double dt, double tau, int refresh, double u_accept,
                                fg_traj_result *out);
 
+/* n HMC trajectories whose momenta come from host memory: trajectory k
+ * starts from the momenta at host_p8[k] (V x 4 x 8 doubles, layout above)
+ * and takes its Metropolis uniform from u_accept[k] (u_accept NULL, or an
+ * entry < 0: the handle's host RNG; every entry must be < 1).  Links, momenta,
+ * pseudofermion and results are those of n calls of fg_set_momenta(host_p8[k])
+ * followed by fg_trajectory(h, integ, dt, tau, 0, u_accept[k], &out[k]).
+ * The upload of trajectory k+1's momenta runs on a second stream while
+ * trajectory k runs on the handle's stream, so the transfers overlap the MD
+ * when the host arrays are page-locked (pageable memory works, without the
+ * overlap).  The two uploads in flight share the handle's canonical staging
+ * buffer (4 V 18 doubles, allocated on first use as for fg_set_gauge): the
+ * call needs no device buffer beyond those; the second stream and its
+ * events are created on the first call.  The host
+ * arrays are not read after the call returns.  out may be NULL; on an error
+ * at trajectory k, out[0..k-1] hold the completed trajectories.  FG_EINVAL on
+ * n < 0, a NULL array or pointer (n > 0), or u_accept[k] >= 1. */
+fg_status fg_trajectories_host_momenta(fg_lattice *h, fg_integrator integ, double dt, double tau, int n,
+                                       const double *const *host_p8, const double *u_accept,
+                                       fg_traj_result *out);
+
 /* Building blocks for callers and tests (even-site spinors, host layout above). */
 /* out = Mhat in (dagger = 0) or Mhat^dagger in (dagger = 1). */
 fg_status fg_apply_mhat(fg_lattice *h, const double *host_in_even, double *host_out_even,

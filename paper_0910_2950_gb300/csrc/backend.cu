@@ -50,8 +50,12 @@ class Backend final : public IBackend {
     for (void* p : allocs_) cudaFree(p);
     if (host_out_) cudaFreeHost(host_out_);
     if (mapped_) cudaFreeHost(mapped_);
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 2; ++i) {
       if (ev_[i]) cudaEventDestroy(ev_[i]);
+      if (ev_copied_[i]) cudaEventDestroy(ev_copied_[i]);
+      if (ev_read_[i]) cudaEventDestroy(ev_read_[i]);
+    }
+    if (cs_) cudaStreamDestroy(cs_);
     for (const CgGraph& c : cg_graphs_) cudaGraphExecDestroy(c.exec);
   }
 
@@ -115,6 +119,51 @@ class Backend final : public IBackend {
     return sync();
   }
   fg_status get_momenta(double* host) override { return download_mom(P_, host); }
+
+  // n trajectories from host momenta: the upload of trajectory k+1's momenta
+  // (into the other half of the canonical staging buffer, on a copy stream)
+  // overlaps trajectory k on st_.  Each half is rewritten only after the
+  // conversion that read it two trajectories earlier has run.
+  fg_status trajectories_host_momenta(int integ, double dt, int nsteps, int n, const double* const* hp,
+                                      const double* u, fg_traj_result* out) override {
+    if (n <= 0) return FG_OK;
+    const size_t nd = (size_t)4 * g_.V * 8;
+    fg_status s = ensure_canon(2 * nd);
+    if (s != FG_OK) return s;
+    if ((s = ensure_copy_stream()) != FG_OK) return s;
+    double* const stage[2] = {canon_, canon_ + nd};
+    auto upload = [&](int j) -> fg_status {
+      const int b = j & 1;
+      if (j >= 2 && cudaStreamWaitEvent(cs_, ev_read_[b], 0) != cudaSuccess) return cuda_fail("stream wait");
+      if (cudaMemcpyAsync(stage[b], hp[j], nd * sizeof(double), cudaMemcpyHostToDevice, cs_) != cudaSuccess)
+        return cuda_fail("momenta upload");
+      if (cudaEventRecord(ev_copied_[b], cs_) != cudaSuccess) return cuda_fail("event record");
+      return FG_OK;
+    };
+    s = upload(0);
+    for (int k = 0; s == FG_OK && k < n; ++k) {
+      if (k + 1 < n && (s = upload(k + 1)) != FG_OK) break;
+      const int b = k & 1;
+      if (cudaStreamWaitEvent(st_, ev_copied_[b], 0) != cudaSuccess) {
+        s = cuda_fail("stream wait");
+        break;
+      }
+      s = run(KC_CONVERT, [&] { return launch_mom_to_device<R>(g_, stage[b], P_, st_); });
+      if (s != FG_OK) break;
+      if (cudaEventRecord(ev_read_[b], st_) != cudaSuccess) {
+        s = cuda_fail("event record");
+        break;
+      }
+      fg_traj_result r;
+      std::memset(&r, 0, sizeof(r));
+      s = trajectory(integ, dt, nsteps, 0, u ? u[k] : -1.0, &r);
+      if (out) out[k] = r;
+    }
+    // no copy may read the caller's memory after the call returns
+    const cudaError_t e = cudaStreamSynchronize(cs_);
+    if (s == FG_OK && e != cudaSuccess) s = h_->fail(FG_ECUDA, cudaGetErrorString(e));
+    return s;
+  }
 
   fg_status refresh_momenta() override {
     const uint32_t d = draw_++;
@@ -350,6 +399,10 @@ class Backend final : public IBackend {
   double* part_rr_ = nullptr;
   Mapped* mapped_ = nullptr;
   cudaEvent_t ev_[2] = {nullptr, nullptr};
+  // copy stream and its events for trajectories_host_momenta
+  cudaStream_t cs_ = nullptr;
+  cudaEvent_t ev_copied_[2] = {nullptr, nullptr};
+  cudaEvent_t ev_read_[2] = {nullptr, nullptr};
   double sf0_ = 0.0;
   bool sf0_valid_ = false;
   int solves_ = 0;
@@ -375,6 +428,18 @@ class Backend final : public IBackend {
     fg_status s = alloc((void**)&canon_, want * sizeof(double));
     if (s != FG_OK) return s;
     canon_n_ = want;
+    return FG_OK;
+  }
+  fg_status ensure_copy_stream() {
+    if (cs_) return FG_OK;
+    if (cudaStreamCreateWithFlags(&cs_, cudaStreamNonBlocking) != cudaSuccess) {
+      cs_ = nullptr;
+      return cuda_fail("copy stream");
+    }
+    for (int i = 0; i < 2; ++i)
+      if (cudaEventCreateWithFlags(&ev_copied_[i], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&ev_read_[i], cudaEventDisableTiming) != cudaSuccess)
+        return cuda_fail("event");
     return FG_OK;
   }
   fg_status cuda_fail(const char* what) {

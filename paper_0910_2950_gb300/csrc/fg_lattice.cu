@@ -332,6 +332,22 @@ fg_status fg_trajectory_nested(fg_lattice* h, fg_integrator outer, fg_integrator
   if (out) *out = r;
   return s;
 }
+fg_status fg_trajectories_host_momenta(fg_lattice* h, fg_integrator integ, double dt, double tau, int n,
+                                       const double* const* host_p8, const double* u_accept,
+                                       fg_traj_result* out) {
+  FG_CHECK_HANDLE(h);
+  if ((int)integ < 0 || (int)integ > 5) return h->fail(FG_EINVAL, "bad integrator");
+  if (!(dt > 0.0) || !(tau > 0.0)) return h->fail(FG_EINVAL, "dt and tau must be positive");
+  const int ns = (int)std::llround(tau / dt);
+  if (ns < 1 || std::fabs(ns * dt - tau) > 1e-9 * tau) return h->fail(FG_EINVAL, "tau must be a multiple of dt");
+  if (n < 0) return h->fail(FG_EINVAL, "n must be >= 0");
+  if (n > 0 && !host_p8) return h->fail(FG_EINVAL, "null momenta array");
+  for (int k = 0; k < n; ++k) {
+    if (!host_p8[k]) return h->fail(FG_EINVAL, "null momenta pointer");
+    if (u_accept && !(u_accept[k] < 1.0)) return h->fail(FG_EINVAL, "u_accept must be < 1");
+  }
+  return h->be->trajectories_host_momenta((int)integ, dt, ns, n, host_p8, u_accept, out);
+}
 fg_status fg_apply_mhat(fg_lattice* h, const double* in, double* out, int dagger) {
   FG_CHECK_HANDLE(h);
   if (!in || !out) return h->fail(FG_EINVAL, "null spinor pointer");

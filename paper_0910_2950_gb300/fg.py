@@ -86,6 +86,8 @@ SIGNATURES = {
     "fg_timing_reset": (_i, [_vp]),
     "fg_kernel_time": (_i, [_vp, C.c_char_p, _dp, C.POINTER(C.c_longlong)]),
     "fg_trajectory_nested": (_i, [_vp, _i, _i, _i, _d, _d, _i, _d, C.POINTER(FgTrajResult)]),
+    "fg_trajectories_host_momenta": (_i, [_vp, _i, _d, _d, _i, C.POINTER(_dp), _dp,
+                                         C.POINTER(FgTrajResult)]),
     "fg_launch_count": (C.c_longlong, [_vp]),
     "fg_sync": (_i, [_vp]),
     "fg_device_bytes": (C.c_ulonglong, [_vp]),
@@ -266,6 +268,19 @@ class Lattice:
         self._call("fg_trajectory_nested", INTEGRATORS[outer], INTEGRATORS[inner], int(n_inner), float(dt),
                    float(tau), int(bool(refresh)), float(u_accept), C.byref(r))
         return {k: getattr(r, k) for k, _ in FgTrajResult._fields_}
+
+    def trajectories_host_momenta(self, integrator, dt, tau, momenta, u_accept=None):
+        """len(momenta) trajectories (refresh off), trajectory k from the host
+        momenta ``momenta[k]``; uploads overlap the previous trajectory (use
+        page-locked arrays for the overlap).  Returns one result dict each."""
+        arrs = [_f64(p, (self.V, 4, 8)) for p in momenta]
+        n = len(arrs)
+        ptrs = (_dp * max(n, 1))(*[_ptr(a) for a in arrs])
+        u = None if u_accept is None else _f64(u_accept, (n,))
+        res = (FgTrajResult * max(n, 1))()
+        self._call("fg_trajectories_host_momenta", INTEGRATORS[integrator], float(dt), float(tau), n, ptrs,
+                   _ptr(u) if u is not None else None, res)
+        return [{k: getattr(r, k) for k, _ in FgTrajResult._fields_} for r in res[:n]]
 
     # -- fermion building blocks
     def apply_mhat(self, x_even, dagger=False):
