@@ -54,13 +54,18 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12
 # FP64 is nominal (1.25 TFLOP/s for the whole GPU).
 FP64_PEAK_TFLOPS = 1.25
 
-# Algorithmic work per link of the fused gauge-force kernel, by mode:
-# staple sum 6 x (2 products of 198 flop + 18 to accumulate) = 2484, U*A 198,
-# projection and scale 24, kick 16; exp(i c P) (Cayley-Hamilton) 420 and U <- E U 198;
-# FP32 re-unitarisation 100.
-FLOP_FORCE = 2484 + 198 + 24
+# Algorithmic work per link of the fused gauge-force kernel, by mode, with
+# 198 flop per 3x3 complex product and 18 per accumulation: the staple sum is
+# 6 x (2 x 198 + 18) = 2484; the FP32 12-real kernel shares the upper-staple
+# product T of a plane between its two links (per site 6 T products and 12
+# accumulated products instead of 12 and 12), 3 x 414 + (6 x 198 + 12 x 216) / 4
+# = 2187; then U*A 198, projection and scale 24, kick 16; exp(i c P)
+# (Cayley-Hamilton with the Hermitian square) 322 and U <- E U 198; FP32
+# re-unitarisation 100.  Rebuilding the third row of 12-real links is not counted.
+FLOP_STAPLES = {("fp32", 18): 2484, ("fp32", 12): 2187, ("fp64", 18): 2484, ("fp64", 12): 2484}
+FLOP_FORCE_REST = 198 + 24
 FLOP_KICK = 16
-FLOP_EXP_MUL = 420 + 198
+FLOP_EXP_MUL = 322 + 198
 FLOP_REUNIT = 100
 
 
@@ -651,6 +656,7 @@ def run_ours(args):
     # ---------------------------------------------------------------- roofline (gauge force)
     links = 4 * lat.V
     reunit = 1 if args.precision == "fp32" else 0
+    FLOP_FORCE = FLOP_STAPLES[(args.precision, args.link_reals)] + FLOP_FORCE_REST
     # per FG trajectory: n (kick+drift) + n displacements + n (FG kick + drift) + 1 final kick
     if args.integrator in ("fg", "force_gradient"):
         per_traj = nsteps * (FLOP_FORCE + FLOP_KICK + FLOP_EXP_MUL + reunit * FLOP_REUNIT)   # P Q

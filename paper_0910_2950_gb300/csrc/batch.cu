@@ -74,9 +74,8 @@ __global__ void __launch_bounds__(8 * H, TileBounds<H>::min_blocks)
     const ChainDesc& cd = chains[t.chain];
     const Geom g = cd.g;
     int s;
-    if (!tile_site<H>(t, g, s)) continue;
-    int c[4], par;
-    cb_coords(g, s, c, par);
+    const bool ok = tile_site<H>(t, g, s);
+    if (!kForceSharedT<R, NC> && !ok) continue;
     Gauge<R, NC> u, ub, uo;
     u.p = U + cd.goff; u.V = g.V;
     ub.p = Ubase ? Ubase + cd.goff : nullptr; ub.V = g.V;
@@ -85,9 +84,26 @@ __global__ void __launch_bounds__(8 * H, TileBounds<H>::min_blocks)
     p.p = P ? P + cd.moff : nullptr; p.V = g.V;
     f.p = F ? F + cd.moff : nullptr; f.V = g.V;
     ff.p = nullptr; ff.V = g.V;
-    force_link<R, NC, MODE>(u, p, f, ff, ub, uo, g, c, s, (int)threadIdx.y, R(cd.beta / 6.0), R(ckick),
-                            R(cdrift), R(cdisp), reunit);
+    if constexpr (kForceSharedT<R, NC>) {
+      // the same staple arithmetic as the single-lattice kernel; the whole
+      // block takes the barriers (uniform tile loop)
+      extern __shared__ float2 batch_tsh[];
+      force_link_shared<NC, MODE, 2 * H>(reinterpret_cast<float2(*)[9][2 * H]>(batch_tsh), ok, s, u, p, f, ff, ub,
+                                         uo, g, R(cd.beta / 6.0), R(ckick), R(cdrift), R(cdisp), reunit, R(1));
+      __syncthreads();   // the next tile rewrites the slots
+    } else {
+      int c[4], par;
+      cb_coords(g, s, c, par);
+      force_link<R, NC, MODE>(u, p, f, ff, ub, uo, g, c, s, (int)threadIdx.y, R(cd.beta / 6.0), R(ckick),
+                              R(cdrift), R(cdisp), reunit);
+    }
   }
+}
+
+// Dynamic shared memory of batch_force_kernel with H half-sites per tile.
+template <typename R, int NC, int H>
+constexpr size_t batch_force_smem() {
+  return kForceSharedT<R, NC> ? (size_t)6 * 9 * 2 * H * sizeof(float2) : 0;
 }
 
 template <typename R, int NC, int H>
@@ -296,6 +312,20 @@ class Batch final : public IBatch {
   }
 
   fg_status init() {
+    // 64-half-site tiles of the FP32 force kernel use more than the default
+    // 48 KB of dynamic shared memory
+    if (batch_force_smem<R, NC, 64>() > 48 * 1024) {
+      const int bytes = (int)batch_force_smem<R, NC, 64>();
+      if (cudaFuncSetAttribute(batch_force_kernel<R, NC, FM_STORE, 64>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess ||
+          cudaFuncSetAttribute(batch_force_kernel<R, NC, FM_KICK, 64>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess ||
+          cudaFuncSetAttribute(batch_force_kernel<R, NC, FM_KICK_DRIFT, 64>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess ||
+          cudaFuncSetAttribute(batch_force_kernel<R, NC, FM_DISPLACE, 64>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess)
+        return cuda_fail("force kernel shared-memory attribute");
+    }
     const int n = b_->prm.nchains;
     std::vector<ChainDesc> cds(n);
     long long goff = 0, moff = 0, soff = 0;
@@ -573,26 +603,29 @@ class Batch final : public IBatch {
     const int reunit = b_->prm.reunitarize;
     char* Pp = (char*)P_;
     return lrun([&] {
+      const size_t sm = batch_force_smem<R, NC, H>();
+      const Tile* tl = d_tiles_[hi];
+      const ChainDesc* cds = d_chains_h_[hi];
       switch (mode) {
         case FM_STORE:
-          batch_force_kernel<R, NC, FM_STORE, H><<<gr, blk, 0, st_>>>(d_tiles_[hi], nt, d_chains_h_[hi], (char*)U, Pp,
-                                                                      (char*)F, (char*)Ubase, (char*)Uout, ckick,
-                                                                      cdrift, cdisp, reunit);
+          batch_force_kernel<R, NC, FM_STORE, H><<<gr, blk, sm, st_>>>(tl, nt, cds, (char*)U, Pp, (char*)F,
+                                                                      (char*)Ubase, (char*)Uout, ckick, cdrift,
+                                                                      cdisp, reunit);
           break;
         case FM_KICK:
-          batch_force_kernel<R, NC, FM_KICK, H><<<gr, blk, 0, st_>>>(d_tiles_[hi], nt, d_chains_h_[hi], (char*)U, Pp,
-                                                                     (char*)F, (char*)Ubase, (char*)Uout, ckick,
-                                                                     cdrift, cdisp, reunit);
+          batch_force_kernel<R, NC, FM_KICK, H><<<gr, blk, sm, st_>>>(tl, nt, cds, (char*)U, Pp, (char*)F,
+                                                                     (char*)Ubase, (char*)Uout, ckick, cdrift,
+                                                                     cdisp, reunit);
           break;
         case FM_KICK_DRIFT:
-          batch_force_kernel<R, NC, FM_KICK_DRIFT, H><<<gr, blk, 0, st_>>>(d_tiles_[hi], nt, d_chains_h_[hi],
-                                                                           (char*)U, Pp, (char*)F, (char*)Ubase,
-                                                                           (char*)Uout, ckick, cdrift, cdisp, reunit);
+          batch_force_kernel<R, NC, FM_KICK_DRIFT, H><<<gr, blk, sm, st_>>>(tl, nt, cds, (char*)U, Pp, (char*)F,
+                                                                           (char*)Ubase, (char*)Uout, ckick,
+                                                                           cdrift, cdisp, reunit);
           break;
         default:
-          batch_force_kernel<R, NC, FM_DISPLACE, H><<<gr, blk, 0, st_>>>(d_tiles_[hi], nt, d_chains_h_[hi],
-                                                                         (char*)U, Pp, (char*)F, (char*)Ubase,
-                                                                         (char*)Uout, ckick, cdrift, cdisp, reunit);
+          batch_force_kernel<R, NC, FM_DISPLACE, H><<<gr, blk, sm, st_>>>(tl, nt, cds, (char*)U, Pp, (char*)F,
+                                                                         (char*)Ubase, (char*)Uout, ckick, cdrift,
+                                                                         cdisp, reunit);
           break;
       }
       return cudaGetLastError();

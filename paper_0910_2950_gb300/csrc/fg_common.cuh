@@ -192,8 +192,33 @@ template <> struct ExpSmall<float> { static constexpr float c1_min = 1e-12f; };
 // Morningstar and Peardon (Phys. Rev. D 69 (2004) 054501, section III):
 // exp(iA) = f0 + f1 A + f2 A^2 with f_j from c0 = det A and c1 = Tr A^2 / 2;
 // negative c0 is mapped to positive through f_j(-c0) = (-1)^j conj(f_j(c0)).
+// A^2 for Hermitian A: real diagonal entries sum_k |a_ik|^2, the lower
+// triangle the conjugate of the upper one (half the products of mul).
+template <typename R> __device__ __forceinline__ M3<R> herm_sq(const M3<R>& a) {
+  M3<R> s;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    R d = R(0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) d = fma(a.e[i][k].re, a.e[i][k].re, fma(a.e[i][k].im, a.e[i][k].im, d));
+    s.e[i][i] = cx<R>(d, R(0));
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = i + 1; j < 3; ++j) {
+      Cx<R> c = a.e[i][0] * a.e[0][j];
+      cmac(c, a.e[i][1], a.e[1][j]);
+      cmac(c, a.e[i][2], a.e[2][j]);
+      s.e[i][j] = c;
+      s.e[j][i] = conj(c);
+    }
+  return s;
+}
+
+// Requires A exactly Hermitian (as alg_to_mat builds it).
 template <typename R> __device__ __forceinline__ M3<R> expi_herm(const M3<R>& a) {
-  M3<R> a2 = mul(a, a);
+  M3<R> a2 = herm_sq(a);
   R c0 = re_tr_mul(a, a2) * R(1.0 / 3.0);
   R c1 = R(0.5) * (a2.e[0][0].re + a2.e[1][1].re + a2.e[2][2].re);
   Cx<R> f0, f1, f2;
@@ -213,14 +238,15 @@ template <typename R> __device__ __forceinline__ M3<R> expi_herm(const M3<R>& a)
     const R u = r * ct;
     const R w = sqrt(c1) * st;
     const R u2 = u * u, w2 = w * w;
-    R xi0;
-    if (fabs(w) < R(0.05)) xi0 = R(1) - w2 * R(1.0 / 6.0) * (R(1) - w2 * R(0.05) * (R(1) - w2 * R(1.0 / 42.0)));
-    else xi0 = sin(w) / w;
-    R s2u, c2u, su, cu, sw, cw;
-    sincos(R(2) * u, &s2u, &c2u);
+    R su, cu, sw, cw;
     sincos(u, &su, &cu);
     sincos(w, &sw, &cw);
-    (void)sw;
+    R xi0;
+    if (fabs(w) < R(0.05)) xi0 = R(1) - w2 * R(1.0 / 6.0) * (R(1) - w2 * R(0.05) * (R(1) - w2 * R(1.0 / 42.0)));
+    else xi0 = sw / w;
+    // double-angle identities for 2u (a few ulp, as a third sincos would give)
+    const R s2u = R(2) * su * cu;
+    const R c2u = (cu - su) * (cu + su);
     const Cx<R> e2 = cx<R>(c2u, s2u);
     const Cx<R> em = cx<R>(cu, -su);
     const Cx<R> h0 = (u2 - w2) * e2 + em * cx<R>(R(8) * u2 * cw, R(2) * u * (R(3) * u2 + w2) * xi0);

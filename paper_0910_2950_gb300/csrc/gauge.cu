@@ -12,6 +12,8 @@
 //
 // One thread per link; a block is 64 consecutive checkerboard sites x 4
 // directions, so the four links of a site and their staples share L1/L2 lines.
+#include <type_traits>
+
 #include "fg_common.cuh"
 #include "fg_kernels.h"
 #include "gauge_device.cuh"
@@ -32,16 +34,24 @@ constexpr int kSitesPerBlock = 64;
 
 
 template <typename R, int NC, int MODE>
-__global__ void __launch_bounds__(256, FG_FORCE_MIN_BLOCKS) gauge_force_kernel(Gauge<R, NC> U, Mom<R> P, Mom<R> F,
+__global__ void __launch_bounds__(256, (kForceMinBlocks<R, NC>)) gauge_force_kernel(Gauge<R, NC> U, Mom<R> P, Mom<R> F,
                                                           Mom<R> FF, Gauge<R, NC> Ubase,
                                                           Gauge<R, NC> Uout, Geom g, R beta6,
                                                           R ckick, R cdrift, R cdisp, int reunit, R ffw) {
-  int s;
-  if (!link_site(g, s)) return;
-  int c[4], par;
-  cb_coords(g, s, c, par);
-  force_link<R, NC, MODE>(U, P, F, FF, Ubase, Uout, g, c, s, (int)threadIdx.y, beta6, ckick, cdrift, cdisp, reunit,
-                          ffw);
+  if constexpr (kForceSharedT<R, NC>) {
+    __shared__ float2 tsh[6][9][64];   // 64 sites: both parities x 32 half-sites (link_site)
+    int s;
+    const bool ok = link_site(g, s);
+    force_link_shared<NC, MODE, 64>(tsh, ok, s, U, P, F, FF, Ubase, Uout, g, beta6, ckick, cdrift, cdisp, reunit,
+                                    ffw);
+  } else {
+    int s;
+    if (!link_site(g, s)) return;
+    int c[4], par;
+    cb_coords(g, s, c, par);
+    force_link<R, NC, MODE>(U, P, F, FF, Ubase, Uout, g, c, s, (int)threadIdx.y, beta6, ckick, cdrift, cdisp,
+                            reunit, ffw);
+  }
 }
 
 template <typename R, int NC>
@@ -243,6 +253,23 @@ static inline dim3 link_block() { return dim3(kSitesPerBlock, 4); }
 
 template <typename R, int NC>
 cudaError_t launch_gauge_force(const GeomH& gh, int mode, const ForceArgs& a, cudaStream_t st) {
+  if constexpr (kForceSharedT<R, NC> && FG_FORCE_CARVEOUT > 0) {
+    // keep the L1 share of the unified L1/shared storage as large as the
+    // staple-product slots allow: the kernel's neighbour loads live in L1
+    static bool carved = false;
+    if (!carved) {
+      cudaFuncSetAttribute(gauge_force_kernel<R, NC, FM_STORE>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           FG_FORCE_CARVEOUT);
+      cudaFuncSetAttribute(gauge_force_kernel<R, NC, FM_KICK>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           FG_FORCE_CARVEOUT);
+      cudaFuncSetAttribute(gauge_force_kernel<R, NC, FM_KICK_DRIFT>,
+                           cudaFuncAttributePreferredSharedMemoryCarveout, FG_FORCE_CARVEOUT);
+      cudaFuncSetAttribute(gauge_force_kernel<R, NC, FM_DISPLACE>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           FG_FORCE_CARVEOUT);
+      cudaGetLastError();
+      carved = true;
+    }
+  }
   const Geom g = to_dev(gh);
   const int V = g.V;
   auto U = gauge_of<R, NC>(a.U, V);

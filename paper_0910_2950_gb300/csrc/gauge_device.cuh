@@ -3,6 +3,8 @@
 // (batch.cu), so that a chain in a batch runs the same arithmetic.
 #pragma once
 
+#include <type_traits>
+
 #include "df64.cuh"
 #include "fg_common.cuh"
 #include "fg_kernels.h"
@@ -78,13 +80,13 @@ __device__ __forceinline__ M3<R> staple_sum(const Gauge<R, NC>& U, const Geom& g
   return a;
 }
 
+// Everything after the staple sum a of U_mu(x): the force, then what MODE
+// does with it on this link.
 template <typename R, int NC, int MODE>
-__device__ __forceinline__ void force_link(const Gauge<R, NC>& U, const Mom<R>& P, const Mom<R>& F,
-                                           const Mom<R>& FF, const Gauge<R, NC>& Ubase,
-                                           const Gauge<R, NC>& Uout, const Geom& g, const int c[4], int s,
-                                           int mu, R beta6, R ckick, R cdrift, R cdisp, int reunit,
-                                           R ffw = R(1)) {
-  const M3<R> a = staple_sum(U, g, c, s, mu);
+__device__ __forceinline__ void force_finish(const Gauge<R, NC>& U, const Mom<R>& P, const Mom<R>& F,
+                                             const Mom<R>& FF, const Gauge<R, NC>& Ubase,
+                                             const Gauge<R, NC>& Uout, int s, int mu, const M3<R>& a, R beta6,
+                                             R ckick, R cdrift, R cdisp, int reunit, R ffw) {
   const M3<R> ul = U.load(mu, s);
   const M3<R> omega = mul(ul, a);
   R f[8];
@@ -122,6 +124,129 @@ __device__ __forceinline__ void force_link(const Gauge<R, NC>& U, const Mom<R>& 
     if (reunit) reunitarize(un);
     Uout.store(mu, s, un);
   }
+}
+
+template <typename R, int NC, int MODE>
+__device__ __forceinline__ void force_link(const Gauge<R, NC>& U, const Mom<R>& P, const Mom<R>& F,
+                                           const Mom<R>& FF, const Gauge<R, NC>& Ubase,
+                                           const Gauge<R, NC>& Uout, const Geom& g, const int c[4], int s,
+                                           int mu, R beta6, R ckick, R cdrift, R cdisp, int reunit,
+                                           R ffw = R(1)) {
+  const M3<R> a = staple_sum(U, g, c, s, mu);
+  force_finish<R, NC, MODE>(U, P, F, FF, Ubase, Uout, s, mu, a, beta6, ckick, cdrift, cdisp, reunit, ffw);
+}
+
+// Whether the FP32 12-real force kernels share the upper-staple products of
+// a plane between its two links through shared memory (below).  With 12-real
+// links every load rebuilds a row, and the two loads a shared product saves
+// pay for the barrier and the shared memory: 418 vs 437 us per launch at
+// 32^4.  With 18-real links the same change executed 8% fewer instructions
+// but ran 2% slower (426 vs 416 us; the slots take L1 capacity from the
+// neighbour loads and the barrier stalls), and the FP64 kernels would need
+// 55 KB of slots per block; those compute every staple in full.
+#ifndef FG_FORCE_SHARED_T
+#define FG_FORCE_SHARED_T 1
+#endif
+// Resident blocks per SM of the sharing kernel (its register cap) and its
+// preferred shared-memory carveout in percent of the SM's maximum (44%: the
+// 100 KB configuration, room for three blocks of 64 sites).
+#ifndef FG_FORCE_SHARED_MIN_BLOCKS
+#define FG_FORCE_SHARED_MIN_BLOCKS 3
+#endif
+#ifndef FG_FORCE_CARVEOUT
+#define FG_FORCE_CARVEOUT 44
+#endif
+
+// Upper staples of the plane (mu, nu) at x, for its two links: with
+// T_{mu,nu} = U_nu(x+mu) U_mu(x+nu)^dag, the upper staple of U_mu(x) is
+// T U_nu(x)^dag and that of U_nu(x) is U_mu(x+nu) U_nu(x+mu)^dag U_mu(x)^dag
+// = T^dag U_mu(x)^dag = (U_mu(x) T)^dag.  The four direction threads of a
+// site are in one block: thread mu computes T_{mu,mu+1} and, for mu < 2,
+// T_{mu,mu+2} (6 products per site, 1 or 2 per thread), keeps its own term
+// and leaves T in shared memory; after a barrier the other thread of each
+// plane reads it.  A site's four links then take 46 3x3 products instead of
+// 52 and two fewer link loads per shared plane.  Slots: T_{mu,mu+1} in mu,
+// T_{mu,mu+2} in 4 + mu; entries as (re, im) pairs, site-minor.
+// The block is NS sites (threadIdx.x) x 4 directions (threadIdx.y); tsh has
+// room for the six slots of its NS sites.  Every thread of the block must
+// call this (it holds a barrier); ok = false threads only take part in the
+// barrier.  The caller separates two calls on the same tsh by a barrier.
+template <typename R, int NC>
+constexpr bool kForceSharedT = FG_FORCE_SHARED_T && std::is_same<R, float>::value && NC == 6;
+template <typename R, int NC>
+constexpr int kForceMinBlocks = kForceSharedT<R, NC> ? FG_FORCE_SHARED_MIN_BLOCKS : FG_FORCE_MIN_BLOCKS;
+
+template <int NC, int MODE, int NS>
+__device__ __forceinline__ void force_link_shared(float2 (*tsh)[9][NS], bool ok, int s, const Gauge<float, NC>& U,
+                                                  const Mom<float>& P, const Mom<float>& F, const Mom<float>& FF,
+                                                  const Gauge<float, NC>& Ubase, const Gauge<float, NC>& Uout,
+                                                  const Geom& g, float beta6, float ckick, float cdrift,
+                                                  float cdisp, int reunit, float ffw) {
+  const int x = threadIdx.x;
+  const int mu = threadIdx.y;
+  M3<float> a;
+  zero(a);
+  int c[4], par;
+  if (ok) {
+    cb_coords(g, s, c, par);
+    const int other = s + (par ? -g.Vh : g.Vh);
+    int dmu, dmu_m;
+    cb_half_steps(g, c, mu, dmu, dmu_m);
+    (void)dmu_m;
+    const int s_pmu = other + dmu;
+#pragma unroll 1
+    for (int k = 1; k < 4; ++k) {
+      const int nu = (mu + k) & 3;
+      int dp, dm;
+      cb_half_steps(g, c, nu, dp, dm);
+      if (k == 1 || (k == 2 && mu < 2)) {
+        const M3<float> t = mul_nd(U.load(nu, s_pmu), U.load(mu, other + dp));
+        const int slot = k == 1 ? mu : 4 + mu;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j) tsh[slot][3 * i + j][x] = make_float2(t.e[i][j].re, t.e[i][j].im);
+        mac_nd(a, t, U.load(nu, s));
+      }
+      {
+        // lower: (U_mu(x-nu) U_nu(x+mu-nu))^dag U_nu(x-nu)
+        const int s_mnu = other + dm;
+        const M3<float> t = mul(U.load(mu, s_mnu), U.load(nu, s + dm + dmu));
+        mac_dn(a, t, U.load(nu, s_mnu));
+      }
+    }
+  }
+  __syncthreads();
+  if (!ok) return;
+  // planes whose T the other thread left: p = mu - 1 (slot p) and, for
+  // mu >= 2, p = mu - 2 (slot 4 + p); add (U_p(x) T_{p,mu})^dag
+#pragma unroll 1
+  for (int r = 0; r < 2; ++r) {
+    if (r == 1 && mu < 2) break;
+    const int p = r == 0 ? ((mu + 3) & 3) : mu - 2;
+    const int slot = r == 0 ? p : 4 + p;
+    M3<float> t;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const float2 v = tsh[slot][3 * i + j][x];
+        t.e[i][j] = cx<float>(v.x, v.y);
+      }
+    const M3<float> up = U.load(p, s);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        // a_ij += conj((U_p T)_ji)
+        Cx<float> acc = conj(a.e[i][j]);
+        cmac(acc, up.e[j][0], t.e[0][i]);
+        cmac(acc, up.e[j][1], t.e[1][i]);
+        cmac(acc, up.e[j][2], t.e[2][i]);
+        a.e[i][j] = conj(acc);
+      }
+  }
+  force_finish<float, NC, MODE>(U, P, F, FF, Ubase, Uout, s, mu, a, beta6, ckick, cdrift, cdisp, reunit, ffw);
 }
 
 // U_out(s, mu) = exp(i c P) U_in(s, mu), the exact T-hat flow of section 2.

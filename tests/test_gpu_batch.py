@@ -47,11 +47,14 @@ def test_batch_fp64_matches_oracle(fgmod, integ):
             assert _rel(bat.get_momenta(k), p1) < 1e-11
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp64"])
-def test_same_alone_and_in_the_mix(fgmod, precision):
+# FP32 12-real runs the kernel that shares the upper-staple products through
+# shared memory, in every tile shape
+@pytest.mark.parametrize("precision,link_reals,tile", [("fp32", 18, 0), ("fp64", 18, 0), ("fp32", 12, 16),
+                                                       ("fp32", 12, 32), ("fp32", 12, 64)])
+def test_same_alone_and_in_the_mix(fgmod, precision, link_reals, tile):
     dims_list = [d for d, _ in CHAINS]
     betas = [b for _, b in CHAINS]
-    with fgmod.Batch(dims_list, betas, precision=precision, tile=0) as bat:
+    with fgmod.Batch(dims_list, betas, precision=precision, link_reals=link_reals, tile=tile) as bat:
         for k, dims in enumerate(dims_list):
             u, p = _inputs(k, dims)
             bat.set_gauge(k, u)
@@ -61,7 +64,7 @@ def test_same_alone_and_in_the_mix(fgmod, precision):
         mixed = [bat.get_gauge(k) for k in range(len(CHAINS))]
     for k, (dims, beta) in enumerate(CHAINS):
         u, p = _inputs(k, dims)
-        with fgmod.Lattice(dims, beta, precision=precision) as lat:
+        with fgmod.Lattice(dims, beta, precision=precision, link_reals=link_reals) as lat:
             lat.set_gauge(u)
             lat.set_momenta(p)
             r = lat.trajectory("fg", 0.25, 1.0, refresh=False, u_accept=0.0)
