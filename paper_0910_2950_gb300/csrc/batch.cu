@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(2 * H) batch_energy_kernel(const Tile* __restr
       u.p = U + cd.goff; u.V = cd.g.V;
       Mom<R> p;
       p.p = P ? P + cd.moff : nullptr; p.V = cd.g.V;
-      site_energy(u, p, cd.g, s, cd.beta, mode, h0 + cd.soff, v);
+      site_energy(u, p, cd.g, s, 6.0 * cd.beta, cd.beta / 3.0, mode, h0 + cd.soff, v);
     }
     // one partial per tile (a block may handle several tiles)
     __shared__ double sh[3][32];

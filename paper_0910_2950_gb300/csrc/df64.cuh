@@ -103,4 +103,34 @@ template <> struct Quad<DF> {
   }
 };
 
+// block_reduce_store (fg_common.cuh) for double-float values (fixed tree, FP32 arithmetic only); the
+// partials are stored as doubles.
+template <int NV>
+__device__ __forceinline__ void block_reduce_store_df(DF v[NV], double* __restrict__ partial,
+                                                      int nblocks_stride) {
+  __shared__ DF shd[NV][32];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int nwarps = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    DF x = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+      x = x + DF(__shfl_down_sync(0xffffffffu, x.hi, o), __shfl_down_sync(0xffffffffu, x.lo, o));
+    if (lane == 0) shd[k][warp] = x;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      DF x = lane < nwarps ? shd[k][lane] : DF(0.0f);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+        x = x + DF(__shfl_down_sync(0xffffffffu, x.hi, o), __shfl_down_sync(0xffffffffu, x.lo, o));
+      if (lane == 0) partial[(size_t)k * nblocks_stride + blockIdx.x] = double(x);
+    }
+  }
+}
+
 }  // namespace fg

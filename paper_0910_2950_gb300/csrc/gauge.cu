@@ -6,8 +6,9 @@
 //    link, or displace the link along the force for the force-gradient step
 //    of Table 1 (U' = exp(-i dt^2/24 F) U).
 //  * drift_kernel: the exact T-hat flow U <- exp(i c P) U (section 2).
-//  * energy_kernel: per-site T(x) + S_G(x) in FP64, block partial sums for the
-//    dH of section 5 (summed as site-by-site differences).
+//  * energy_kernel: per-site T(x) + S_G(x) (double-float sums of FP32 terms,
+//    FP64 for FP64 fields), block partial sums for the dH of section 5
+//    (summed as site-by-site differences).
 //  * refresh_momenta_kernel: unit-Gaussian momenta from a counter-based RNG.
 //
 // One thread per link; a block is 64 consecutive checkerboard sites x 4
@@ -117,17 +118,25 @@ __global__ void __launch_bounds__(256) reunitarize_kernel(Gauge<R, NC> U, int V)
 
 constexpr int kEnergyThreads = 256;
 
+// Per-site energies, one thread per site (blocks of 128 half-sites of both
+// parities), block partial sums in the per-site value type A (double-float
+// for FP32 fields: GB300's FP64 unit made the FP64 block tree and per-site
+// arithmetic most of this kernel's time).
+template <typename R> using EnergyAcc = typename std::conditional<std::is_same<R, float>::value, DF, double>::type;
+
 template <typename R, int NC>
 __global__ void __launch_bounds__(kEnergyThreads) energy_kernel(Gauge<R, NC> U, Mom<R> P, Geom g,
-                                                                double beta, int mode,
-                                                                double* __restrict__ h0,
+                                                                EnergyAcc<R> beta6, EnergyAcc<R> beta3, int mode,
+                                                                EnergyAcc<R>* __restrict__ h0,
                                                                 double* __restrict__ partial,
-                                                                const double* __restrict__ sg_in,
-                                                                double* __restrict__ sg_out) {
+                                                                const EnergyAcc<R>* __restrict__ sg_in,
+                                                                EnergyAcc<R>* __restrict__ sg_out) {
+  using A = EnergyAcc<R>;
   int s;
-  double v[3] = {0.0, 0.0, 0.0};  // S_G, T, dh
-  if (pair_site<kEnergyThreads / 2>(g, s)) site_energy(U, P, g, s, beta, mode, h0, v, sg_in, sg_out);
-  block_reduce_store<3>(v, partial, gridDim.x);
+  A v[3] = {A(0), A(0), A(0)};  // S_G, T, dh
+  if (pair_site<kEnergyThreads / 2>(g, s)) site_energy(U, P, g, s, beta6, beta3, mode, h0, v, sg_in, sg_out);
+  if constexpr (std::is_same<A, DF>::value) block_reduce_store_df<3>(v, partial, gridDim.x);
+  else block_reduce_store<3>(v, partial, gridDim.x);
 }
 
 __global__ void __launch_bounds__(1024) reduce_kernel(const double* __restrict__ partial, int nblocks,
@@ -336,8 +345,12 @@ cudaError_t launch_energy(const GeomH& gh, const void* U, const void* P, double 
                           double* sg_out) {
   const int nb = (gh.Vh + kEnergyThreads / 2 - 1) / (kEnergyThreads / 2);
   *nblocks = nb;
-  energy_kernel<R, NC><<<nb, kEnergyThreads, 0, st>>>(gauge_of<R, NC>(U, gh.V), mom_of<R>(P, gh.V),
-                                                      to_dev(gh), beta, mode, h0, partial, sg_in, sg_out);
+  // the per-site arrays are 8 bytes a site: doubles, or double-floats for FP32 fields
+  using A = EnergyAcc<R>;
+  static_assert(sizeof(A) == sizeof(double), "per-site slot size");
+  energy_kernel<R, NC><<<nb, kEnergyThreads, 0, st>>>(
+      gauge_of<R, NC>(U, gh.V), mom_of<R>(P, gh.V), to_dev(gh), A(6.0 * beta), A(beta / 3.0), mode,
+      reinterpret_cast<A*>(h0), partial, reinterpret_cast<const A*>(sg_in), reinterpret_cast<A*>(sg_out));
   return cudaGetLastError();
 }
 

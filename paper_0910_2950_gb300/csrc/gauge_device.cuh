@@ -263,25 +263,30 @@ __device__ __forceinline__ void drift_link(const Gauge<R, NC>& Uin, const Mom<R>
   Uout.store(mu, s, un);
 }
 
-// Per-site energy h(x) = T(x) + S_G(x) in FP64 (T = 0 if P is null): v[0] = S_G(x),
-// v[1] = T(x); mode 0 stores h0[s] = h(x), mode 1 sets v[2] = h(x) - h0[s].
-// If sg_in is given, S_G(x) is read from it instead of recomputed (the links
-// have not changed since it was stored); if sg_out is given, S_G(x) is stored.
-template <typename R, int NC>
+// Per-site energy h(x) = T(x) + S_G(x) (T = 0 if P is null), with
+// S_G(x) = sum_{mu<nu} beta (1 - Re Tr P_mu,nu(x) / 3) = beta6 - beta3 sum Re Tr
+// (beta6 = 6 beta, beta3 = beta / 3): v[0] = S_G(x), v[1] = T(x); mode 0
+// stores h0[s] = h(x), mode 1 sets v[2] = h(x) - h0[s].  If sg_in is given,
+// S_G(x) is read from it instead of recomputed (the links have not changed
+// since it was stored); if sg_out is given, S_G(x) is stored.  A is the type
+// of the per-site values: double, or DF for FP32 fields, which keeps FP64
+// arithmetic (1/64 of the FP32 rate on GB300) out of the kernel.  Sums of
+// FP32 terms are double-float in either case (each p^2 split exactly by an
+// FMA, each plaquette trace added with two_sum); FP64 fields sum in FP64.
+template <typename A> __device__ __forceinline__ A acc_of(DF x);
+template <> __device__ __forceinline__ DF acc_of<DF>(DF x) { return x; }
+template <> __device__ __forceinline__ double acc_of<double>(DF x) { return double(x); }
+
+template <typename R, int NC, typename A>
 __device__ __forceinline__ void site_energy(const Gauge<R, NC>& U, const Mom<R>& P, const Geom& g, int s,
-                                            double beta, int mode, double* __restrict__ h0, double v[3],
-                                            const double* __restrict__ sg_in = nullptr,
-                                            double* __restrict__ sg_out = nullptr) {
-  int c[4], par;
-  cb_coords(g, s, c, par);
-  // Sums of FP32 terms are taken in double-float (each p^2 split exactly by
-  // an FMA, each plaquette trace added with two_sum): as accurate as FP64
-  // sums to ~1e-14 relative, without GB300's slow FP64 unit; FP64 fields
-  // keep FP64 sums.
-  constexpr bool kDF = sizeof(R) == sizeof(float);
-  double t = 0.0;
+                                            A beta6, A beta3, int mode, A* __restrict__ h0, A v[3],
+                                            const A* __restrict__ sg_in = nullptr, A* __restrict__ sg_out = nullptr) {
+  constexpr bool kDF = std::is_same<R, float>::value;
+  static_assert(kDF || std::is_same<A, double>::value, "FP64 fields keep FP64 per-site values");
+  A t = A(0);
   if (P.p != nullptr) {
     DF tdf(0.0f);
+    double t64 = 0.0;
 #pragma unroll 1
     for (int mu = 0; mu < 4; ++mu) {
       R p[8];
@@ -292,18 +297,21 @@ __device__ __forceinline__ void site_energy(const Gauge<R, NC>& U, const Mom<R>&
           const float sq = __fmul_rn(p[k], p[k]);
           tdf = tdf + DF(sq, __fmaf_rn(p[k], p[k], -sq));
         } else {
-          t += double(p[k]) * double(p[k]);
+          t64 += double(p[k]) * double(p[k]);
         }
       }
     }
-    if constexpr (kDF) t = double(tdf);
-    t *= 0.5;
+    if constexpr (kDF) t = acc_of<A>(tdf) * A(0.5f);
+    else t = A(0.5 * t64);
   }
-  double sg = 0.0;
+  A sg;
   if (sg_in != nullptr) {
     sg = sg_in[s];
   } else {
+    int c[4], par;
+    cb_coords(g, s, c, par);
     DF trdf(0.0f);
+    double tr64 = 0.0;
 #pragma unroll
     for (int mu = 0; mu < 4; ++mu) {
       const M3<R> umu = U.load(mu, s);
@@ -312,16 +320,16 @@ __device__ __forceinline__ void site_energy(const Gauge<R, NC>& U, const Mom<R>&
         const M3<R> a = mul(umu, U.load(nu, cb_neighbor(g, c, mu, +1)));
         const M3<R> b = mul(U.load(nu, s), U.load(mu, cb_neighbor(g, c, nu, +1)));
         if constexpr (kDF) trdf = trdf + DF(float(re_tr_mul_nd(a, b)));
-        else sg += 1.0 - double(re_tr_mul_nd(a, b)) * (1.0 / 3.0);
+        else tr64 += double(re_tr_mul_nd(a, b));
       }
     }
-    if constexpr (kDF) sg = 6.0 - double(trdf) * (1.0 / 3.0);
-    sg *= beta;
+    if constexpr (kDF) sg = beta6 - beta3 * acc_of<A>(trdf);
+    else sg = beta6 - beta3 * A(tr64);
   }
   if (sg_out != nullptr) sg_out[s] = sg;
   v[0] = sg;
   v[1] = t;
-  const double h = sg + t;
+  const A h = sg + t;
   if (mode == 0) h0[s] = h;
   else if (mode == 1) v[2] = h - h0[s];
 }
