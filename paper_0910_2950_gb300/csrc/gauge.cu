@@ -264,20 +264,19 @@ template <typename R, int NC>
 cudaError_t launch_gauge_force(const GeomH& gh, int mode, const ForceArgs& a, cudaStream_t st) {
   if constexpr (kForceSharedT<R, NC> && FG_FORCE_CARVEOUT > 0) {
     // keep the L1 share of the unified L1/shared storage as large as the
-    // staple-product slots allow: the kernel's neighbour loads live in L1
-    static bool carved = false;
-    if (!carved) {
-      cudaFuncSetAttribute(gauge_force_kernel<R, NC, FM_STORE>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                           FG_FORCE_CARVEOUT);
-      cudaFuncSetAttribute(gauge_force_kernel<R, NC, FM_KICK>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                           FG_FORCE_CARVEOUT);
-      cudaFuncSetAttribute(gauge_force_kernel<R, NC, FM_KICK_DRIFT>,
-                           cudaFuncAttributePreferredSharedMemoryCarveout, FG_FORCE_CARVEOUT);
-      cudaFuncSetAttribute(gauge_force_kernel<R, NC, FM_DISPLACE>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                           FG_FORCE_CARVEOUT);
+    // staple-product slots allow: the kernel's neighbour loads live in L1.
+    // A preference only (once per process, thread-safe static initialisation);
+    // a refusal leaves the driver's choice and is not an error.
+    static const bool carved = [] {
+      const cudaFuncAttribute a = cudaFuncAttributePreferredSharedMemoryCarveout;
+      cudaFuncSetAttribute(gauge_force_kernel<R, NC, FM_STORE>, a, FG_FORCE_CARVEOUT);
+      cudaFuncSetAttribute(gauge_force_kernel<R, NC, FM_KICK>, a, FG_FORCE_CARVEOUT);
+      cudaFuncSetAttribute(gauge_force_kernel<R, NC, FM_KICK_DRIFT>, a, FG_FORCE_CARVEOUT);
+      cudaFuncSetAttribute(gauge_force_kernel<R, NC, FM_DISPLACE>, a, FG_FORCE_CARVEOUT);
       cudaGetLastError();
-      carved = true;
-    }
+      return true;
+    }();
+    (void)carved;
   }
   const Geom g = to_dev(gh);
   const int V = g.V;

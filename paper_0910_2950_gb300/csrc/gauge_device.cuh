@@ -117,12 +117,14 @@ __device__ __forceinline__ void force_finish(const Gauge<R, NC>& U, const Mom<R>
       Uout.store(mu, s, un);
     }
   } else {  // FM_DISPLACE
+    // The displaced links only serve one force evaluation and are then
+    // dropped, so they are not re-projected: exp(i A) U is unitary to the
+    // rounding of the product, and no error accumulates.
+    (void)reunit;
 #pragma unroll
     for (int k = 0; k < 8; ++k) f[k] *= -cdisp;
     const M3<R> e = expi_herm(alg_to_mat(f));
-    M3<R> un = mul(e, ul);
-    if (reunit) reunitarize(un);
-    Uout.store(mu, s, un);
+    Uout.store(mu, s, mul(e, ul));
   }
 }
 
