@@ -6,8 +6,8 @@
 //    link, or displace the link along the force for the force-gradient step
 //    of Table 1 (U' = exp(-i dt^2/24 F) U).
 //  * drift_kernel: the exact T-hat flow U <- exp(i c P) U (section 2).
-//  * energy_kernel: per-site T(x) + S_G(x) (double-float sums of FP32 terms,
-//    FP64 for FP64 fields), block partial sums for the dH of section 5
+//  * energy_kernel: per-site T(x) + S_G(x), in double-float for FP32 fields
+//    and FP64 for FP64 fields, block partial sums for the dH of section 5
 //    (summed as site-by-site differences).
 //  * refresh_momenta_kernel: unit-Gaussian momenta from a counter-based RNG.
 //
