@@ -111,7 +111,7 @@ typedef enum {
 } fg_precision;
 
 typedef struct {
-  int dims[4];             /* Lx, Ly, Lz, Lt; each even, >= 2 */
+  int dims[4];             /* Lx, Ly, Lz, Lt; each even, >= 2; volume <= 2^28 sites */
   double beta;             /* gauge coupling */
   double kappa;            /* hopping parameter; 0 => pure gauge (no fermions) */
   double alpha;            /* PQPQP parameter for FG_OMELYAN (default 0.1932) */
@@ -307,7 +307,7 @@ typedef struct fg_batch fg_batch;
 
 typedef struct {
   int nchains;             /* number of chains, >= 1 */
-  const int *dims;         /* nchains x 4 extents (Lx, Ly, Lz, Lt; even, >= 2); copied */
+  const int *dims;         /* nchains x 4 extents (Lx, Ly, Lz, Lt; even, >= 2; volume <= 2^28); copied */
   const double *beta;      /* nchains couplings; copied */
   int precision;           /* FG_FP32 (default) or FG_FP64 */
   int link_reals;          /* 18 or 12 */

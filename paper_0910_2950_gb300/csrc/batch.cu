@@ -832,6 +832,7 @@ fg_status fg_batch_create(const fg_batch_params* p, fg_batch** out) {
       if (d < 2 || (d & 1)) return FG_EINVAL;
       V *= d;
     }
+    if (V > (1LL << 28)) return FG_EINVAL;  // 32-bit element indices, as for one lattice
     if (!(p->beta[c] >= 0.0)) return FG_EINVAL;
     total += V;
   }

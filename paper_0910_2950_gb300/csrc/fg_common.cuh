@@ -486,18 +486,23 @@ template <typename R, int NC> struct Gauge {
   static constexpr int NP = NC / 2;
   void* __restrict__ p;
   int V;
+  // Element indices in 32 bits (the largest is 4 NP V + V, and the handles
+  // reject lattices where that would overflow), widened once per access.
+  __device__ __forceinline__ unsigned idx(int mu, int q, int s) const {
+    return ((unsigned)mu * NP + (unsigned)q) * (unsigned)V + (unsigned)s;
+  }
   __device__ __forceinline__ M3<R> load(int mu, int s) const {
     M3<R> m;
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
       Cx<R> a, b;
-      Quad<R>::load(p, ((size_t)mu * NP + q) * V + s, a, b);
+      Quad<R>::load(p, (size_t)idx(mu, q, s), a, b);
       m.e[(2 * q) / 3][(2 * q) % 3] = a;
       m.e[(2 * q + 1) / 3][(2 * q + 1) % 3] = b;
     }
     if (NC == 9) {
       const C2* tail = (const C2*)((const char*)p + (size_t)4 * NP * V * 4 * sizeof(R));
-      const C2 v = __ldg(tail + (size_t)mu * V + s);
+      const C2 v = __ldg(tail + (size_t)((unsigned)mu * (unsigned)V + (unsigned)s));
       m.e[2][2] = cx<R>(v.x, v.y);
     } else {
       rebuild_row2(m);
@@ -507,14 +512,14 @@ template <typename R, int NC> struct Gauge {
   __device__ __forceinline__ void store(int mu, int s, const M3<R>& m) const {
 #pragma unroll
     for (int q = 0; q < NP; ++q)
-      Quad<R>::store(p, ((size_t)mu * NP + q) * V + s, m.e[(2 * q) / 3][(2 * q) % 3],
+      Quad<R>::store(p, (size_t)idx(mu, q, s), m.e[(2 * q) / 3][(2 * q) % 3],
                      m.e[(2 * q + 1) / 3][(2 * q + 1) % 3]);
     if (NC == 9) {
       C2* tail = (C2*)((char*)p + (size_t)4 * NP * V * 4 * sizeof(R));
       C2 v;
       v.x = m.e[2][2].re;
       v.y = m.e[2][2].im;
-      tail[(size_t)mu * V + s] = v;
+      tail[(size_t)((unsigned)mu * (unsigned)V + (unsigned)s)] = v;
     }
   }
 };
@@ -534,13 +539,13 @@ template <int NC> struct Gauge<Half16, NC> {
     M3<float> m;
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
-      const uint2 v = __ldg((const uint2*)p + ((size_t)mu * NP + q) * V + s);
+      const uint2 v = __ldg((const uint2*)p + (size_t)(((unsigned)mu * NP + (unsigned)q) * (unsigned)V + (unsigned)s));
       m.e[(2 * q) / 3][(2 * q) % 3] = cx_of(v.x);
       m.e[(2 * q + 1) / 3][(2 * q + 1) % 3] = cx_of(v.y);
     }
     if (NC == 9) {
       const unsigned int* tail = (const unsigned int*)((const char*)p + (size_t)4 * NP * V * 8);
-      m.e[2][2] = cx_of(__ldg(tail + (size_t)mu * V + s));
+      m.e[2][2] = cx_of(__ldg(tail + (size_t)((unsigned)mu * (unsigned)V + (unsigned)s)));
     } else {
       rebuild_row2(m);
     }
@@ -549,11 +554,11 @@ template <int NC> struct Gauge<Half16, NC> {
   __device__ __forceinline__ void store(int mu, int s, const M3<float>& m) const {
 #pragma unroll
     for (int q = 0; q < NP; ++q)
-      ((uint2*)p)[((size_t)mu * NP + q) * V + s] =
+      ((uint2*)p)[(size_t)(((unsigned)mu * NP + (unsigned)q) * (unsigned)V + (unsigned)s)] =
           make_uint2(word_of(m.e[(2 * q) / 3][(2 * q) % 3]), word_of(m.e[(2 * q + 1) / 3][(2 * q + 1) % 3]));
     if (NC == 9) {
       unsigned int* tail = (unsigned int*)((char*)p + (size_t)4 * NP * V * 8);
-      tail[(size_t)mu * V + s] = word_of(m.e[2][2]);
+      tail[(size_t)((unsigned)mu * (unsigned)V + (unsigned)s)] = word_of(m.e[2][2]);
     }
   }
 };
@@ -563,18 +568,21 @@ template <int NC> struct Gauge<Half16, NC> {
 template <typename R> struct Mom {
   void* __restrict__ p;
   int V;
+  __device__ __forceinline__ unsigned idx(int mu, int q, int s) const {
+    return ((unsigned)mu * 2u + (unsigned)q) * (unsigned)V + (unsigned)s;
+  }
   __device__ __forceinline__ void load(int mu, int s, R out[8]) const {
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       Cx<R> a, b;
-      Quad<R>::load_cg(p, ((size_t)mu * 2 + q) * V + s, a, b);
+      Quad<R>::load_cg(p, (size_t)idx(mu, q, s), a, b);
       out[4 * q] = a.re; out[4 * q + 1] = a.im; out[4 * q + 2] = b.re; out[4 * q + 3] = b.im;
     }
   }
   __device__ __forceinline__ void store(int mu, int s, const R in[8]) const {
 #pragma unroll
     for (int q = 0; q < 2; ++q)
-      Quad<R>::store(p, ((size_t)mu * 2 + q) * V + s, cx<R>(in[4 * q], in[4 * q + 1]),
+      Quad<R>::store(p, (size_t)idx(mu, q, s), cx<R>(in[4 * q], in[4 * q + 1]),
                      cx<R>(in[4 * q + 2], in[4 * q + 3]));
   }
 };

@@ -212,7 +212,7 @@ fg_status fg_lattice_create(const fg_params* p, fg_lattice** out) {
   for (int i = 0; i < 4; ++i)
     if (p->dims[i] < 2 || (p->dims[i] & 1)) return FG_EINVAL;
   const long long V = (long long)p->dims[0] * p->dims[1] * p->dims[2] * p->dims[3];
-  if (V > (1LL << 28)) return FG_EINVAL;  // 32-bit link indices: 4V < 2^31
+  if (V > (1LL << 28)) return FG_EINVAL;  // 32-bit element indices of links and momenta: 16 V - 1 < 2^32
   if (p->precision != FG_FP64 && p->precision != FG_FP32 && p->precision != FG_FP32_FP16CG) return FG_EINVAL;
   if (p->link_reals != 18 && p->link_reals != 12) return FG_EINVAL;
   if (!(p->beta >= 0.0) || !(p->kappa >= 0.0) || !(p->cg_tol > 0.0) || !(p->cg_tol_action > 0.0) ||
