@@ -53,6 +53,7 @@ def test_params_default(lib):
 
 
 @pytest.mark.parametrize("field,value", [("dims", (3, 4, 4, 4)), ("dims", (4, 4, 0, 4)),
+                                         ("dims", (130, 128, 128, 128)),   # over 2^28 sites
                                          ("link_reals", 10), ("precision", 7), ("cg_maxiter", 0),
                                          ("cg_tol", 0.0), ("cg_delta", 1.5)])
 def test_create_rejects_bad_parameters_before_touching_the_device(lib, field, value):
@@ -74,3 +75,28 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.fg_launch_count(None) == -1
     assert lib.fg_last_error(None) == b"null handle"
     lib.fg_lattice_destroy(None)
+    assert lib.fg_trajectories_host_momenta(None, 2, 0.25, 1.0, 0, None, None, None) == fg.FG_EINVAL
+
+
+@pytest.mark.parametrize("case", ["odd", "too_large", "tile", "link_reals"])
+def test_batch_create_rejects_bad_parameters_before_touching_the_device(lib, case):
+    dims = [4, 4, 4, 4, 6, 6, 6, 6]
+    if case == "odd":
+        dims[5] = 5
+    elif case == "too_large":
+        dims[4:] = [130, 128, 128, 128]
+    betas = [6.0, 5.8]
+    p = fg.FgBatchParams()
+    lib.fg_batch_params_default(C.byref(p))
+    p.nchains = 2
+    d = (C.c_int * 8)(*dims)
+    b = (C.c_double * 2)(*betas)
+    p.dims = C.cast(d, C.POINTER(C.c_int))
+    p.beta = C.cast(b, C.POINTER(C.c_double))
+    if case == "tile":
+        p.tile = 48
+    elif case == "link_reals":
+        p.link_reals = 16
+    h = C.c_void_p()
+    assert lib.fg_batch_create(C.byref(p), C.byref(h)) == fg.FG_EINVAL
+    assert not h.value
