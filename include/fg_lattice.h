@@ -130,7 +130,8 @@ typedef struct {
 
 /* Result of one HMC trajectory (section 5, Fig. 1: dH over a whole trajectory). */
 typedef struct {
-  double dH;               /* H_end - H_start, summed site by site in FP64 */
+  double dH;               /* H_end - H_start, summed site by site (per-site values and block
+                              sums in double-float for FP32 fields, FP64 otherwise; FP64 total) */
   double H0, H1;           /* total H at start and end */
   double S_gauge0, S_gauge1;
   double S_ferm0, S_ferm1; /* pseudofermion action (0 for pure gauge) */

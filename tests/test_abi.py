@@ -6,6 +6,8 @@ These run without a GPU: nothing here launches a kernel.
 import ctypes as C
 import os
 import re
+import shutil
+import subprocess
 
 import pytest
 
@@ -100,3 +102,26 @@ def test_batch_create_rejects_bad_parameters_before_touching_the_device(lib, cas
     h = C.c_void_p()
     assert lib.fg_batch_create(C.byref(p), C.byref(h)) == fg.FG_EINVAL
     assert not h.value
+
+
+def _cc():
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    return cc
+
+
+def test_header_and_example_build_as_plain_c(lib, tmp_path):
+    """The ABI is usable from strict C99: the header alone, and the example
+    chain program compiled and linked against the library (not run: no GPU)."""
+    cc = _cc()
+    inc = os.path.join(ROOT, "include")
+    pkg = os.path.join(ROOT, "paper_0910_2950_gb300")
+    flags = ["-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", inc]
+    hdr_only = tmp_path / "h.c"
+    hdr_only.write_text('#include "fg_lattice.h"\nint main(void) { return FG_OK; }\n')
+    subprocess.run([cc] + flags + ["-c", str(hdr_only), "-o", str(tmp_path / "h.o")], check=True)
+    exe = tmp_path / "hmc_chain"
+    subprocess.run([cc] + flags + [os.path.join(pkg, "examples", "hmc_chain.c"), "-L", pkg, "-l:libfg_lattice.so",
+                                   "-Wl,-rpath," + pkg, "-lm", "-o", str(exe)], check=True)
+    assert exe.exists()

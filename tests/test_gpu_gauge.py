@@ -261,3 +261,28 @@ def test_stored_site_action_matches_recomputation(fgmod, precision):
         out.append(rows)
     assert out[0] == out[1]
     assert any(not a for _, _, a in out[0]) and any(a for _, _, a in out[0])
+
+
+def test_c_example_chain_runs(fgmod, tmp_path):
+    """The plain-C example (examples/hmc_chain.c) runs a short FG HMC chain
+    through the ABI alone: every dH finite, the plaquette of the evolving
+    field in (0, 1)."""
+    import os
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    pkg = os.path.join(root, "paper_0910_2950_gb300")
+    exe = tmp_path / "hmc_chain"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(root, "include"), os.path.join(pkg, "examples", "hmc_chain.c"),
+                    "-L", pkg, "-l:libfg_lattice.so", "-Wl,-rpath," + pkg, "-lm", "-o", str(exe)], check=True)
+    res = subprocess.run([str(exe), "6", "6"], capture_output=True, text=True, timeout=300)
+    assert res.returncode == 0, res.stderr
+    lines = [ln.split() for ln in res.stdout.splitlines() if ln.startswith("trajectory")]
+    assert len(lines) == 6
+    for ln in lines:
+        assert np.isfinite(float(ln[3]))
+        assert 0.0 < float(ln[9]) < 1.0
+    assert res.stdout.splitlines()[-1].startswith("accepted")
