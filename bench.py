@@ -672,8 +672,9 @@ def run_ours(args):
     esize = 4 if args.precision == "fp32" else 8
     bytes_per_launch = links * (args.link_reals * esize + 2 * 8 * esize)
     peak = FP32_PEAK_TFLOPS if args.precision == "fp32" else FP64_PEAK_TFLOPS
-    # DRAM bytes per link of the FP32 18-real FG mix from one ncu capture at
-    # 28^4 (profiles/gauge_force_fp32_28x4.md), scaled to this lattice
+    # DRAM bytes per link of the FP32 18-real FG mix from one ncu capture of
+    # the force kernel at 28^4 (its summary is kept with the profiles),
+    # scaled to this lattice
     traffic = (FORCE_TRAFFIC_BYTES_PER_LINK * links
                if FORCE_TRAFFIC_BYTES_PER_LINK is not None
                and (args.precision, args.link_reals, args.integrator) == ("fp32", 18, "fg") else None)
