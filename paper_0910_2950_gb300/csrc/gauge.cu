@@ -125,12 +125,10 @@ constexpr int kEnergyThreads = 256;
 template <typename R> using EnergyAcc = typename std::conditional<std::is_same<R, float>::value, DF, double>::type;
 
 template <typename R, int NC>
-__global__ void __launch_bounds__(kEnergyThreads) energy_kernel(Gauge<R, NC> U, Mom<R> P, Geom g,
-                                                                EnergyAcc<R> beta6, EnergyAcc<R> beta3, int mode,
-                                                                EnergyAcc<R>* __restrict__ h0,
-                                                                double* __restrict__ partial,
-                                                                const EnergyAcc<R>* __restrict__ sg_in,
-                                                                EnergyAcc<R>* __restrict__ sg_out) {
+__global__ void __launch_bounds__(kEnergyThreads, (std::is_same<R, float>::value ? 2 : 1))
+    energy_kernel(Gauge<R, NC> U, Mom<R> P, Geom g, EnergyAcc<R> beta6, EnergyAcc<R> beta3, int mode,
+                  EnergyAcc<R>* __restrict__ h0, double* __restrict__ partial,
+                  const EnergyAcc<R>* __restrict__ sg_in, EnergyAcc<R>* __restrict__ sg_out) {
   using A = EnergyAcc<R>;
   int s;
   A v[3] = {A(0), A(0), A(0)};  // S_G, T, dh

@@ -312,6 +312,15 @@ __device__ __forceinline__ void site_energy(const Gauge<R, NC>& U, const Mom<R>&
   } else {
     int c[4], par;
     cb_coords(g, s, c, par);
+    // x + mu as a half-index step from s (see staple_sum)
+    const int other = s + (par ? -g.Vh : g.Vh);
+    int dp[4];
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+      int dm;
+      cb_half_steps(g, c, mu, dp[mu], dm);
+      (void)dm;
+    }
     DF trdf(0.0f);
     double tr64 = 0.0;
 #pragma unroll
@@ -319,8 +328,8 @@ __device__ __forceinline__ void site_energy(const Gauge<R, NC>& U, const Mom<R>&
       const M3<R> umu = U.load(mu, s);
 #pragma unroll
       for (int nu = mu + 1; nu < 4; ++nu) {
-        const M3<R> a = mul(umu, U.load(nu, cb_neighbor(g, c, mu, +1)));
-        const M3<R> b = mul(U.load(nu, s), U.load(mu, cb_neighbor(g, c, nu, +1)));
+        const M3<R> a = mul(umu, U.load(nu, other + dp[mu]));
+        const M3<R> b = mul(U.load(nu, s), U.load(mu, other + dp[nu]));
         if constexpr (kDF) trdf = trdf + DF(float(re_tr_mul_nd(a, b)));
         else tr64 += double(re_tr_mul_nd(a, b));
       }
