@@ -71,3 +71,27 @@ def test_reference_arm_only_runs_on_rank_zero(monkeypatch, capsys):
         steps, warmup, lattice, integrator, dt, gpus, link_reals, precision = 1, 0, 32, "fg", 0.25, 2, 18, "fp32"
     assert bench.run_reference(A()) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_prints_the_contract_line(monkeypatch, capsys):
+    """Rank 0 of the reference arm prints one JSON line with the keys the
+    driver reads (the oracle's trajectory timing is stubbed: the line's
+    structure is what is tested here)."""
+    import json
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    monkeypatch.setattr(bench, "oracle_trajectory_rate",
+                        lambda sample_l, target_l, integ, dt, seed: (0.004, 250.0, "stub sample"))
+
+    class A:
+        steps, warmup, lattice, integrator, dt, gpus, link_reals, precision = 2, 1, 32, "fg", 0.25, 1, 18, "fp32"
+    assert bench.run_reference(A()) == 0
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["value"] == pytest.approx(0.004) and d["higher_is_better"] is True
+    assert d["steps"] == 2 and d["warmup"] == 1 and d["n_gpus"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["config"]["workload"]
