@@ -103,11 +103,22 @@ typedef enum {
  * every reliable update (the solution increment stays FP32, arithmetic is
  * FP32).  The reliable updates, on the FP32 links in double-float and FP64,
  * correct the ~5e-4 relative error of the inner operator; they come at least
- * every factor 0.1 of residual reduction, whatever cg_delta says. */
+ * every factor 0.1 of residual reduction, whatever cg_delta says.
+ * FG_DF64 ("double-float") stores every real of the links and momenta as an
+ * unevaluated sum hi + lo of two floats (about 48 significant bits, the same
+ * 8 bytes as FP64) and computes the staples, force, kicks, exponential and
+ * action sums in double-float arithmetic on the FP32 pipes (error-free FMA
+ * products and two-sums), with no FP64 instruction in the MD step: on a
+ * GB300 the FP64 unit runs at 1/64 of the FP32 rate.  It serves the dH of
+ * a trajectory (section 5, Fig. 1), whose error against FP64 arithmetic
+ * grows with the rounding of every MD operation: ~2^-47 relative here, 2^-24
+ * with FP32 fields.  Momentum refreshes draw FP32 Gaussians (exact as
+ * double-floats).  Pure gauge only: kappa must be 0. */
 typedef enum {
   FG_FP64 = 0,
   FG_FP32 = 1,
-  FG_FP32_FP16CG = 2
+  FG_FP32_FP16CG = 2,
+  FG_DF64 = 3
 } fg_precision;
 
 typedef struct {
@@ -115,10 +126,10 @@ typedef struct {
   double beta;             /* gauge coupling */
   double kappa;            /* hopping parameter; 0 => pure gauge (no fermions) */
   double alpha;            /* PQPQP parameter for FG_OMELYAN (default 0.1932) */
-  int precision;           /* fg_precision (default FG_FP64) */
+  int precision;           /* fg_precision (default FG_FP64); FG_DF64 needs kappa == 0 */
   int link_reals;          /* 18 (full) or 12 (two rows + reconstruction); default 18 */
   int reunitarize;         /* 1: re-project links onto SU(3) after every drift;
-                              default 0 for FG_FP64, 1 for FG_FP32 */
+                              default 0 for FG_FP64 and FG_DF64, 1 for FG_FP32 */
   double cg_tol;           /* relative residual |phi - M x| / |phi| for force solves (1e-10) */
   double cg_tol_action;    /* the same for the action solve at trajectory end (1e-12) */
   int cg_maxiter;          /* CG iteration cap (default 20000) */
@@ -310,9 +321,9 @@ typedef struct {
   int nchains;             /* number of chains, >= 1 */
   const int *dims;         /* nchains x 4 extents (Lx, Ly, Lz, Lt; even, >= 2; volume <= 2^28); copied */
   const double *beta;      /* nchains couplings; copied */
-  int precision;           /* FG_FP32 (default) or FG_FP64 */
+  int precision;           /* FG_FP32 (default), FG_FP64 or FG_DF64 */
   int link_reals;          /* 18 or 12 */
-  int reunitarize;         /* -1: after every drift for FP32, never for FP64 */
+  int reunitarize;         /* -1: after every drift for FP32, never for FP64 and FG_DF64 */
   double alpha;            /* PQPQP parameter for FG_OMELYAN (0.1932) */
   int tile;                /* half-sites per block: 16, 32 or 64; 0 = time all three on the
                               first trajectory and keep the fastest (autotuning) */

@@ -11,6 +11,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <utility>
 #include <vector>
 
@@ -172,33 +173,49 @@ class Backend final : public IBackend {
 
   // ---------------------------------------------------------------- fermions (ABI)
   fg_status set_pseudofermion(const double* chi) override {
-    fg_status s = upload_spinor(chi, chi64_);
-    if (s != FG_OK) return s;
-    if ((s = heatbath_from_chi()) != FG_OK) return s;
-    return sync();
+    if constexpr (!kFerm) {
+      return no_fermions();
+    } else {
+      fg_status s = upload_spinor(chi, chi64_);
+      if (s != FG_OK) return s;
+      if ((s = heatbath_from_chi()) != FG_OK) return s;
+      return sync();
+    }
   }
   fg_status refresh_pseudofermion() override {
-    const uint32_t d = pf_draw_++;
-    fg_status s = run(KC_MOMENTA, [&] { return launch_gaussian_spinor<double>(chi64_, g_.Vh, h_->prm.seed, d, st_); });
-    if (s != FG_OK) return s;
-    return heatbath_from_chi();
+    if constexpr (!kFerm) {
+      return no_fermions();
+    } else {
+      const uint32_t d = pf_draw_++;
+      fg_status s = run(KC_MOMENTA, [&] { return launch_gaussian_spinor<double>(chi64_, g_.Vh, h_->prm.seed, d, st_); });
+      if (s != FG_OK) return s;
+      return heatbath_from_chi();
+    }
   }
   fg_status apply_mhat(const double* in, double* out, int dagger) override {
-    fg_status s = upload_spinor(in, b64_);
-    if (s != FG_OK) return s;
-    if ((s = apply_mhat64(ax64_, b64_, U_, dagger)) != FG_OK) return s;
-    return download_spinor(ax64_, out);
+    if constexpr (!kFerm) {
+      return no_fermions();
+    } else {
+      fg_status s = upload_spinor(in, b64_);
+      if (s != FG_OK) return s;
+      if ((s = apply_mhat64(ax64_, b64_, U_, dagger)) != FG_OK) return s;
+      return download_spinor(ax64_, out);
+    }
   }
   fg_status cg_solve(const double* b, double* x, fg_cg_result* r) override {
-    fg_status s = upload_spinor(b, b64_);
-    if (s != FG_OK) return s;
-    CgStats cs;
-    s = cg(U_, b64_, h_->prm.cg_tol, &cs);
-    r->iterations = cs.iters;
-    r->reliable_updates = cs.nru;
-    r->true_residual = cs.true_res;
-    if (s != FG_OK) return s;
-    return download_spinor(x64_, x);
+    if constexpr (!kFerm) {
+      return no_fermions();
+    } else {
+      fg_status s = upload_spinor(b, b64_);
+      if (s != FG_OK) return s;
+      CgStats cs;
+      s = cg(U_, b64_, h_->prm.cg_tol, &cs);
+      r->iterations = cs.iters;
+      r->reliable_updates = cs.nru;
+      r->true_residual = cs.true_res;
+      if (s != FG_OK) return s;
+      return download_spinor(x64_, x);
+    }
   }
 
   // ---------------------------------------------------------------- observables
@@ -389,6 +406,10 @@ class Backend final : public IBackend {
   // (its Dslash temporaries reuse ax64_, te64_, to64_, which have the same size)
   void *xdf_ = nullptr, *bdf_ = nullptr;
   static constexpr bool kMixed = sizeof(R) < sizeof(double);
+  // Double-float handles are pure gauge (fg_lattice_create rejects kappa > 0):
+  // their fermion entry points are not compiled.
+  static constexpr bool kFerm = !std::is_same<R, DF>::value;
+  fg_status no_fermions() { return h_->fail(FG_ESTATE, "fermions need FG_FP64, FG_FP32 or FG_FP32_FP16CG"); }
   // inner CG Dslash on a half-precision copy of the links (FG_FP32_FP16CG)
   void* U16_ = nullptr;
   const bool half_links_ = kMixed && h_->prm.precision == FG_FP32_FP16CG;
@@ -540,54 +561,58 @@ class Backend final : public IBackend {
   // Y~ = (Y_e, Y_o) move with it and with the links, and the force's
   // bilinear form is differentiated in each argument in turn.
   fg_status fermion_force_tangent(const void* U, double tol) {
-    const int n = nvec();
-    const double k2 = h_->prm.kappa * h_->prm.kappa;
-    fg_status s;
-    auto ds = [&](void* out, const void* in, const void* x, const void* links, bool tangent, int out_par, int dag,
-                  int mode, double b) {
-      return run(KC_DSLASH, [&] {
-        return tangent ? launch_dslash<R, 9, R>(g_, out, in, x, nullptr, links, out_par, dag, mode, b, nullptr,
-                                                nullptr, st_)
-                       : launch_dslash<R, NC, R>(g_, out, in, x, nullptr, links, out_par, dag, mode, b, nullptr,
-                                                 nullptr, st_);
-      });
-    };
-    auto lc = [&](auto launch) { return run(KC_CG_BLAS, launch); };
-    // dMhat X_e = -k2 (dD_eo X_o + D_eo dD_oe X_e)
-    if ((s = ds(To1_, Xe_, nullptr, dU_, true, 1, 0, 0, 1.0)) != FG_OK) return s;
-    if ((s = ds(Te1_, Xo_, nullptr, dU_, true, 0, 0, 0, -k2)) != FG_OK) return s;
-    if ((s = ds(dYe_, To1_, Te1_, U, false, 0, 0, 1, -k2)) != FG_OK) return s;
-    // dMhat^dag Y_e = -k2 (dD^dag_eo Y_o + D^dag_eo dD^dag_oe Y_e); dD^dag_oe Y_e kept in dYo_
-    if ((s = ds(dYo_, Ye_, nullptr, dU_, true, 1, 1, 0, 1.0)) != FG_OK) return s;
-    if ((s = ds(Te1_, Yo_, nullptr, dU_, true, 0, 1, 0, -k2)) != FG_OK) return s;
-    if ((s = ds(Te2_, dYo_, Te1_, U, false, 0, 1, 1, -k2)) != FG_OK) return s;
-    // Mhat^dag (dMhat X_e)
-    if ((s = ds(To2_, dYe_, nullptr, U, false, 1, 1, 0, 1.0)) != FG_OK) return s;
-    if ((s = ds(Te1_, To2_, dYe_, U, false, 0, 1, 1, -k2)) != FG_OK) return s;
-    // F(calM) X = dMhat^dag Y_e + Mhat^dag dMhat X_e, in FP64, and the solve
-    if ((s = lc([&] { return launch_lincomb<double, R, R>(b64_, 1.0, Te1_, 1.0, Te2_, n, st_); })) != FG_OK) return s;
-    CgStats cs;
-    if ((s = cg(U, b64_, tol, &cs)) != FG_OK) return s;
-    // dX_e = -calM^{-1} F(calM) X; dX_o = dD_oe X_e + D_oe dX_e
-    if ((s = lc([&] { return launch_lincomb<R, double, double>(dXe_, -1.0, x64_, 0.0, nullptr, n, st_); })) != FG_OK)
-      return s;
-    if ((s = ds(To2_, dXe_, nullptr, U, false, 1, 0, 0, 1.0)) != FG_OK) return s;
-    if ((s = lc([&] { return launch_lincomb<R, R, R>(dXo_, 1.0, To1_, 1.0, To2_, n, st_); })) != FG_OK) return s;
-    // dY_e = dMhat X_e + Mhat dX_e; dY_o = dD^dag_oe Y_e + D^dag_oe dY_e
-    if ((s = ds(Te1_, To2_, dXe_, U, false, 0, 0, 1, -k2)) != FG_OK) return s;
-    if ((s = lc([&] { return launch_lincomb<R, R, R>(dYe_, 1.0, dYe_, 1.0, Te1_, n, st_); })) != FG_OK) return s;
-    if ((s = ds(dYo_, dYe_, dYo_, U, false, 1, 1, 1, 1.0)) != FG_OK) return s;
-    // the bilinear force form with the links, X~ and Y~ moved in turn
-    auto ff = [&](const void* links, bool tangent, const void* xe, const void* xo, const void* ye, const void* yo,
-                  int acc) {
-      return run(KC_FERMION_FORCE, [&] {
-        return tangent ? launch_fermion_force<R, 9, R>(g_, links, xe, xo, ye, yo, FFt_, k2, acc, st_)
-                       : launch_fermion_force<R, NC, R>(g_, links, xe, xo, ye, yo, FFt_, k2, acc, st_);
-      });
-    };
-    if ((s = ff(dU_, true, Xe_, Xo_, Ye_, Yo_, 0)) != FG_OK) return s;
-    if ((s = ff(U, false, dXe_, dXo_, Ye_, Yo_, 1)) != FG_OK) return s;
-    return ff(U, false, Xe_, Xo_, dYe_, dYo_, 1);
+    if constexpr (!kFerm) {
+      return no_fermions();
+    } else {
+      const int n = nvec();
+      const double k2 = h_->prm.kappa * h_->prm.kappa;
+      fg_status s;
+      auto ds = [&](void* out, const void* in, const void* x, const void* links, bool tangent, int out_par, int dag,
+                    int mode, double b) {
+        return run(KC_DSLASH, [&] {
+          return tangent ? launch_dslash<R, 9, R>(g_, out, in, x, nullptr, links, out_par, dag, mode, b, nullptr,
+                                                  nullptr, st_)
+                         : launch_dslash<R, NC, R>(g_, out, in, x, nullptr, links, out_par, dag, mode, b, nullptr,
+                                                   nullptr, st_);
+        });
+      };
+      auto lc = [&](auto launch) { return run(KC_CG_BLAS, launch); };
+      // dMhat X_e = -k2 (dD_eo X_o + D_eo dD_oe X_e)
+      if ((s = ds(To1_, Xe_, nullptr, dU_, true, 1, 0, 0, 1.0)) != FG_OK) return s;
+      if ((s = ds(Te1_, Xo_, nullptr, dU_, true, 0, 0, 0, -k2)) != FG_OK) return s;
+      if ((s = ds(dYe_, To1_, Te1_, U, false, 0, 0, 1, -k2)) != FG_OK) return s;
+      // dMhat^dag Y_e = -k2 (dD^dag_eo Y_o + D^dag_eo dD^dag_oe Y_e); dD^dag_oe Y_e kept in dYo_
+      if ((s = ds(dYo_, Ye_, nullptr, dU_, true, 1, 1, 0, 1.0)) != FG_OK) return s;
+      if ((s = ds(Te1_, Yo_, nullptr, dU_, true, 0, 1, 0, -k2)) != FG_OK) return s;
+      if ((s = ds(Te2_, dYo_, Te1_, U, false, 0, 1, 1, -k2)) != FG_OK) return s;
+      // Mhat^dag (dMhat X_e)
+      if ((s = ds(To2_, dYe_, nullptr, U, false, 1, 1, 0, 1.0)) != FG_OK) return s;
+      if ((s = ds(Te1_, To2_, dYe_, U, false, 0, 1, 1, -k2)) != FG_OK) return s;
+      // F(calM) X = dMhat^dag Y_e + Mhat^dag dMhat X_e, in FP64, and the solve
+      if ((s = lc([&] { return launch_lincomb<double, R, R>(b64_, 1.0, Te1_, 1.0, Te2_, n, st_); })) != FG_OK) return s;
+      CgStats cs;
+      if ((s = cg(U, b64_, tol, &cs)) != FG_OK) return s;
+      // dX_e = -calM^{-1} F(calM) X; dX_o = dD_oe X_e + D_oe dX_e
+      if ((s = lc([&] { return launch_lincomb<R, double, double>(dXe_, -1.0, x64_, 0.0, nullptr, n, st_); })) != FG_OK)
+        return s;
+      if ((s = ds(To2_, dXe_, nullptr, U, false, 1, 0, 0, 1.0)) != FG_OK) return s;
+      if ((s = lc([&] { return launch_lincomb<R, R, R>(dXo_, 1.0, To1_, 1.0, To2_, n, st_); })) != FG_OK) return s;
+      // dY_e = dMhat X_e + Mhat dX_e; dY_o = dD^dag_oe Y_e + D^dag_oe dY_e
+      if ((s = ds(Te1_, To2_, dXe_, U, false, 0, 0, 1, -k2)) != FG_OK) return s;
+      if ((s = lc([&] { return launch_lincomb<R, R, R>(dYe_, 1.0, dYe_, 1.0, Te1_, n, st_); })) != FG_OK) return s;
+      if ((s = ds(dYo_, dYe_, dYo_, U, false, 1, 1, 1, 1.0)) != FG_OK) return s;
+      // the bilinear force form with the links, X~ and Y~ moved in turn
+      auto ff = [&](const void* links, bool tangent, const void* xe, const void* xo, const void* ye, const void* yo,
+                    int acc) {
+        return run(KC_FERMION_FORCE, [&] {
+          return tangent ? launch_fermion_force<R, 9, R>(g_, links, xe, xo, ye, yo, FFt_, k2, acc, st_)
+                         : launch_fermion_force<R, NC, R>(g_, links, xe, xo, ye, yo, FFt_, k2, acc, st_);
+        });
+      };
+      if ((s = ff(dU_, true, Xe_, Xo_, Ye_, Yo_, 0)) != FG_OK) return s;
+      if ((s = ff(U, false, dXe_, dXo_, Ye_, Yo_, 1)) != FG_OK) return s;
+      return ff(U, false, Xe_, Xo_, dYe_, dYo_, 1);
+    }
   }
 
   // Closed-form force-gradient kick P -= c (F - shift G), G the derivative of
@@ -775,37 +800,41 @@ class Backend final : public IBackend {
 
   // ---------------------------------------------------------------- fermion internals
   fg_status init_fermions() {
-    const size_t n = (size_t)nvec();
-    const size_t b64 = n * sizeof(double2), bR = n * sizeof(C2);
-    fg_status s;
-    void** d64[] = {&chi64_, &phi64_, &b64_, &x64_, &r64_, &ax64_, &te64_, &to64_};
-    for (void** p : d64)
-      if ((s = alloc(p, b64)) != FG_OK) return s;
-    if (kMixed) {
-      if ((s = alloc(&xdf_, b64)) != FG_OK) return s;
-      if ((s = alloc(&bdf_, b64)) != FG_OK) return s;
+    if constexpr (!kFerm) {
+      return no_fermions();
+    } else {
+      const size_t n = (size_t)nvec();
+      const size_t b64 = n * sizeof(double2), bR = n * sizeof(C2);
+      fg_status s;
+      void** d64[] = {&chi64_, &phi64_, &b64_, &x64_, &r64_, &ax64_, &te64_, &to64_};
+      for (void** p : d64)
+        if ((s = alloc(p, b64)) != FG_OK) return s;
+      if (kMixed) {
+        if ((s = alloc(&xdf_, b64)) != FG_OK) return s;
+        if ((s = alloc(&bdf_, b64)) != FG_OK) return s;
+      }
+      // two bytes per real, NC complex entries per link
+      if (half_links_ && (s = alloc(&U16_, (size_t)4 * NC * g_.V * 4)) != FG_OK) return s;
+      void** dR[] = {&xs_, &rs_, &p_, &ap_, &te_, &to_, &Xe_, &Xo_, &Ye_, &Yo_};
+      for (void** p : dR)
+        if ((s = alloc(p, bR)) != FG_OK) return s;
+      if ((s = alloc(&FF_, (size_t)4 * 4 * g_.V * sizeof(C2))) != FG_OK) return s;
+      if ((s = alloc((void**)&cgd_, sizeof(CgDev))) != FG_OK) return s;
+      if (cudaMemsetAsync(cgd_, 0, sizeof(CgDev), st_) != cudaSuccess) return cuda_fail("cg state init");
+      if ((s = alloc((void**)&part_pap_, (dslash_blocks(g_.Vh) + 1) * sizeof(double))) != FG_OK) return s;
+      if ((s = alloc((void**)&part_rr_, (vec_blocks(nvec()) + 1) * sizeof(double))) != FG_OK) return s;
+      const size_t mbytes = sizeof(Mapped) + (size_t)(h_->prm.cg_maxiter + 8) * sizeof(double);
+      if (cudaHostAlloc((void**)&mapped_, mbytes, cudaHostAllocMapped) != cudaSuccess) {
+        mapped_ = nullptr;
+        return h_->fail(FG_ENOMEM, "mapped host allocation failed");
+      }
+      std::memset(mapped_, 0, mbytes);
+      for (int i = 0; i < 2; ++i)
+        if (cudaEventCreateWithFlags(&ev_[i], cudaEventDisableTiming) != cudaSuccess) return cuda_fail("event");
+      if (cudaMemsetAsync(chi64_, 0, b64, st_) != cudaSuccess || cudaMemsetAsync(phi64_, 0, b64, st_) != cudaSuccess)
+        return cuda_fail("memset");
+      return FG_OK;
     }
-    // two bytes per real, NC complex entries per link
-    if (half_links_ && (s = alloc(&U16_, (size_t)4 * NC * g_.V * 4)) != FG_OK) return s;
-    void** dR[] = {&xs_, &rs_, &p_, &ap_, &te_, &to_, &Xe_, &Xo_, &Ye_, &Yo_};
-    for (void** p : dR)
-      if ((s = alloc(p, bR)) != FG_OK) return s;
-    if ((s = alloc(&FF_, (size_t)4 * 4 * g_.V * sizeof(C2))) != FG_OK) return s;
-    if ((s = alloc((void**)&cgd_, sizeof(CgDev))) != FG_OK) return s;
-    if (cudaMemsetAsync(cgd_, 0, sizeof(CgDev), st_) != cudaSuccess) return cuda_fail("cg state init");
-    if ((s = alloc((void**)&part_pap_, (dslash_blocks(g_.Vh) + 1) * sizeof(double))) != FG_OK) return s;
-    if ((s = alloc((void**)&part_rr_, (vec_blocks(nvec()) + 1) * sizeof(double))) != FG_OK) return s;
-    const size_t mbytes = sizeof(Mapped) + (size_t)(h_->prm.cg_maxiter + 8) * sizeof(double);
-    if (cudaHostAlloc((void**)&mapped_, mbytes, cudaHostAllocMapped) != cudaSuccess) {
-      mapped_ = nullptr;
-      return h_->fail(FG_ENOMEM, "mapped host allocation failed");
-    }
-    std::memset(mapped_, 0, mbytes);
-    for (int i = 0; i < 2; ++i)
-      if (cudaEventCreateWithFlags(&ev_[i], cudaEventDisableTiming) != cudaSuccess) return cuda_fail("event");
-    if (cudaMemsetAsync(chi64_, 0, b64, st_) != cudaSuccess || cudaMemsetAsync(phi64_, 0, b64, st_) != cudaSuccess)
-      return cuda_fail("memset");
-    return FG_OK;
   }
 
   fg_status upload_spinor(const double* host, void* dst64) {
@@ -882,40 +911,48 @@ class Backend final : public IBackend {
 
   // S_F = phi^dagger (Mhat^dagger Mhat)^{-1} phi at links U (section 4's action).
   fg_status fermion_action(const void* U, double* sf) {
-    CgStats cs;
-    fg_status s = cg(U, phi64_, h_->prm.cg_tol_action, &cs);
-    if (s != FG_OK) return s;
-    if ((s = run(KC_CG_BLAS, [&] { return launch_dot64(phi64_, x64_, part_rr_, nvec(), st_); })) != FG_OK) return s;
-    const int nb = vec_blocks(nvec());
-    if ((s = run(KC_REDUCE, [&] { return launch_reduce(part_rr_, nb, 1, dout_ + 9, 0, st_); })) != FG_OK) return s;
-    if (cudaMemcpyAsync(host_out_ + 9, dout_ + 9, sizeof(double), cudaMemcpyDeviceToHost, st_) != cudaSuccess)
-      return cuda_fail("download");
-    if ((s = sync()) != FG_OK) return s;
-    *sf = host_out_[9];
-    return FG_OK;
+    if constexpr (!kFerm) {
+      return no_fermions();
+    } else {
+      CgStats cs;
+      fg_status s = cg(U, phi64_, h_->prm.cg_tol_action, &cs);
+      if (s != FG_OK) return s;
+      if ((s = run(KC_CG_BLAS, [&] { return launch_dot64(phi64_, x64_, part_rr_, nvec(), st_); })) != FG_OK) return s;
+      const int nb = vec_blocks(nvec());
+      if ((s = run(KC_REDUCE, [&] { return launch_reduce(part_rr_, nb, 1, dout_ + 9, 0, st_); })) != FG_OK) return s;
+      if (cudaMemcpyAsync(host_out_ + 9, dout_ + 9, sizeof(double), cudaMemcpyDeviceToHost, st_) != cudaSuccess)
+        return cuda_fail("download");
+      if ((s = sync()) != FG_OK) return s;
+      *sf = host_out_[9];
+      return FG_OK;
+    }
   }
 
   // Pseudofermion force at links U into FF_ (section 4: e_i(S) = -X^dagger e_i(M) X).
   fg_status fermion_force(const void* U, double tol) {
-    CgStats cs;
-    fg_status s = cg(U, phi64_, tol, &cs);
-    if (s != FG_OK) return s;
-    const int n = nvec();
-    const double k2 = h_->prm.kappa * h_->prm.kappa;
-    if ((s = run(KC_CG_BLAS, [&] { return launch_convert<R, double>(Xe_, x64_, nullptr, n, st_); })) != FG_OK) return s;
-    // X_o = D_oe X_e; Y_e = X_e - kappa^2 D_eo X_o; Y_o = g5 D_oe g5 Y_e
-    if ((s = run(KC_DSLASH, [&] {
-           return launch_dslash<R, NC, R>(g_, Xo_, Xe_, nullptr, nullptr, U, 1, 0, 0, 1.0, nullptr, nullptr, st_);
-         })) != FG_OK) return s;
-    if ((s = run(KC_DSLASH, [&] {
-           return launch_dslash<R, NC, R>(g_, Ye_, Xo_, Xe_, nullptr, U, 0, 0, 1, -k2, nullptr, nullptr, st_);
-         })) != FG_OK) return s;
-    if ((s = run(KC_DSLASH, [&] {
-           return launch_dslash<R, NC, R>(g_, Yo_, Ye_, nullptr, nullptr, U, 1, 1, 0, 1.0, nullptr, nullptr, st_);
-         })) != FG_OK) return s;
-    return run(KC_FERMION_FORCE, [&] {
-      return launch_fermion_force<R, NC, R>(g_, U, Xe_, Xo_, Ye_, Yo_, FF_, k2, 0, st_);
-    });
+    if constexpr (!kFerm) {
+      return no_fermions();
+    } else {
+      CgStats cs;
+      fg_status s = cg(U, phi64_, tol, &cs);
+      if (s != FG_OK) return s;
+      const int n = nvec();
+      const double k2 = h_->prm.kappa * h_->prm.kappa;
+      if ((s = run(KC_CG_BLAS, [&] { return launch_convert<R, double>(Xe_, x64_, nullptr, n, st_); })) != FG_OK) return s;
+      // X_o = D_oe X_e; Y_e = X_e - kappa^2 D_eo X_o; Y_o = g5 D_oe g5 Y_e
+      if ((s = run(KC_DSLASH, [&] {
+             return launch_dslash<R, NC, R>(g_, Xo_, Xe_, nullptr, nullptr, U, 1, 0, 0, 1.0, nullptr, nullptr, st_);
+           })) != FG_OK) return s;
+      if ((s = run(KC_DSLASH, [&] {
+             return launch_dslash<R, NC, R>(g_, Ye_, Xo_, Xe_, nullptr, U, 0, 0, 1, -k2, nullptr, nullptr, st_);
+           })) != FG_OK) return s;
+      if ((s = run(KC_DSLASH, [&] {
+             return launch_dslash<R, NC, R>(g_, Yo_, Ye_, nullptr, nullptr, U, 1, 1, 0, 1.0, nullptr, nullptr, st_);
+           })) != FG_OK) return s;
+      return run(KC_FERMION_FORCE, [&] {
+        return launch_fermion_force<R, NC, R>(g_, U, Xe_, Xo_, Ye_, Yo_, FF_, k2, 0, st_);
+      });
+    }
   }
 
   // Dslash of the inner iterations: on the FP32 links, or with
@@ -1301,6 +1338,16 @@ fg_status lattice_init(fg_lattice* h) {
     s = b->init();
   } else if (p.precision == FG_FP64) {
     auto* b = new (std::nothrow) Backend<double, 6>(h);
+    if (!b) return FG_ENOMEM;
+    h->be.reset(b);
+    s = b->init();
+  } else if (p.precision == FG_DF64 && p.link_reals == 18) {
+    auto* b = new (std::nothrow) Backend<DF, 9>(h);
+    if (!b) return FG_ENOMEM;
+    h->be.reset(b);
+    s = b->init();
+  } else if (p.precision == FG_DF64) {
+    auto* b = new (std::nothrow) Backend<DF, 6>(h);
     if (!b) return FG_ENOMEM;
     h->be.reset(b);
     s = b->init();

@@ -23,6 +23,7 @@
 #include <memory>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/fg_lattice.h"
@@ -63,9 +64,13 @@ template <int H> struct TileBounds;
 template <> struct TileBounds<16> { static constexpr int min_blocks = 4; };
 template <> struct TileBounds<32> { static constexpr int min_blocks = 2; };
 template <> struct TileBounds<64> { static constexpr int min_blocks = 1; };
+// Register cap of the force kernel: 128 per thread for FP32 and FP64 links;
+// double-float links get up to 255 (as in the single-lattice kernel).
+template <typename R, int H>
+constexpr int kBatchMinBlocks = std::is_same<R, DF>::value ? (H == 16 ? 2 : 1) : TileBounds<H>::min_blocks;
 
 template <typename R, int NC, int MODE, int H>
-__global__ void __launch_bounds__(8 * H, TileBounds<H>::min_blocks)
+__global__ void __launch_bounds__(8 * H, (kBatchMinBlocks<R, H>))
     batch_force_kernel(const Tile* __restrict__ tiles, int ntiles, const ChainDesc* __restrict__ chains,
                        char* U, char* P, char* F, char* Ubase, char* Uout, double ckick, double cdrift, double cdisp,
                        int reunit) {
@@ -304,6 +309,10 @@ template <typename R, int NC>
 class Batch final : public IBatch {
  public:
   typedef typename Vec2<R>::T C2;
+  // Tile sizes compiled for this precision: 16, 32 and 64 half-sites, or 16
+  // and 32 for double-float links (their force kernel is several times the
+  // size of the FP32 one; fg_batch_create rejects tile 64 for them).
+  static constexpr int kTileSizes = std::is_same<R, DF>::value ? 2 : 3;
   explicit Batch(fg_batch* b) : b_(b), st_(b->st) {}
   ~Batch() override {
     for (auto& g : graphs_) cudaGraphExecDestroy(g.exec);
@@ -314,7 +323,7 @@ class Batch final : public IBatch {
   fg_status init() {
     // 64-half-site tiles of the FP32 force kernel use more than the default
     // 48 KB of dynamic shared memory
-    if (batch_force_smem<R, NC, 64>() > 48 * 1024) {
+    if constexpr (batch_force_smem<R, NC, 64>() > 48 * 1024) {
       const int bytes = (int)batch_force_smem<R, NC, 64>();
       if (cudaFuncSetAttribute(batch_force_kernel<R, NC, FM_STORE, 64>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess ||
@@ -599,7 +608,7 @@ class Batch final : public IBatch {
                     double cdisp) {
     const int nt = ntiles_[hi];
     const dim3 blk(2 * H, 4);
-    const int gr = grid(nt, TileBounds<H>::min_blocks);
+    const int gr = grid(nt, kBatchMinBlocks<R, H>);
     const int reunit = b_->prm.reunitarize;
     char* Pp = (char*)P_;
     return lrun([&] {
@@ -634,7 +643,9 @@ class Batch final : public IBatch {
   fg_status force(int mode, void* U, void* Ubase, void* Uout, double ckick, double cdrift, double cdisp) {
     switch (hsel_) {
       case 0: return force_h<16>(0, mode, U, Ubase, Uout, F_, ckick, cdrift, cdisp);
-      case 2: return force_h<64>(2, mode, U, Ubase, Uout, F_, ckick, cdrift, cdisp);
+      case 2:
+        if constexpr (kTileSizes > 2) return force_h<64>(2, mode, U, Ubase, Uout, F_, ckick, cdrift, cdisp);
+        [[fallthrough]];
       default: return force_h<32>(1, mode, U, Ubase, Uout, F_, ckick, cdrift, cdisp);
     }
   }
@@ -652,7 +663,9 @@ class Batch final : public IBatch {
   fg_status drift(void* Uin, void* Uout, double c) {
     switch (hsel_) {
       case 0: return drift_h<16>(0, Uin, Uout, c);
-      case 2: return drift_h<64>(2, Uin, Uout, c);
+      case 2:
+        if constexpr (kTileSizes > 2) return drift_h<64>(2, Uin, Uout, c);
+        [[fallthrough]];
       default: return drift_h<32>(1, Uin, Uout, c);
     }
   }
@@ -694,7 +707,9 @@ class Batch final : public IBatch {
                  void* Ustart = nullptr, void* Ucur = nullptr, int off = 0) {
     switch (hsel_) {
       case 0: return misc_h<16>(0, what, U, mode, refreshed, accept_mode, Ustart, Ucur, off);
-      case 2: return misc_h<64>(2, what, U, mode, refreshed, accept_mode, Ustart, Ucur, off);
+      case 2:
+        if constexpr (kTileSizes > 2) return misc_h<64>(2, what, U, mode, refreshed, accept_mode, Ustart, Ucur, off);
+        [[fallthrough]];
       default: return misc_h<32>(1, what, U, mode, refreshed, accept_mode, Ustart, Ucur, off);
     }
   }
@@ -771,7 +786,7 @@ class Batch final : public IBatch {
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return cuda_fail("event");
     float best = 1e30f;
     int best_h = 1;
-    for (int hi = 0; hi < 3; ++hi) {
+    for (int hi = 0; hi < kTileSizes; ++hi) {
       hsel_ = hi;
       float tmin = 1e30f;
       for (int rep = 0; rep < 4; ++rep) {
@@ -821,9 +836,11 @@ fg_status fg_batch_create(const fg_batch_params* p, fg_batch** out) {
   if (!out) return FG_EINVAL;
   *out = nullptr;
   if (!p || p->nchains < 1 || !p->dims || !p->beta) return FG_EINVAL;
-  if (p->precision != FG_FP64 && p->precision != FG_FP32) return FG_EINVAL;
+  if (p->precision != FG_FP64 && p->precision != FG_FP32 && p->precision != FG_DF64) return FG_EINVAL;
   if (p->link_reals != 18 && p->link_reals != 12) return FG_EINVAL;
   if (p->tile != 0 && p->tile != 16 && p->tile != 32 && p->tile != 64) return FG_EINVAL;
+  // double-float chains: 18-real links and tiles of 16 or 32 half-sites
+  if (p->precision == FG_DF64 && (p->link_reals != 18 || p->tile == 64)) return FG_EINVAL;
   long long total = 0;
   for (int c = 0; c < p->nchains; ++c) {
     long long V = 1;
@@ -868,6 +885,10 @@ fg_status fg_batch_create(const fg_batch_params* p, fg_batch** out) {
     s = x ? x->init() : FG_ENOMEM;
   } else if (p->precision == FG_FP64) {
     auto* x = new (std::nothrow) Batch<double, 6>(b);
+    b->impl.reset(x);
+    s = x ? x->init() : FG_ENOMEM;
+  } else if (p->precision == FG_DF64) {
+    auto* x = new (std::nothrow) Batch<DF, 9>(b);
     b->impl.reset(x);
     s = x ? x->init() : FG_ENOMEM;
   } else if (p->link_reals == 18) {

@@ -25,14 +25,13 @@ namespace fg {
 struct DF {
   float hi, lo;
   DF() = default;
-  __host__ __device__ __forceinline__ DF(float h) : hi(h), lo(0.0f) {}
-  __host__ __device__ __forceinline__ DF(int h) : hi((float)h), lo(0.0f) {}
-  // Nearest double-float to a double (host or device; uses FP64 arithmetic).
-  __host__ __device__ __forceinline__ explicit DF(double d) {
-    hi = (float)d;
-    lo = (float)(d - (double)hi);
-  }
-  __host__ __device__ __forceinline__ DF(float h, float l) : hi(h), lo(l) {}
+  __host__ __device__ __forceinline__ constexpr DF(float h) : hi(h), lo(0.0f) {}
+  __host__ __device__ __forceinline__ constexpr DF(int h) : hi((float)h), lo(0.0f) {}
+  // Nearest double-float to a double (host or device; FP64 arithmetic, which
+  // the compiler folds away for a literal argument).
+  __host__ __device__ __forceinline__ constexpr explicit DF(double d)
+      : hi((float)d), lo((float)(d - (double)(float)d)) {}
+  __host__ __device__ __forceinline__ constexpr DF(float h, float l) : hi(h), lo(l) {}
   __host__ __device__ __forceinline__ explicit operator double() const { return (double)hi + (double)lo; }
 };
 
@@ -62,10 +61,14 @@ __device__ __forceinline__ DF operator*(DF a, DF b) {
   e = __fmaf_rn(a.lo, b.hi, e);
   return df_fast_two_sum(p, e);
 }
-// a * b + c with one normalisation.  The generic complex helpers call fma
-// unqualified; the using-declaration keeps the float and double overloads
-// visible next to this one.
+// a * b + c with one normalisation.  Generic code calls fma, sqrt, fabs and
+// sincos unqualified; the using-declarations keep the float and double
+// overloads visible next to the double-float ones declared here (otherwise
+// those would hide them, and a float argument would convert to DF).
 using ::fma;
+using ::sqrt;
+using ::fabs;
+using ::sincos;
 __device__ __forceinline__ DF fma(DF a, DF b, DF c) {
   const float p = __fmul_rn(a.hi, b.hi);
   float e = __fmaf_rn(a.hi, b.hi, -p);
@@ -80,12 +83,80 @@ __device__ __forceinline__ DF df_add_f(DF a, float f) {
   const DF s = df_two_sum(a.hi, f);
   return df_fast_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
 }
+__device__ __forceinline__ DF& operator-=(DF& a, DF b) { return a = a - b; }
+__device__ __forceinline__ DF& operator*=(DF& a, DF b) { return a = a * b; }
+// a * f for a float f
+__device__ __forceinline__ DF operator*(DF a, float f) {
+  const float p = __fmul_rn(a.hi, f);
+  float e = __fmaf_rn(a.hi, f, -p);
+  e = __fmaf_rn(a.lo, f, e);
+  return df_fast_two_sum(p, e);
+}
+// Quotient by one correction step: q1 = a.hi / b.hi, then the remainder
+// a - q1 b in double-float divided by b.hi gives the low part (~2^-47 relative).
+__device__ __forceinline__ DF operator/(DF a, DF b) {
+  const float q1 = __fdiv_rn(a.hi, b.hi);
+  const DF r = a - b * q1;
+  return df_fast_two_sum(q1, __fdiv_rn(r.hi, b.hi));
+}
+// Ordering of normalised double-floats (|lo| <= ulp(hi) / 2).
+__device__ __forceinline__ bool operator<(DF a, DF b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+__device__ __forceinline__ bool operator>(DF a, DF b) { return b < a; }
+__device__ __forceinline__ DF fabs(DF a) { return (a.hi < 0.0f || (a.hi == 0.0f && a.lo < 0.0f)) ? -a : a; }
+// Square root: s = sqrt(a.hi) in FP32, then one Newton step on s^2 = a with
+// the residual a - s^2 formed exactly (s^2 = p + e by the FMA product, and
+// a.hi - p is exact by Sterbenz's lemma).
+__device__ __forceinline__ DF sqrt(DF a) {
+  if (!(a.hi > 0.0f)) return DF(0.0f);
+  const float s = __fsqrt_rn(a.hi);
+  const float p = __fmul_rn(s, s);
+  const float e = __fmaf_rn(s, s, -p);
+  const float d = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, p), e), a.lo);
+  return df_fast_two_sum(s, __fdiv_rn(d, __fadd_rn(s, s)));
+}
+
+// sin and cos of a double-float argument from the Taylor series on x / 2^k,
+// |x / 2^k| <= 1/8, and k double-angle steps (sin 2y = 2 sin y cos y,
+// cos 2y = 1 - 2 sin^2 y).  The series stop at y^9 and y^8: the first
+// omitted terms are below 3e-16 of the result.  Each doubling at most doubles
+// the absolute error, so |x| <= 4 (k <= 5) keeps it near 1e-14; arguments
+// here are rotation angles of link updates, usually well below 1.
+__device__ __forceinline__ void sincos(DF x, DF* s, DF* c) {
+  // k = max(0, e + 3) with |x.hi| = m 2^e, m in [0.5, 1)
+  const int e = (int)((__float_as_uint(x.hi) >> 23) & 0xffu) - 126;
+  const int k = e + 3 > 0 ? (e + 3 < 60 ? e + 3 : 60) : 0;
+  const float sc = __uint_as_float((uint32_t)(127 - k) << 23);  // 2^-k, exact scaling
+  const DF y(__fmul_rn(x.hi, sc), __fmul_rn(x.lo, sc));
+  const DF z = y * y;
+  constexpr DF s3(-1.0 / 6.0), s5(1.0 / 120.0), s7(-1.0 / 5040.0), s9(1.0 / 362880.0);
+  constexpr DF c4(1.0 / 24.0), c6(-1.0 / 720.0), c8(1.0 / 40320.0);
+  DF ps = fma(z, s9, s7);
+  ps = fma(z, ps, s5);
+  ps = fma(z, ps, s3);
+  DF sn = fma(y * z, ps, y);
+  DF pc = fma(z, c8, c6);
+  pc = fma(z, pc, c4);
+  DF cs = fma(z * z, pc, DF(1.0f) - z * 0.5f);
+  for (int i = 0; i < k; ++i) {
+    const DF s2 = sn * sn;
+    sn = (sn * cs) * 2.0f;
+    cs = DF(1.0f) - s2 * 2.0f;
+  }
+  *s = sn;
+  *c = cs;
+}
 
 // Storage: one complex double-float is a float4 (re.hi, re.lo, im.hi, im.lo),
 // the same 16 bytes as a complex double; a pair of entries is two float4.
 template <> struct Vec2<DF> { typedef float4 T; };
 template <> struct Quad<DF> {
   static __device__ __forceinline__ Cx<DF> c(float4 v) { return cx<DF>(DF(v.x, v.y), DF(v.z, v.w)); }
+  static __device__ __forceinline__ Cx<DF> load1(const void* base, size_t idx) {
+    return c(__ldg((const float4*)base + idx));
+  }
+  static __device__ __forceinline__ void store1(void* base, size_t idx, Cx<DF> a) {
+    ((float4*)base)[idx] = make_float4(a.re.hi, a.re.lo, a.im.hi, a.im.lo);
+  }
   static __device__ __forceinline__ void load(const void* base, size_t idx, Cx<DF>& a, Cx<DF>& b) {
     const float4* p = (const float4*)base + 2 * idx;
     a = c(__ldg(p));
@@ -132,5 +203,105 @@ __device__ __forceinline__ void block_reduce_store_df(DF v[NV], double* __restri
     }
   }
 }
+
+// exp(i A) for Hermitian traceless A in double-float: the closed form of
+// Morningstar and Peardon (Phys. Rev. D 69 (2004) 054501, section III),
+// exp(iA) = f0 + f1 A + f2 A^2, as in the generic expi_herm, with the
+// scalars computed to double-float accuracy on the FP32 pipes:
+//   * 2u, the largest eigenvalue of A for c0 = det A >= 0 (negative c0 is
+//     mapped through f_j(-c0) = (-1)^j conj(f_j(c0))), is a simple root of the
+//     characteristic polynomial lambda^3 - c1 lambda - c0 separated from the
+//     others by at least sqrt(c1); it starts from the FP32 angle formula and
+//     takes two Newton steps in double-float (1e-7 -> 1e-14 -> rounding);
+//   * w^2 = c1 - 3 u^2 (the eigenvalues are 2u and -u +- w, and
+//     c1 = Tr A^2 / 2 = 3 u^2 + w^2), so cos w and sin(w)/w, the only
+//     functions of w that enter, are even in w and need no angle;
+//   * sin and cos by the double-float series above.
+// Below c1 = 1e-12 (|A| < 1.5e-6) the exponential series to A^4 is used, with
+// A^3 = c1 A + c0 and A^4 = c1 A^2 + c0 A (Cayley-Hamilton); the omitted
+// terms are below |A|^5 / 120 < 1e-31.
+template <>
+__device__ __forceinline__ M3<DF> expi_herm<DF>(const M3<DF>& a) {
+  const M3<DF> a2 = herm_sq(a);
+  const DF c1 = (a2.e[0][0].re + a2.e[1][1].re + a2.e[2][2].re) * 0.5f;
+  constexpr DF third(1.0 / 3.0), sixth(1.0 / 6.0), c24(1.0 / 24.0);
+  const DF c0 = re_tr_mul(a, a2) * third;
+  Cx<DF> f0, f1, f2;
+  if (c1.hi < 1e-12f) {
+    f0 = cx<DF>(DF(1.0f), -(c0 * sixth));
+    f1 = cx<DF>(c0 * c24, DF(1.0f) - c1 * sixth);
+    f2 = cx<DF>(DF(-0.5f) + c1 * c24, DF(0.0f));
+  } else {
+    const bool neg = c0.hi < 0.0f;
+    const DF c0a = neg ? -c0 : c0;
+    // FP32 seed: u = r cos(theta / 3), r = sqrt(c1 / 3), cos theta = c0 / (2 r^3)
+    const float r32 = sqrtf(c1.hi * (1.0f / 3.0f));
+    const float ratio = fminf(c0a.hi / (2.0f * r32 * r32 * r32), 1.0f);
+    DF lam(2.0f * r32 * cosf(acosf(ratio) * (1.0f / 3.0f)));
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+      const DF l2 = lam * lam;
+      const DF pv = (l2 - c1) * lam - c0a;
+      const DF dp = l2 * 3.0f - c1;
+      // the correction is ~1e-7 of lam or less: FP32 accuracy suffices
+      lam = lam - DF(__fdiv_rn(pv.hi, dp.hi));
+    }
+    const DF u = lam * 0.5f;
+    const DF u2 = u * u;
+    DF w2 = c1 - u2 * 3.0f;
+    if (w2.hi < 0.0f) w2 = DF(0.0f);
+    DF su, cu;
+    sincos(u, &su, &cu);
+    DF cw, xi0;
+    if (w2.hi < 0.0025f) {
+      // |w| < 0.05: cos w and sin(w)/w from their series in w^2 (first omitted
+      // terms below 1e-16)
+      constexpr DF k2(1.0 / 2.0), k4(1.0 / 24.0), k6(-1.0 / 720.0), k8(1.0 / 40320.0);
+      constexpr DF x2(-1.0 / 6.0), x4(1.0 / 120.0), x6(-1.0 / 5040.0), x8(1.0 / 362880.0);
+      DF t = fma(w2, k8, k6);
+      t = fma(w2, t, k4);
+      cw = fma(w2 * w2, t, DF(1.0f) - w2 * k2);
+      DF q = fma(w2, x8, x6);
+      q = fma(w2, q, x4);
+      q = fma(w2, q, x2);
+      xi0 = fma(w2, q, DF(1.0f));
+    } else {
+      const DF w = sqrt(w2);
+      DF sw;
+      sincos(w, &sw, &cw);
+      xi0 = sw / w;
+    }
+    const DF s2u = (su * cu) * 2.0f;
+    const DF c2u = (cu - su) * (cu + su);
+    const Cx<DF> e2 = cx<DF>(c2u, s2u);
+    const Cx<DF> em = cx<DF>(cu, -su);
+    const DF u2x3 = u2 * 3.0f;
+    const Cx<DF> h0 = cx<DF>(u2 - w2, DF(0.0f)) * e2 +
+                      em * cx<DF>(u2 * cw * 8.0f, (u * (u2x3 + w2) * xi0) * 2.0f);
+    const Cx<DF> h1 = cx<DF>(u * 2.0f, DF(0.0f)) * e2 - em * cx<DF>((u * cw) * 2.0f, -((u2x3 - w2) * xi0));
+    const Cx<DF> h2 = e2 - em * cx<DF>(cw, (u * xi0) * 3.0f);
+    const DF inv = DF(1.0f) / (u2 * 9.0f - w2);
+    f0 = inv * h0;
+    f1 = inv * h1;
+    f2 = inv * h2;
+    if (neg) {
+      f0 = conj(f0);
+      f1 = cx<DF>(-f1.re, f1.im);
+      f2 = conj(f2);
+    }
+  }
+  M3<DF> e;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      Cx<DF> s = f1 * a.e[i][j];
+      cmac(s, f2, a2.e[i][j]);
+      if (i == j) s = s + f0;
+      e.e[i][j] = s;
+    }
+  return e;
+}
+
 
 }  // namespace fg

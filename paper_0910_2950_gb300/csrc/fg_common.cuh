@@ -416,6 +416,14 @@ __device__ __forceinline__ bool pair_site(const Geom& g, int& s) {
 // combine fields element by element.
 template <typename R> struct Quad;
 template <> struct Quad<float> {
+  // one complex entry (the ninth link entry, stored apart from the pairs)
+  static __device__ __forceinline__ Cx<float> load1(const void* base, size_t idx) {
+    const float2 v = __ldg((const float2*)base + idx);
+    return cx<float>(v.x, v.y);
+  }
+  static __device__ __forceinline__ void store1(void* base, size_t idx, Cx<float> a) {
+    ((float2*)base)[idx] = make_float2(a.re, a.im);
+  }
   static __device__ __forceinline__ void load(const void* base, size_t idx, Cx<float>& a, Cx<float>& b) {
     const float4 v = __ldg((const float4*)base + idx);
     a = cx<float>(v.x, v.y);
@@ -431,6 +439,13 @@ template <> struct Quad<float> {
   }
 };
 template <> struct Quad<double> {
+  static __device__ __forceinline__ Cx<double> load1(const void* base, size_t idx) {
+    const double2 v = __ldg((const double2*)base + idx);
+    return cx<double>(v.x, v.y);
+  }
+  static __device__ __forceinline__ void store1(void* base, size_t idx, Cx<double> a) {
+    ((double2*)base)[idx] = make_double2(a.re, a.im);
+  }
   static __device__ __forceinline__ void load(const void* base, size_t idx, Cx<double>& a, Cx<double>& b) {
     const double2* p = (const double2*)base + 2 * idx;
     const double2 u = __ldg(p), v = __ldg(p + 1);
@@ -501,9 +516,8 @@ template <typename R, int NC> struct Gauge {
       m.e[(2 * q + 1) / 3][(2 * q + 1) % 3] = b;
     }
     if (NC == 9) {
-      const C2* tail = (const C2*)((const char*)p + (size_t)4 * NP * V * 4 * sizeof(R));
-      const C2 v = __ldg(tail + (size_t)((unsigned)mu * (unsigned)V + (unsigned)s));
-      m.e[2][2] = cx<R>(v.x, v.y);
+      const void* tail = (const char*)p + (size_t)4 * NP * V * 4 * sizeof(R);
+      m.e[2][2] = Quad<R>::load1(tail, (size_t)((unsigned)mu * (unsigned)V + (unsigned)s));
     } else {
       rebuild_row2(m);
     }
@@ -515,11 +529,8 @@ template <typename R, int NC> struct Gauge {
       Quad<R>::store(p, (size_t)idx(mu, q, s), m.e[(2 * q) / 3][(2 * q) % 3],
                      m.e[(2 * q + 1) / 3][(2 * q + 1) % 3]);
     if (NC == 9) {
-      C2* tail = (C2*)((char*)p + (size_t)4 * NP * V * 4 * sizeof(R));
-      C2 v;
-      v.x = m.e[2][2].re;
-      v.y = m.e[2][2].im;
-      tail[(size_t)((unsigned)mu * (unsigned)V + (unsigned)s)] = v;
+      void* tail = (char*)p + (size_t)4 * NP * V * 4 * sizeof(R);
+      Quad<R>::store1(tail, (size_t)((unsigned)mu * (unsigned)V + (unsigned)s), m.e[2][2]);
     }
   }
 };

@@ -213,7 +213,10 @@ fg_status fg_lattice_create(const fg_params* p, fg_lattice** out) {
     if (p->dims[i] < 2 || (p->dims[i] & 1)) return FG_EINVAL;
   const long long V = (long long)p->dims[0] * p->dims[1] * p->dims[2] * p->dims[3];
   if (V > (1LL << 28)) return FG_EINVAL;  // 32-bit element indices of links and momenta: 16 V - 1 < 2^32
-  if (p->precision != FG_FP64 && p->precision != FG_FP32 && p->precision != FG_FP32_FP16CG) return FG_EINVAL;
+  if (p->precision != FG_FP64 && p->precision != FG_FP32 && p->precision != FG_FP32_FP16CG &&
+      p->precision != FG_DF64)
+    return FG_EINVAL;
+  if (p->precision == FG_DF64 && p->kappa != 0.0) return FG_EINVAL;  // double-float handles are pure gauge
   if (p->link_reals != 18 && p->link_reals != 12) return FG_EINVAL;
   if (!(p->beta >= 0.0) || !(p->kappa >= 0.0) || !(p->cg_tol > 0.0) || !(p->cg_tol_action > 0.0) ||
       p->cg_maxiter < 1 || !(p->cg_delta > 0.0 && p->cg_delta < 1.0))
@@ -221,7 +224,7 @@ fg_status fg_lattice_create(const fg_params* p, fg_lattice** out) {
   fg_lattice* h = new (std::nothrow) fg_lattice();
   if (!h) return FG_ENOMEM;
   h->prm = *p;
-  if (h->prm.reunitarize < 0) h->prm.reunitarize = (p->precision != FG_FP64) ? 1 : 0;
+  if (h->prm.reunitarize < 0) h->prm.reunitarize = (p->precision == FG_FP32 || p->precision == FG_FP32_FP16CG) ? 1 : 0;
   if (!(h->prm.alpha > 0.0)) h->prm.alpha = 0.1932;
   fg_status s = lattice_init(h);
   if (s != FG_OK) {

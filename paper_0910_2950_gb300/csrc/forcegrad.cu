@@ -224,6 +224,9 @@ FG_INST_TG(double, 9)
 FG_INST_TG(double, 6)
 FG_INST_TG(float, 9)
 FG_INST_TG(float, 6)
+FG_INST_TG(DF, 9)
+FG_INST_TG(DF, 6)
+template cudaError_t launch_kick_fg<DF>(const GeomH&, void*, const void*, const void*, double, double, cudaStream_t);
 template cudaError_t launch_kick_fg<double>(const GeomH&, void*, const void*, const void*, double, double,
                                             cudaStream_t);
 template cudaError_t launch_kick_fg<float>(const GeomH&, void*, const void*, const void*, double, double,

@@ -122,7 +122,9 @@ constexpr int kEnergyThreads = 256;
 // parities), block partial sums in the per-site value type A (double-float
 // for FP32 fields: GB300's FP64 unit made the FP64 block tree and per-site
 // arithmetic most of this kernel's time).
-template <typename R> using EnergyAcc = typename std::conditional<std::is_same<R, float>::value, DF, double>::type;
+template <typename R>
+using EnergyAcc =
+    typename std::conditional<std::is_same<R, float>::value || std::is_same<R, DF>::value, DF, double>::type;
 
 template <typename R, int NC>
 __global__ void __launch_bounds__(kEnergyThreads, (std::is_same<R, float>::value ? 2 : 1))
@@ -200,8 +202,8 @@ __global__ void gauge_to_canon_kernel(Gauge<R, NC> U, double* __restrict__ canon
   double* dst = canon + (size_t)i * 18;
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
-    dst[2 * k] = m.e[k / 3][k % 3].re;
-    dst[2 * k + 1] = m.e[k / 3][k % 3].im;
+    dst[2 * k] = double(m.e[k / 3][k % 3].re);
+    dst[2 * k + 1] = double(m.e[k / 3][k % 3].im);
   }
 }
 
@@ -234,7 +236,7 @@ __global__ void mom_to_canon_kernel(Mom<R> P, double* __restrict__ canon, Geom g
   R p[8];
   P.load(mu, cb_index(g, c), p);
 #pragma unroll
-  for (int k = 0; k < 8; ++k) canon[(size_t)i * 8 + k] = p[k];
+  for (int k = 0; k < 8; ++k) canon[(size_t)i * 8 + k] = double(p[k]);
 }
 
 // ---------------------------------------------------------------------------
@@ -410,6 +412,7 @@ cudaError_t launch_kick_ff(const GeomH& gh, void* P, const void* FF, double c, c
 }
 template cudaError_t launch_kick_ff<double>(const GeomH&, void*, const void*, double, cudaStream_t);
 template cudaError_t launch_kick_ff<float>(const GeomH&, void*, const void*, double, cudaStream_t);
+template cudaError_t launch_kick_ff<DF>(const GeomH&, void*, const void*, double, cudaStream_t);
 
 #define FG_INST_RNC(R, NC)                                                                          \
   template cudaError_t launch_gauge_force<R, NC>(const GeomH&, int, const ForceArgs&, cudaStream_t); \
@@ -429,12 +432,17 @@ FG_INST_RNC(double, 9)
 FG_INST_RNC(double, 6)
 FG_INST_RNC(float, 9)
 FG_INST_RNC(float, 6)
+FG_INST_RNC(DF, 9)
+FG_INST_RNC(DF, 6)
 
 template cudaError_t launch_refresh_momenta<double>(const GeomH&, void*, uint64_t, uint32_t, cudaStream_t);
 template cudaError_t launch_refresh_momenta<float>(const GeomH&, void*, uint64_t, uint32_t, cudaStream_t);
+template cudaError_t launch_refresh_momenta<DF>(const GeomH&, void*, uint64_t, uint32_t, cudaStream_t);
 template cudaError_t launch_mom_to_device<double>(const GeomH&, const double*, void*, cudaStream_t);
 template cudaError_t launch_mom_to_device<float>(const GeomH&, const double*, void*, cudaStream_t);
+template cudaError_t launch_mom_to_device<DF>(const GeomH&, const double*, void*, cudaStream_t);
 template cudaError_t launch_mom_to_canon<double>(const GeomH&, const void*, double*, cudaStream_t);
 template cudaError_t launch_mom_to_canon<float>(const GeomH&, const void*, double*, cudaStream_t);
+template cudaError_t launch_mom_to_canon<DF>(const GeomH&, const void*, double*, cudaStream_t);
 
 }  // namespace fg

@@ -175,8 +175,12 @@ __device__ __forceinline__ void force_link(const Gauge<R, NC>& U, const Mom<R>& 
 // barrier.  The caller separates two calls on the same tsh by a barrier.
 template <typename R, int NC>
 constexpr bool kForceSharedT = FG_FORCE_SHARED_T && std::is_same<R, float>::value && NC == 6;
+// Double-float links need about twice the registers of FP32 ones: one block
+// of 256 threads per SM, up to 255 registers a thread.
 template <typename R, int NC>
-constexpr int kForceMinBlocks = kForceSharedT<R, NC> ? FG_FORCE_SHARED_MIN_BLOCKS : FG_FORCE_MIN_BLOCKS;
+constexpr int kForceMinBlocks = std::is_same<R, DF>::value
+                                    ? 1
+                                    : (kForceSharedT<R, NC> ? FG_FORCE_SHARED_MIN_BLOCKS : FG_FORCE_MIN_BLOCKS);
 
 template <int NC, int MODE, int NS>
 __device__ __forceinline__ void force_link_shared(float2 (*tsh)[9][NS], bool ok, int s, const Gauge<float, NC>& U,
@@ -271,10 +275,11 @@ __device__ __forceinline__ void drift_link(const Gauge<R, NC>& Uin, const Mom<R>
 // stores h0[s] = h(x), mode 1 sets v[2] = h(x) - h0[s].  If sg_in is given,
 // S_G(x) is read from it instead of recomputed (the links have not changed
 // since it was stored); if sg_out is given, S_G(x) is stored.  A is the type
-// of the per-site values: double, or DF for FP32 fields, which keeps FP64
-// arithmetic (1/64 of the FP32 rate on GB300) out of the kernel.  Sums of
-// FP32 terms are double-float in either case (each p^2 split exactly by an
-// FMA, each plaquette trace added with two_sum); FP64 fields sum in FP64.
+// of the per-site values: double, or DF for FP32 and double-float fields,
+// which keeps FP64 arithmetic (1/64 of the FP32 rate on GB300) out of the
+// kernel.  Sums of FP32 terms are double-float in either case (each p^2
+// split exactly by an FMA, each plaquette trace added with two_sum);
+// double-float fields compute and sum in double-float, FP64 fields in FP64.
 template <typename A> __device__ __forceinline__ A acc_of(DF x);
 template <> __device__ __forceinline__ DF acc_of<DF>(DF x) { return x; }
 template <> __device__ __forceinline__ double acc_of<double>(DF x) { return double(x); }
@@ -284,7 +289,8 @@ __device__ __forceinline__ void site_energy(const Gauge<R, NC>& U, const Mom<R>&
                                             A beta6, A beta3, int mode, A* __restrict__ h0, A v[3],
                                             const A* __restrict__ sg_in = nullptr, A* __restrict__ sg_out = nullptr) {
   constexpr bool kDF = std::is_same<R, float>::value;
-  static_assert(kDF || std::is_same<A, double>::value, "FP64 fields keep FP64 per-site values");
+  constexpr bool kDD = std::is_same<R, DF>::value;
+  static_assert(kDF || kDD || std::is_same<A, double>::value, "FP64 fields keep FP64 per-site values");
   A t = A(0);
   if (P.p != nullptr) {
     DF tdf(0.0f);
@@ -298,12 +304,14 @@ __device__ __forceinline__ void site_energy(const Gauge<R, NC>& U, const Mom<R>&
         if constexpr (kDF) {
           const float sq = __fmul_rn(p[k], p[k]);
           tdf = tdf + DF(sq, __fmaf_rn(p[k], p[k], -sq));
+        } else if constexpr (kDD) {
+          tdf = fma(p[k], p[k], tdf);
         } else {
           t64 += double(p[k]) * double(p[k]);
         }
       }
     }
-    if constexpr (kDF) t = acc_of<A>(tdf) * A(0.5f);
+    if constexpr (kDF || kDD) t = acc_of<A>(tdf) * A(0.5f);
     else t = A(0.5 * t64);
   }
   A sg;
@@ -331,10 +339,11 @@ __device__ __forceinline__ void site_energy(const Gauge<R, NC>& U, const Mom<R>&
         const M3<R> a = mul(umu, U.load(nu, other + dp[mu]));
         const M3<R> b = mul(U.load(nu, s), U.load(mu, other + dp[nu]));
         if constexpr (kDF) trdf = trdf + DF(float(re_tr_mul_nd(a, b)));
+        else if constexpr (kDD) trdf = trdf + re_tr_mul_nd(a, b);
         else tr64 += double(re_tr_mul_nd(a, b));
       }
     }
-    if constexpr (kDF) sg = beta6 - beta3 * acc_of<A>(trdf);
+    if constexpr (kDF || kDD) sg = beta6 - beta3 * acc_of<A>(trdf);
     else sg = beta6 - beta3 * A(tr64);
   }
   if (sg_out != nullptr) sg_out[s] = sg;
@@ -357,6 +366,17 @@ __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, R& z0, R& z1)
   sincospi(R(2) * u2, &sn, &cs);
   z0 = r * cs;
   z1 = r * sn;
+}
+
+// Double-float fields take FP32 draws: the Gaussian deviates need no more
+// than FP32 resolution, and every later use of them (kinetic term, MD) is
+// exact to double-float rounding for whatever value was drawn.
+template <>
+__device__ __forceinline__ void box_muller<DF>(uint32_t a, uint32_t b, DF& z0, DF& z1) {
+  float x0, x1;
+  box_muller<float>(a, b, x0, x1);
+  z0 = DF(x0);
+  z1 = DF(x1);
 }
 
 // Unit-Gaussian momenta of link (s, mu): two Philox-4x32-10 draws with

@@ -89,7 +89,7 @@ def footprint_bytes(spec: ChainSpec, precision: str = "fp32", link_reals: int = 
     rounding of the small buffers.  (The closed-form force gradient's
     buffers are not included: the server does not offer that integrator.)"""
     v = int(np.prod(spec.dims))
-    r = 8 if precision == "fp64" else 4
+    r = 8 if precision in ("fp64", "df64") else 4     # bytes per real (double-float: two floats)
     gauge = 4 * v * link_reals * r
     mom = 4 * v * 8 * r
     total = 3 * gauge + 2 * mom + 3 * 8 * v + 4 * 8 * ((v + 255) // 256 + 1) + 32 * 8 + 4 * v * 18 * 8

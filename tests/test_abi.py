@@ -71,6 +71,16 @@ def test_create_rejects_bad_parameters_before_touching_the_device(lib, field, va
     assert not h.value
 
 
+def test_double_float_handles_are_pure_gauge(lib):
+    p = fg.FgParams()
+    lib.fg_params_default(C.byref(p))
+    p.precision = fg.PRECISIONS["df64"]
+    p.kappa = 0.158
+    h = C.c_void_p()
+    assert lib.fg_lattice_create(C.byref(p), C.byref(h)) == fg.FG_EINVAL
+    assert not h.value
+
+
 def test_null_handle_calls_fail_cleanly(lib):
     assert lib.fg_refresh_momenta(None) == fg.FG_EINVAL
     assert lib.fg_sync(None) == fg.FG_EINVAL
@@ -80,7 +90,7 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.fg_trajectories_host_momenta(None, 2, 0.25, 1.0, 0, None, None, None) == fg.FG_EINVAL
 
 
-@pytest.mark.parametrize("case", ["odd", "too_large", "tile", "link_reals"])
+@pytest.mark.parametrize("case", ["odd", "too_large", "tile", "link_reals", "df64_tile64", "df64_12real"])
 def test_batch_create_rejects_bad_parameters_before_touching_the_device(lib, case):
     dims = [4, 4, 4, 4, 6, 6, 6, 6]
     if case == "odd":
@@ -99,6 +109,10 @@ def test_batch_create_rejects_bad_parameters_before_touching_the_device(lib, cas
         p.tile = 48
     elif case == "link_reals":
         p.link_reals = 16
+    elif case == "df64_tile64":       # double-float batches compile tiles of 16 and 32 half-sites only
+        p.precision, p.tile = fg.PRECISIONS["df64"], 64
+    elif case == "df64_12real":       # and 18-real links only
+        p.precision, p.link_reals = fg.PRECISIONS["df64"], 12
     h = C.c_void_p()
     assert lib.fg_batch_create(C.byref(p), C.byref(h)) == fg.FG_EINVAL
     assert not h.value
