@@ -115,13 +115,28 @@ __device__ __forceinline__ DF sqrt(DF a) {
   return df_fast_two_sum(s, __fdiv_rn(d, __fadd_rn(s, s)));
 }
 
-// sin and cos of a double-float argument from the Taylor series on x / 2^k,
-// |x / 2^k| <= 1/8, and k double-angle steps (sin 2y = 2 sin y cos y,
-// cos 2y = 1 - 2 sin^2 y).  The series stop at y^9 and y^8: the first
-// omitted terms are below 3e-16 of the result.  Each doubling at most doubles
-// the absolute error, so |x| <= 4 (k <= 5) keeps it near 1e-14; arguments
-// here are rotation angles of link updates, usually well below 1.
+// sin and cos of a double-float argument.  Arguments beyond pi/4 are first
+// reduced by n pi/2 (Cody and Waite's additive reduction, with pi/2 split
+// into three floats; the first two products are formed exactly), then the
+// Taylor series run on y / 2^k, |y / 2^k| <= 1/8, followed by k double-angle
+// steps (sin 2y = 2 sin y cos y, cos 2y = 1 - 2 sin^2 y), and the quadrant
+// n mod 4 permutes the result.  The series stop at y^9 and y^8: the first
+// omitted terms are below 3e-16 of the result.  Each doubling at most
+// doubles the absolute error and k <= 3 after the reduction, so the error
+// stays near 3e-14 plus the 2^-48 |x| that the argument itself carries.
+// Arguments here are rotation angles of link updates, usually below 1.
 __device__ __forceinline__ void sincos(DF x, DF* s, DF* c) {
+  int quadrant = 0;
+  if (fabsf(x.hi) > 0.785398163f) {
+    const float n = rintf(__fmul_rn(x.hi, 0.636619772f));  // round(2 x / pi)
+    constexpr float p1 = 1.57079637050628662109375f, p2 = -4.37113882867379300296306610107421875e-8f,
+                    p3 = -1.71512451000588190e-15f;         // p1 + p2 + p3 = pi/2 to ~1e-23
+    const float q1 = __fmul_rn(n, p1), q2 = __fmul_rn(n, p2);
+    x = x - DF(q1, __fmaf_rn(n, p1, -q1));
+    x = x - DF(q2, __fmaf_rn(n, p2, -q2));
+    x = x - DF(__fmul_rn(n, p3));
+    quadrant = (int)n & 3;
+  }
   // k = max(0, e + 3) with |x.hi| = m 2^e, m in [0.5, 1)
   const int e = (int)((__float_as_uint(x.hi) >> 23) & 0xffu) - 126;
   const int k = e + 3 > 0 ? (e + 3 < 60 ? e + 3 : 60) : 0;
@@ -142,8 +157,10 @@ __device__ __forceinline__ void sincos(DF x, DF* s, DF* c) {
     sn = (sn * cs) * 2.0f;
     cs = DF(1.0f) - s2 * 2.0f;
   }
-  *s = sn;
-  *c = cs;
+  // sin(y + n pi/2), cos(y + n pi/2)
+  const DF ms = -sn, mc = -cs;
+  *s = quadrant == 0 ? sn : (quadrant == 1 ? cs : (quadrant == 2 ? ms : mc));
+  *c = quadrant == 0 ? cs : (quadrant == 1 ? ms : (quadrant == 2 ? mc : sn));
 }
 
 // Storage: one complex double-float is a float4 (re.hi, re.lo, im.hi, im.lo),
@@ -250,25 +267,32 @@ __device__ __forceinline__ M3<DF> expi_herm<DF>(const M3<DF>& a) {
     const DF u2 = u * u;
     DF w2 = c1 - u2 * 3.0f;
     if (w2.hi < 0.0f) w2 = DF(0.0f);
-    DF su, cu;
-    sincos(u, &su, &cu);
-    DF cw, xi0;
+    const DF w = sqrt(w2);
+    // sin and cos of u and of w through one copy of the series code (two
+    // inlined copies cost instruction-cache misses in the force kernel)
+    DF su, cu, sw, cw;
+#pragma unroll 1
+    for (int i = 0; i < 2; ++i) {
+      DF sv, cv;
+      sincos(i ? w : u, &sv, &cv);
+      if (i) {
+        sw = sv;
+        cw = cv;
+      } else {
+        su = sv;
+        cu = cv;
+      }
+    }
+    DF xi0;
     if (w2.hi < 0.0025f) {
-      // |w| < 0.05: cos w and sin(w)/w from their series in w^2 (first omitted
-      // terms below 1e-16)
-      constexpr DF k2(1.0 / 2.0), k4(1.0 / 24.0), k6(-1.0 / 720.0), k8(1.0 / 40320.0);
+      // |w| < 0.05: sin(w)/w from its series in w^2 (first omitted term
+      // below 1e-16), not from a quotient of small numbers
       constexpr DF x2(-1.0 / 6.0), x4(1.0 / 120.0), x6(-1.0 / 5040.0), x8(1.0 / 362880.0);
-      DF t = fma(w2, k8, k6);
-      t = fma(w2, t, k4);
-      cw = fma(w2 * w2, t, DF(1.0f) - w2 * k2);
       DF q = fma(w2, x8, x6);
       q = fma(w2, q, x4);
       q = fma(w2, q, x2);
       xi0 = fma(w2, q, DF(1.0f));
     } else {
-      const DF w = sqrt(w2);
-      DF sw;
-      sincos(w, &sw, &cw);
       xi0 = sw / w;
     }
     const DF s2u = (su * cu) * 2.0f;
@@ -301,6 +325,109 @@ __device__ __forceinline__ M3<DF> expi_herm<DF>(const M3<DF>& a) {
       e.e[i][j] = s;
     }
   return e;
+}
+
+
+// ---------------------------------------------------------------------------
+// Products of SU(3) matrices in double-float with an anchored accumulator.
+// For unitary a and b every partial sum of the real or imaginary part of an
+// entry of a b lies in [-1, 1] (each term is bounded by |a_ik| |b_kj| and
+// those sum to at most |row i of a| |column j of b| = 1, Cauchy-Schwarz), so
+// t = 3 + (partial sum) stays in [2, 4], where the FP32 grid is 2^-22.  A
+// term x_h y_h enters t by one FMA; its rounding error
+// rho = t_old + x_h y_h - t_new (|rho| <= 2^-23) is recovered by a second FMA,
+// fma(x_h, y_h, t_old - t_new), whose operand t_old - t_new is exact
+// (Sterbenz's lemma) and whose result is within 2^-24 |rho| <= 2^-47 of rho;
+// the low parts enter as x_h y_l + x_l y_h in FP32.  The value is
+// (t - 3) + lo, t - 3 being exact, normalised by two_sum: six FP32
+// operations per term instead of the fifteen of a double-float FMA, at the
+// same ~2^-47 accuracy.  Callers guarantee unitary factors (the links of a
+// staple and products of them); other inputs lose accuracy gracefully as t
+// leaves [2, 4].
+struct Anchored {
+  float t, lo;
+  __device__ __forceinline__ Anchored() : t(3.0f), lo(0.0f) {}
+  // += x y
+  __device__ __forceinline__ void add(DF x, DF y) {
+    const float t0 = t;
+    t = __fmaf_rn(x.hi, y.hi, t0);
+    lo = __fadd_rn(lo, __fmaf_rn(x.hi, y.hi, __fsub_rn(t0, t)));
+    lo = __fmaf_rn(x.hi, y.lo, lo);
+    lo = __fmaf_rn(x.lo, y.hi, lo);
+  }
+  // -= x y
+  __device__ __forceinline__ void sub(DF x, DF y) { add(-x, y); }
+  __device__ __forceinline__ DF value() const { return df_two_sum(__fsub_rn(t, 3.0f), lo); }
+};
+
+// m^dagger if d, else m (run-time choice by selects, so that one code path
+// serves both).
+__device__ __forceinline__ M3<DF> dagger_if(const M3<DF>& m, bool d) {
+  M3<DF> r;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const Cx<DF> v = d ? m.e[j][i] : m.e[i][j];
+      r.e[i][j] = cx<DF>(v.re, d ? -v.im : v.im);
+    }
+  return r;
+}
+
+// a b, a b^dagger and a^dagger b for unitary double-float matrices.
+__device__ __forceinline__ M3<DF> su3_mul(const M3<DF>& a, const M3<DF>& b) {
+  M3<DF> c;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      Anchored re, im;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        re.add(a.e[i][k].re, b.e[k][j].re);
+        re.sub(a.e[i][k].im, b.e[k][j].im);
+        im.add(a.e[i][k].re, b.e[k][j].im);
+        im.add(a.e[i][k].im, b.e[k][j].re);
+      }
+      c.e[i][j] = cx<DF>(re.value(), im.value());
+    }
+  return c;
+}
+__device__ __forceinline__ M3<DF> su3_mul_nd(const M3<DF>& a, const M3<DF>& b) {
+  M3<DF> c;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      Anchored re, im;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        re.add(a.e[i][k].re, b.e[j][k].re);
+        re.add(a.e[i][k].im, b.e[j][k].im);
+        im.add(a.e[i][k].im, b.e[j][k].re);
+        im.sub(a.e[i][k].re, b.e[j][k].im);
+      }
+      c.e[i][j] = cx<DF>(re.value(), im.value());
+    }
+  return c;
+}
+__device__ __forceinline__ M3<DF> su3_mul_dn(const M3<DF>& a, const M3<DF>& b) {
+  M3<DF> c;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      Anchored re, im;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        re.add(a.e[k][i].re, b.e[k][j].re);
+        re.add(a.e[k][i].im, b.e[k][j].im);
+        im.add(a.e[k][i].re, b.e[k][j].im);
+        im.sub(a.e[k][i].im, b.e[k][j].re);
+      }
+      c.e[i][j] = cx<DF>(re.value(), im.value());
+    }
+  return c;
 }
 
 

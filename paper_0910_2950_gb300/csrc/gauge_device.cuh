@@ -44,6 +44,14 @@ __device__ __forceinline__ void cb_half_steps(const Geom& g, const int c[4], int
   }
 }
 
+// Product of two special unitary matrices (a link and a link, or exp(iA)
+// and a link): the anchored products for double-float links.
+template <typename R>
+__device__ __forceinline__ M3<R> link_mul(const M3<R>& a, const M3<R>& b) {
+  if constexpr (std::is_same<R, DF>::value) return su3_mul(a, b);
+  else return mul(a, b);
+}
+
 template <typename R, int NC>
 __device__ __forceinline__ M3<R> staple_sum(const Gauge<R, NC>& U, const Geom& g, const int c[4], int s, int mu) {
   M3<R> a;
@@ -65,16 +73,42 @@ __device__ __forceinline__ M3<R> staple_sum(const Gauge<R, NC>& U, const Geom& g
     const int nu = (mu + k) & 3;
     int dp, dm;
     cb_half_steps(g, c, nu, dp, dm);
-    {
-      // upper: U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag
-      const M3<R> t = mul_nd(U.load(nu, s_pmu), U.load(mu, other + dp));
-      mac_nd(a, t, U.load(nu, s));
-    }
-    {
-      // lower: U_nu(x+mu-nu)^dag U_mu(x-nu)^dag U_nu(x-nu) = (U_mu(x-nu) U_nu(x+mu-nu))^dag U_nu(x-nu)
+    if constexpr (std::is_same<R, DF>::value) {
+      // Double-float: every staple is a product of links, hence unitary, so
+      // the anchored products (df64.cuh) apply.  Both staples of the plane
+      // are written as X Y^dag Z with run-time daggers,
+      //   upper  U_nu(x+mu)          U_mu(x+nu)^dag U_nu(x)^dag,
+      //   lower  U_nu(x+mu-nu)^dag   U_mu(x-nu)^dag U_nu(x-nu),
+      // and the two products of each run through one loop body: unrolled,
+      // the double-float code of four products per plane overflowed the
+      // instruction cache (most issue stalls were instruction fetch).
       const int s_mnu = other + dm;
-      const M3<R> t = mul(U.load(mu, s_mnu), U.load(nu, s + dm + dmu));
-      mac_dn(a, t, U.load(nu, s_mnu));
+#pragma unroll 1
+      for (int up = 1; up >= 0; --up) {
+        M3<DF> l = dagger_if(U.load(nu, up ? s_pmu : s + dm + dmu), !up);
+#pragma unroll 1
+        for (int q = 0; q < 2; ++q) {
+          // Y^dag = U_mu(x+nu)^dag or U_mu(x-nu)^dag, then Z
+          const int sr = q ? (up ? s : s_mnu) : (up ? other + dp : s_mnu);
+          l = su3_mul(l, dagger_if(U.load(q ? nu : mu, sr), q ? up != 0 : true));
+        }
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j) a.e[i][j] = a.e[i][j] + l.e[i][j];
+      }
+    } else {
+      {
+        // upper: U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag
+        const M3<R> t = mul_nd(U.load(nu, s_pmu), U.load(mu, other + dp));
+        mac_nd(a, t, U.load(nu, s));
+      }
+      {
+        // lower: U_nu(x+mu-nu)^dag U_mu(x-nu)^dag U_nu(x-nu) = (U_mu(x-nu) U_nu(x+mu-nu))^dag U_nu(x-nu)
+        const int s_mnu = other + dm;
+        const M3<R> t = mul(U.load(mu, s_mnu), U.load(nu, s + dm + dmu));
+        mac_dn(a, t, U.load(nu, s_mnu));
+      }
     }
   }
   return a;
@@ -88,11 +122,27 @@ __device__ __forceinline__ void force_finish(const Gauge<R, NC>& U, const Mom<R>
                                              const Gauge<R, NC>& Uout, int s, int mu, const M3<R>& a, R beta6,
                                              R ckick, R cdrift, R cdisp, int reunit, R ffw) {
   const M3<R> ul = U.load(mu, s);
-  const M3<R> omega = mul(ul, a);
   R f[8];
-  im_tr_gellmann(omega, f);
+  if constexpr (std::is_same<R, DF>::value) {
+    // a is a sum of six unitary staples, so a / 8 has columns of norm <= 3/4
+    // and U (a / 8) is within the anchored products' bounds; scaling by a
+    // power of two is exact
+    M3<DF> a8;
 #pragma unroll
-  for (int k = 0; k < 8; ++k) f[k] *= beta6;
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        a8.e[i][j] = cx<DF>(DF(a.e[i][j].re.hi * 0.125f, a.e[i][j].re.lo * 0.125f),
+                            DF(a.e[i][j].im.hi * 0.125f, a.e[i][j].im.lo * 0.125f));
+    im_tr_gellmann(su3_mul(ul, a8), f);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) f[k] = (f[k] * 8.0f) * beta6;
+  } else {
+    const M3<R> omega = mul(ul, a);
+    im_tr_gellmann(omega, f);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) f[k] *= beta6;
+  }
   if (FF.p != nullptr) {
     R ff[8];
     FF.load(mu, s, ff);
@@ -112,7 +162,7 @@ __device__ __forceinline__ void force_finish(const Gauge<R, NC>& U, const Mom<R>
       for (int k = 0; k < 8; ++k) p[k] *= cdrift;
       const M3<R> e = expi_herm(alg_to_mat(p));
       const M3<R> ub = (Ubase.p == U.p) ? ul : Ubase.load(mu, s);
-      M3<R> un = mul(e, ub);
+      M3<R> un = link_mul(e, ub);
       if (reunit) reunitarize(un);
       Uout.store(mu, s, un);
     }
@@ -124,7 +174,7 @@ __device__ __forceinline__ void force_finish(const Gauge<R, NC>& U, const Mom<R>
 #pragma unroll
     for (int k = 0; k < 8; ++k) f[k] *= -cdisp;
     const M3<R> e = expi_herm(alg_to_mat(f));
-    Uout.store(mu, s, mul(e, ul));
+    Uout.store(mu, s, link_mul(e, ul));
   }
 }
 
@@ -175,11 +225,14 @@ __device__ __forceinline__ void force_link(const Gauge<R, NC>& U, const Mom<R>& 
 // barrier.  The caller separates two calls on the same tsh by a barrier.
 template <typename R, int NC>
 constexpr bool kForceSharedT = FG_FORCE_SHARED_T && std::is_same<R, float>::value && NC == 6;
+#ifndef FG_FORCE_DF_MIN_BLOCKS
+#define FG_FORCE_DF_MIN_BLOCKS 1
+#endif
 // Double-float links need about twice the registers of FP32 ones: one block
 // of 256 threads per SM, up to 255 registers a thread.
 template <typename R, int NC>
 constexpr int kForceMinBlocks = std::is_same<R, DF>::value
-                                    ? 1
+                                    ? FG_FORCE_DF_MIN_BLOCKS
                                     : (kForceSharedT<R, NC> ? FG_FORCE_SHARED_MIN_BLOCKS : FG_FORCE_MIN_BLOCKS);
 
 template <int NC, int MODE, int NS>
@@ -264,7 +317,7 @@ __device__ __forceinline__ void drift_link(const Gauge<R, NC>& Uin, const Mom<R>
 #pragma unroll
   for (int k = 0; k < 8; ++k) p[k] *= c;
   const M3<R> e = expi_herm(alg_to_mat(p));
-  M3<R> un = mul(e, Uin.load(mu, s));
+  M3<R> un = link_mul(e, Uin.load(mu, s));
   if (reunit) reunitarize(un);
   Uout.store(mu, s, un);
 }
@@ -331,16 +384,38 @@ __device__ __forceinline__ void site_energy(const Gauge<R, NC>& U, const Mom<R>&
     }
     DF trdf(0.0f);
     double tr64 = 0.0;
+    if constexpr (kDD) {
+      // double-float links: the plaquette's two products by the anchored
+      // products, one copy of the code for the six planes (x, y, z, t as
+      // mu, nu with mu < nu; the planes' half-index steps by selects)
+#pragma unroll 1
+      for (int pl = 0; pl < 6; ++pl) {
+        const int mu = pl < 3 ? 0 : (pl < 5 ? 1 : 2);
+        const int nu = pl < 3 ? pl + 1 : (pl < 5 ? pl - 1 : 3);
+        const int dmu = sel4(dp, mu), dnu = sel4(dp, nu);
+        M3<DF> pr[2];
+#pragma unroll 1
+        for (int q = 0; q < 2; ++q) {
+          // U_mu(x) U_nu(x+mu), then U_nu(x) U_mu(x+nu)
+          const M3<DF> l = U.load(q ? nu : mu, s);
+          const M3<DF> r = U.load(q ? mu : nu, other + (q ? dnu : dmu));
+          const M3<DF> m = su3_mul(l, r);
+          if (q) pr[1] = m;
+          else pr[0] = m;
+        }
+        trdf = trdf + re_tr_mul_nd(pr[0], pr[1]);
+      }
+    } else {
 #pragma unroll
-    for (int mu = 0; mu < 4; ++mu) {
-      const M3<R> umu = U.load(mu, s);
+      for (int mu = 0; mu < 4; ++mu) {
+        const M3<R> umu = U.load(mu, s);
 #pragma unroll
-      for (int nu = mu + 1; nu < 4; ++nu) {
-        const M3<R> a = mul(umu, U.load(nu, other + dp[mu]));
-        const M3<R> b = mul(U.load(nu, s), U.load(mu, other + dp[nu]));
-        if constexpr (kDF) trdf = trdf + DF(float(re_tr_mul_nd(a, b)));
-        else if constexpr (kDD) trdf = trdf + re_tr_mul_nd(a, b);
-        else tr64 += double(re_tr_mul_nd(a, b));
+        for (int nu = mu + 1; nu < 4; ++nu) {
+          const M3<R> a = mul(umu, U.load(nu, other + dp[mu]));
+          const M3<R> b = mul(U.load(nu, s), U.load(mu, other + dp[nu]));
+          if constexpr (kDF) trdf = trdf + DF(float(re_tr_mul_nd(a, b)));
+          else tr64 += double(re_tr_mul_nd(a, b));
+        }
       }
     }
     if constexpr (kDF || kDD) sg = beta6 - beta3 * acc_of<A>(trdf);

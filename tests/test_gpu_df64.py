@@ -87,7 +87,8 @@ def test_large_step_exponential_df64(fgmod):
     uo, po = it.md_step(it.GaugeSystem(BETA), it.Integrator("qpq"), u, p, 1.0)
     assert _rel(ug, uo) < 1e-12
     assert _rel(pg, po) < 1e-12
-    assert su3.unitarity_defect(ug) < 1e-13
+    # exp(iA) = f0 + f1 A + f2 A^2 rounds at ~2^-48 |A|^2 with |A| up to ~6 here
+    assert su3.unitarity_defect(ug) < 1e-12
 
 
 @pytest.fixture(scope="module")
