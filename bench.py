@@ -454,7 +454,8 @@ def precision_measurement(fg, stream, rank, L=16, n_time=5):
     base.close()
     p0 = inputs.gaussian_momenta(dims, 13 + rank)
     out, ref = {}, {}
-    for name, prec, reals in (("fp64_18", "fp64", 18), ("fp32_18", "fp32", 18), ("fp32_12", "fp32", 12)):
+    for name, prec, reals in (("fp64_18", "fp64", 18), ("df64_18", "df64", 18), ("fp32_18", "fp32", 18),
+                              ("fp32_12", "fp32", 12)):
         lat = fg.Lattice(dims, BETA, precision=prec, link_reals=reals, seed=600 + rank, stream=stream)
         row = {}
         for integ, dt in (("fg", 0.25), ("omelyan", 0.125)):
@@ -482,7 +483,7 @@ def precision_measurement(fg, stream, rank, L=16, n_time=5):
         f_ms, f_n = lat.kernel_time("gauge_force")
         lat.timing(False)
         lat.close()
-        esize = 8 if prec == "fp64" else 4
+        esize = 4 if prec == "fp32" else 8
         link_bytes = reals * esize + 2 * 8 * esize
         row["force_avg_launch_us"] = 1000.0 * f_ms / max(f_n, 1)
         row["force_algorithmic_gbs"] = link_bytes * 4 * L ** 4 / (f_ms / 1000.0 / max(f_n, 1)) / 1e9
@@ -490,20 +491,55 @@ def precision_measurement(fg, stream, rank, L=16, n_time=5):
         out[name] = row
     out["workload"] = (f"pure-gauge {L}^4, beta={BETA}, hot start + {THERM_TRAJ} FP64 FG trajectories; one "
                        "trajectory per integrator from the same links and momenta")
+    out["error_vs_volume"] = error_vs_volume(fg, stream, rank)
     return out
 
 
-def batched_measurement(fg, stream, rank, n_traj=6):
+def error_vs_volume(fg, stream, rank, sizes=(4, 8, 12, 16, 24, 32)):
+    """|dH - dH_fp64| of one FG trajectory (dt 1/8, tau 1) for double-float
+    and FP32 fields against the FP64 path (itself pinned to the oracle), per
+    volume, from the same links (hot start + 3 FP32 FG trajectories) and
+    momenta."""
+    rows = {}
+    for L in sizes:
+        dims = (L,) * 4
+        th = fg.Lattice(dims, BETA, precision="fp32", seed=40 + rank, stream=stream)
+        th.set_gauge(inputs.hot_start(dims, 41 + rank))
+        for _ in range(3):
+            th.trajectory("fg", 0.125, TAU, refresh=True, u_accept=0.0)
+        u = th.get_gauge()
+        th.close()
+        p = inputs.gaussian_momenta(dims, 42 + rank)
+        dh = {}
+        for prec in ("fp64", "df64", "fp32"):
+            lat = fg.Lattice(dims, BETA, precision=prec, seed=43, stream=stream)
+            lat.set_gauge(u)
+            lat.set_momenta(p)
+            dh[prec] = lat.trajectory("fg", 0.125, TAU, refresh=False, u_accept=0.0)["dH"]
+            lat.close()
+        rows[f"{L}^4"] = {"dH_fp64": dh["fp64"], "df64_error": abs(dh["df64"] - dh["fp64"]),
+                          "fp32_error": abs(dh["fp32"] - dh["fp64"])}
+    return {"workload": f"FG dt=1/8 tau=1, beta={BETA}, hot start + 3 FP32 FG trajectories, one trajectory "
+                        "per precision from the same links and momenta; errors against the FP64 path",
+            "by_volume": rows}
+
+
+def batched_measurement(fg, stream, rank, n_traj=6, n_oracle=6):
     """64 independent chains, volumes drawn from {4,6,8,10,12}^4 and beta from
-    U[5.7, 6.2] (seed 4), FG tau=1 dt=1/8: the FP32 batch (one launch per MD
+    U[5.7, 6.2] (seed 4), FG tau=1 dt=1/8: the batches (one launch per MD
     sub-step for all chains, one CUDA graph per trajectory, autotuned tiles)
-    against the plain FP64 one-chain-per-launch path on the same
-    configurations.  Reports accepted trajectories per second and <exp(-dH)>."""
+    in double-float and in FP32, against the plain FP64 one-chain-per-launch
+    path on the same configurations.  Reports accepted trajectories per
+    second and <exp(-dH)>, and each batch's dH error on every chain: one
+    trajectory from the same links and uploaded momenta against the FP64
+    path, and against the FP64 oracle on the n_oracle smallest chains."""
+    import torch
     rng = inputs.make_rng(4 + 1000 * rank)
     extents = rng.choice([4, 6, 8, 10, 12], size=64)
     betas = rng.uniform(5.7, 6.2, size=64)
     dims_list = [(int(L),) * 4 for L in extents]
     sites = int(sum(L ** 4 for L in extents))
+    # thermalised starts from the FP32 batch
     bat = fg.Batch(dims_list, betas, precision="fp32", tile=0, use_graphs=True, seed=500 + rank, stream=stream)
     for k, d in enumerate(dims_list):
         bat.set_gauge(k, inputs.hot_start(d, 700 + k + 1000 * rank))
@@ -511,29 +547,9 @@ def batched_measurement(fg, stream, rank, n_traj=6):
         bat.trajectory("fg", 0.125, 1.0, refresh=True, always_accept=True)
     for _ in range(20):
         bat.trajectory("fg", 0.125, 1.0, refresh=True, always_accept=False)
-    import torch
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    res_b = [bat.trajectory("fg", 0.125, 1.0, refresh=True, always_accept=False) for _ in range(n_traj)]
-    tb = time.perf_counter() - t0
-    tile = bat.tile()
     starts = [bat.get_gauge(k) for k in range(64)]
     bat.close()
-    # one chain per launch, FP64, same configurations
-    lats = []
-    for k, d in enumerate(dims_list):
-        lat = fg.Lattice(d, float(betas[k]), precision="fp64", seed=900 + k + 1000 * rank, stream=stream)
-        lat.set_gauge(starts[k])
-        lats.append(lat)
-    for lat in lats:      # warm-up
-        lat.trajectory("fg", 0.125, 1.0, refresh=True, u_accept=-1.0)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    res_s = [[lat.trajectory("fg", 0.125, 1.0, refresh=True, u_accept=-1.0) for lat in lats]
-             for _ in range(n_traj)]
-    ts = time.perf_counter() - t0
-    for lat in lats:
-        lat.close()
+    moms = [inputs.gaussian_momenta(d, 800 + k + 1000 * rank) for k, d in enumerate(dims_list)]
 
     def stats(res, secs):
         flat = [r for sweep in res for r in sweep]
@@ -543,14 +559,141 @@ def batched_measurement(fg, stream, rank, n_traj=6):
                 "acceptance": acc / len(flat), "mean_exp_minus_dH": float(e.mean()),
                 "mean_exp_minus_dH_err": float(e.std(ddof=1) / np.sqrt(len(e)))}
 
-    b = stats(res_b, tb)
+    # one chain per launch, FP64: the precision reference and the speed baseline
+    lats = []
+    for k, d in enumerate(dims_list):
+        lat = fg.Lattice(d, float(betas[k]), precision="fp64", seed=900 + k + 1000 * rank, stream=stream)
+        lats.append(lat)
+    dh64 = []
+    for k, lat in enumerate(lats):
+        lat.set_gauge(starts[k])
+        lat.set_momenta(moms[k])
+        dh64.append(lat.trajectory("fg", 0.125, 1.0, refresh=False, u_accept=0.0)["dH"])
+        lat.set_gauge(starts[k])
+    dh64 = np.array(dh64)
+    for lat in lats:      # warm-up
+        lat.trajectory("fg", 0.125, 1.0, refresh=True, u_accept=-1.0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res_s = [[lat.trajectory("fg", 0.125, 1.0, refresh=True, u_accept=-1.0) for lat in lats]
+             for _ in range(n_traj)]
+    ts = time.perf_counter() - t0
+    for lat in lats:
+        lat.close()
     s1 = stats(res_s, ts)
-    return {"workload": "64 pure-gauge chains, L^4 with L drawn from {4,6,8,10,12} and beta from U[5.7,6.2] "
-                        "(seed 4), FG tau=1 dt=1/8", "sites_total": sites,
-            "batched_fp32_graphs": dict(b, tile=tile),
-            "one_chain_per_launch_fp64": s1,
-            "speedup_accepted_per_s": b["accepted_traj_per_s"] / s1["accepted_traj_per_s"],
-            "trajectories_timed_per_chain": n_traj}
+
+    # the FP64 oracle on the smallest chains (same links and momenta)
+    from oracle import integrators as it
+    small = sorted(range(64), key=lambda k: (extents[k], k))[:n_oracle]
+    dh_or = {}
+    for k in small:
+        _, _, h0, h1 = it.trajectory(it.GaugeSystem(float(betas[k])), it.Integrator("fg"), starts[k], moms[k],
+                                     0.125, 1.0)
+        dh_or[k] = h1 - h0
+    out = {"workload": "64 pure-gauge chains, L^4 with L drawn from {4,6,8,10,12} and beta from U[5.7,6.2] "
+                       "(seed 4), FG tau=1 dt=1/8", "sites_total": sites,
+           "one_chain_per_launch_fp64": s1, "trajectories_timed_per_chain": n_traj,
+           "fp64_path_vs_oracle_max_abs_dH_error": float(max(abs(dh64[k] - dh_or[k]) for k in small)),
+           "oracle_chains": [int(extents[k]) for k in small]}
+    for prec in ("df64", "fp32"):
+        bat = fg.Batch(dims_list, betas, precision=prec, tile=0, use_graphs=True, seed=500 + rank, stream=stream)
+        for k in range(64):
+            bat.set_gauge(k, starts[k])
+            bat.set_momenta(k, moms[k])
+        r0 = bat.trajectory("fg", 0.125, 1.0, refresh=False, always_accept=False)
+        dh = np.array([r["dH"] for r in r0])
+        for k in range(64):
+            bat.set_gauge(k, starts[k])
+        for _ in range(2):   # autotune, graph capture, warm-up
+            bat.trajectory("fg", 0.125, 1.0, refresh=True, always_accept=False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res_b = [bat.trajectory("fg", 0.125, 1.0, refresh=True, always_accept=False) for _ in range(n_traj)]
+        tb = time.perf_counter() - t0
+        b = stats(res_b, tb)
+        b["tile"] = bat.tile()
+        bat.close()
+        err = np.abs(dh - dh64)
+        b["dH_error_vs_fp64_path"] = {"max": float(err.max()), "median": float(np.median(err)),
+                                      "max_by_L": {str(L): float(err[extents == L].max()) for L in (4, 6, 8, 10, 12)
+                                                   if (extents == L).any()}}
+        b["dH_error_vs_oracle_max"] = float(max(abs(dh[k] - dh_or[k]) for k in small))
+        b["meets_1e-6"] = bool(err.max() <= 1e-6 and b["dH_error_vs_oracle_max"] <= 1e-6)
+        b["speedup_accepted_per_s_vs_fp64_one_chain"] = b["accepted_traj_per_s"] / s1["accepted_traj_per_s"]
+        out[f"batched_{prec}_graphs"] = b
+    return out
+
+
+def fixed_acceptance_comparison(lat, torch, n_stat=200, n_tune=30, target=0.75):
+    """FG against Omelyan at matched acceptance on the running chain (section
+    5 compares integrators at equal acceptance, Fig. 2 at 75%): for each
+    integrator the fewest steps per unit trajectory whose acceptance over
+    n_tune trajectories reaches the target (else the most steps tried),
+    then n_stat trajectories there.  Reports acceptance and <exp(-dH)> with
+    their standard errors, accepted trajectories/s and force evaluations per
+    accepted trajectory (the paper's cost model counts force/solve
+    evaluations), and the FG / Omelyan ratio of accepted trajectories/s with
+    its error from the two acceptances."""
+    out = {}
+    for integ, steps in (("fg", (5, 6, 7, 8, 10)), ("omelyan", (20, 24, 28, 32, 40))):
+        chosen, tune = steps[-1], {}
+        for n in steps:
+            rs = [lat.trajectory(integ, 1.0 / n, TAU, refresh=True, u_accept=-1.0) for _ in range(n_tune)]
+            a = float(np.mean([r["accepted"] for r in rs]))
+            tune[str(n)] = a
+            if a >= target:
+                chosen = n
+                break
+        dt = 1.0 / chosen
+        torch.cuda.synchronize()
+        c0 = time.perf_counter()
+        rs = [lat.trajectory(integ, dt, TAU, refresh=True, u_accept=-1.0) for _ in range(n_stat)]
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - c0
+        acc = np.array([r["accepted"] for r in rs], dtype=float)
+        e = np.exp(-np.array([r["dH"] for r in rs]))
+        a = float(acc.mean())
+        a_err = float(np.sqrt(max(a * (1 - a), 1e-12) / len(rs)))
+        out[integ] = {"md_steps": chosen, "dt": dt, "forces_per_trajectory": rs[0]["n_force"],
+                      "trajectories": len(rs), "acceptance": a, "acceptance_err": a_err,
+                      "mean_exp_minus_dH": float(e.mean()), "mean_exp_minus_dH_err": float(e.std(ddof=1) / np.sqrt(len(e))),
+                      "trajectories_per_s": len(rs) / secs, "accepted_per_s": a * len(rs) / secs,
+                      "accepted_per_s_err": a_err * len(rs) / secs,
+                      "forces_per_accepted_trajectory": rs[0]["n_force"] / max(a, 1e-12),
+                      "tuning_acceptance": tune}
+    f, o = out["fg"], out["omelyan"]
+    ratio = f["accepted_per_s"] / o["accepted_per_s"]
+    rel = np.hypot(f["acceptance_err"] / f["acceptance"], o["acceptance_err"] / o["acceptance"])
+    out["fg_over_omelyan_accepted_per_s"] = {"ratio": ratio, "err": float(ratio * rel)}
+    cost = o["forces_per_accepted_trajectory"] / f["forces_per_accepted_trajectory"]
+    out["omelyan_over_fg_forces_per_accepted"] = {"ratio": cost, "err": float(cost * rel)}
+    out["target_acceptance"] = target
+    return out
+
+
+def headline_precision_check(fg, lat, stream, args, seed=91):
+    """dH of one trajectory of the benchmark chain's configuration (its
+    current links, fresh momenta) in its own precision, in double-float and
+    in FP64 (the FP64 path is pinned to the oracle): the error against FP64.
+    The chain's links are put back afterwards."""
+    u = lat.get_gauge()
+    p = inputs.gaussian_momenta(lat.dims, seed)
+    dh = {}
+    for prec in dict.fromkeys((args.precision, "df64", "fp64")):
+        if prec == args.precision:
+            x = lat
+        else:
+            x = fg.Lattice(lat.dims, BETA, precision=prec, link_reals=18, seed=92, stream=stream)
+        x.set_gauge(u)
+        x.set_momenta(p)
+        dh[prec] = x.trajectory(args.integrator, args.dt, TAU, refresh=False, u_accept=0.0)["dH"]
+        if x is not lat:
+            x.close()
+    lat.set_gauge(u)
+    return {"dH_fp64": dh["fp64"],
+            "dH_error_vs_fp64": {k: abs(v - dh["fp64"]) for k, v in dh.items() if k != "fp64"},
+            "note": "one trajectory from the benchmark chain's links after the timed region, momenta seed "
+                    f"{seed}; each precision from the same links and momenta"}
 
 
 def serving_measurement(duration_s=4.0, rate_hz=200.0, slots=8, budget_gb=24.0):
@@ -688,9 +831,13 @@ def run_ours(args):
             "algorithmic_gbs": bytes_per_launch / avg_launch_s / 1e9,
             "share_of_step": force_ms / elapsed_ms}
 
-    # ---------------------------------------------------------------- FG vs Omelyan at matched acceptance
+    # ---------------------------------------------------------------- dH error of the headline precision
+    headline_dh = headline_precision_check(fg, lat, stream.cuda_stream, args) if not args.no_compare else None
+
+    # ---------------------------------------------------------------- FG vs Omelyan
     # Section 5 compares integrators at equal acceptance; on this chain: FG at
-    # the configured dt and at dt/2, Omelyan at the configured 0.125 and 1/16.
+    # the configured dt and at dt/2, Omelyan at the configured 0.125 and 1/16,
+    # then both tuned to ~75% acceptance with statistics.
     comparison = None
     if not args.no_compare:
         comparison = {}
@@ -705,10 +852,11 @@ def run_ours(args):
             rs = [lat.trajectory(integ, dt, TAU, refresh=True, u_accept=-1.0) for _ in range(args.compare_steps)]
             torch.cuda.synchronize()
             secs = time.perf_counter() - c0
-            acc = float(np.mean([r["accepted"] for r in rs]))
-            comparison[name] = {"dt": dt, "forces_per_trajectory": rs[0]["n_force"], "acceptance": acc,
+            a_cmp = float(np.mean([r["accepted"] for r in rs]))
+            comparison[name] = {"dt": dt, "forces_per_trajectory": rs[0]["n_force"], "acceptance": a_cmp,
                                 "mean_dH": float(np.mean([r["dH"] for r in rs])),
-                                "trajectories_per_s": len(rs) / secs, "accepted_per_s": acc * len(rs) / secs}
+                                "trajectories_per_s": len(rs) / secs, "accepted_per_s": a_cmp * len(rs) / secs}
+        comparison["fixed_acceptance"] = fixed_acceptance_comparison(lat, torch)
 
     # ---------------------------------------------------------------- e2e through host buffers
     e2e = None
@@ -796,7 +944,7 @@ def run_ours(args):
         cfg.update({"acceptance": acc, "mean_exp_minus_dH": emdh,
                     "dH": [round(r["dH"], 6) for r in results[:8]],
                     "forces_per_trajectory": n_force, "md_steps": nsteps,
-                    "plaquette": lat.plaquette()})
+                    "plaquette": lat.plaquette(), "dH_precision_check": headline_dh})
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
