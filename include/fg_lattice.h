@@ -64,7 +64,7 @@ typedef enum {
   FG_ENOMEM = 2,     /* device or pinned-host allocation failed */
   FG_ECUDA = 3,      /* CUDA runtime error */
   FG_ENOCONV = 4,    /* CG reached cg_maxiter without converging */
-  FG_ETIMEOUT = 5,   /* a host wait exceeded its limit */
+  FG_ETIMEOUT = 5,   /* a host wait exceeded its limit (fg_set_wait_limit) */
   FG_ESTATE = 6      /* call not valid in the handle's state (e.g. no pseudofermion) */
 } fg_status;
 
@@ -262,6 +262,15 @@ fg_status fg_trajectories_host_momenta(fg_lattice *h, fg_integrator integ, doubl
 /* out = Mhat in (dagger = 0) or Mhat^dagger in (dagger = 1). */
 fg_status fg_apply_mhat(fg_lattice *h, const double *host_in_even, double *host_out_even,
                         int dagger);
+/* The same operator as the inner CG iterations apply it (section 4's
+ * calM = Mhat^dagger Mhat is built from it): the input rounded to the inner
+ * precision, the two Dslash launches of Mhat in that precision, the output
+ * widened to FP64.  Inner precision: FP32 links and spinors for FG_FP32;
+ * half-precision links (a copy made for the call) and half-precision spinors
+ * scaled by sigma, sigma^2 = |in|^2 / n, for FG_FP32_FP16CG; FP64 for FG_FP64
+ * (then equal to fg_apply_mhat).  FG_ESTATE for pure-gauge handles. */
+fg_status fg_apply_mhat_inner(fg_lattice *h, const double *host_in_even, double *host_out_even,
+                              int dagger);
 /* Solve Mhat^dagger Mhat x = b to cg_tol with x0 = 0. */
 fg_status fg_cg_solve(fg_lattice *h, const double *host_b_even, double *host_x_even,
                       fg_cg_result *res);
@@ -298,6 +307,16 @@ long long fg_launch_count(const fg_lattice *h);
 
 /* Block until all work queued on the handle's stream has finished. */
 fg_status fg_sync(fg_lattice *h);
+
+/* Upper limit, in seconds, on every wait of the host for this handle's GPU
+ * work (0, the default: no limit).  A call whose wait would last longer
+ * returns FG_ETIMEOUT and leaves its work queued on the GPU; the handle's
+ * fields and results are then undefined until a later fg_sync (with a
+ * larger limit, or 0) succeeds.  The copy-stream drain at the end of
+ * fg_trajectories_host_momenta (the host arrays must not be read after it
+ * returns) and fg_lattice_destroy wait without limit.  FG_EINVAL for a
+ * negative or NaN limit. */
+fg_status fg_set_wait_limit(fg_lattice *h, double seconds);
 
 /* Device bytes held by the handle. */
 unsigned long long fg_device_bytes(const fg_lattice *h);
@@ -354,6 +373,8 @@ fg_status fg_batch_trajectory(fg_batch *b, fg_integrator integ, double dt, doubl
 fg_status fg_batch_tile(const fg_batch *b, int *tile);
 /* Kernels launched by the batch (a graph launch counts its kernels). */
 long long fg_batch_launch_count(const fg_batch *b);
+/* Limit on the host waits of a batch, as fg_set_wait_limit. */
+fg_status fg_batch_set_wait_limit(fg_batch *b, double seconds);
 
 /* ------------------------------------------------------------------------
  * Allocation-free action sums (no handle).
@@ -380,11 +401,13 @@ long long fg_batch_launch_count(const fg_batch *b);
  * itself allocates nothing (no cudaMalloc, cudaFree or allocating library
  * routine).  The first call on each device looks up the array's device
  * address with that device current and caches it, so make that first call
- * before any stream capture.  Every call shares the array and overwrites
- * each entry it later reads, so nothing carries over from the previous
- * call; calls whose kernels overlap on the GPU (other streams or other host
- * threads on the same device) race on the array and must be serialised by
- * the caller.
+ * before any stream capture; calls outside a capture look it up again (a
+ * device reset may move the array), calls inside one use the cached value,
+ * so after a device reset make one call outside capture before capturing.
+ * Every call shares the array and overwrites each entry it later reads, so
+ * nothing carries over from the previous call; calls whose kernels overlap
+ * on the GPU (other streams or other host threads on the same device) race
+ * on the array and must be serialised by the caller.
  *
  * Errors: FG_EINVAL for a null links/out/dims pointer, an odd or < 2 extent,
  * or more than FG_NOALLOC_MAX_SITES sites (nothing is queued); FG_ECUDA if

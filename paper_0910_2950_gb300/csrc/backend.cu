@@ -202,6 +202,47 @@ class Backend final : public IBackend {
       return download_spinor(ax64_, out);
     }
   }
+  // Mhat (or Mhat^dagger) by the inner solver's operator: the Dslash launches
+  // of a CG iteration on vectors in the inner precision (FP32, or half
+  // precision scaled by sigma with sigma^2 = |in|^2 / n on the half-precision
+  // copy of the links), the input rounded to that precision and the output
+  // widened to FP64.  FP64 handles iterate in FP64: apply_mhat.
+  fg_status apply_mhat_inner(const double* in, double* out, int dagger) override {
+    if constexpr (!kFerm) {
+      return no_fermions();
+    } else {
+      if (!kMixed) return apply_mhat(in, out, dagger);
+      const int n = nvec();
+      const double k2 = h_->prm.kappa * h_->prm.kappa;
+      fg_status s = upload_spinor(in, b64_);
+      if (s != FG_OK) return s;
+      const void* Uin = U_;
+      if (half_links_) {
+        const int nbv = vec_blocks(n);
+        double* bbp = &mapped_->bb;
+        if ((s = run(KC_CG_BLAS, [&] { return launch_dot64(b64_, b64_, part_rr_, n, st_); })) != FG_OK) return s;
+        if ((s = run(KC_REDUCE, [&] { return launch_cg_init_h16(part_rr_, nbv, cgd_, 0.0, bbp, n, st_); })) != FG_OK)
+          return s;
+        if ((s = run(KC_CG_BLAS, [&] { return launch_scale_to_h16(rs_, b64_, cgd_, n, st_); })) != FG_OK) return s;
+        if ((s = run(KC_CONVERT, [&] { return launch_links_to_half<NC>(g_, U_, U16_, st_); })) != FG_OK) return s;
+        Uin = U16_;
+      } else {
+        if ((s = run(KC_CG_BLAS, [&] { return launch_convert<R, double>(rs_, b64_, nullptr, n, st_); })) != FG_OK)
+          return s;
+      }
+      if ((s = run(KC_DSLASH, [&] {
+             return inner_dslash(to_, rs_, nullptr, nullptr, Uin, 1, dagger, 0, 1.0, nullptr, false);
+           })) != FG_OK)
+        return s;
+      if ((s = run(KC_DSLASH, [&] { return inner_dslash(te_, to_, rs_, nullptr, Uin, 0, dagger, 1, -k2, nullptr, false); })) !=
+          FG_OK)
+        return s;
+      if (half_links_) s = run(KC_CONVERT, [&] { return launch_h16_to_double_scaled(ax64_, te_, cgd_, n, st_); });
+      else s = run(KC_CONVERT, [&] { return launch_convert<double, R>(ax64_, te_, nullptr, n, st_); });
+      if (s != FG_OK) return s;
+      return download_spinor(ax64_, out);
+    }
+  }
   fg_status cg_solve(const double* b, double* x, fg_cg_result* r) override {
     if constexpr (!kFerm) {
       return no_fermions();
@@ -468,8 +509,9 @@ class Backend final : public IBackend {
     return h_->fail(FG_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
   }
   fg_status sync() {
-    cudaError_t e = cudaStreamSynchronize(st_);
-    if (e != cudaSuccess) return h_->fail(FG_ECUDA, cudaGetErrorString(e));
+    std::string why;
+    const fg_status s = host_wait_stream(st_, h_->wait_limit_s, &why);
+    if (s != FG_OK) return h_->fail(s, why);
     return FG_OK;
   }
 
@@ -958,13 +1000,16 @@ class Backend final : public IBackend {
   // Dslash of the inner iterations: on the FP32 links, or with
   // FG_FP32_FP16CG on their half-precision copy (then U is that copy) and
   // half-precision spinors.
+  // `solver` = false: outside a solve (no early return on the solver's
+  // converged flag).
   cudaError_t inner_dslash(void* out, const void* in, const void* x, const void* pdot, const void* U, int out_par,
-                           int dag, int mode, double b, double* partial) {
+                           int dag, int mode, double b, double* partial, bool solver = true) {
+    CgDev* const cgd = solver ? cgd_ : nullptr;
     if constexpr (kMixed) {
       if (half_links_)
-        return launch_dslash_h16<Half16, NC>(g_, out, in, x, pdot, U, out_par, dag, mode, b, partial, cgd_, st_);
+        return launch_dslash_h16<Half16, NC>(g_, out, in, x, pdot, U, out_par, dag, mode, b, partial, cgd, st_);
     }
-    return launch_dslash<R, NC, R>(g_, out, in, x, pdot, U, out_par, dag, mode, b, partial, cgd_, st_);
+    return launch_dslash<R, NC, R>(g_, out, in, x, pdot, U, out_par, dag, mode, b, partial, cgd, st_);
   }
 
   // One CG iteration in the inner precision R: 4 Dslash + 2 vector kernels,
@@ -1249,7 +1294,8 @@ class Backend final : public IBackend {
         if (cudaEventRecord(ev_[slot], st_) != cudaSuccess) return cuda_fail("event");
         if (pending >= 0) {
           // wait for the batch before this one; the GPU keeps working on this one
-          if (cudaEventSynchronize(ev_[pending]) != cudaSuccess) return cuda_fail("event sync");
+          std::string why;
+          if ((s = host_wait_event(ev_[pending], h_->wait_limit_s, &why)) != FG_OK) return h_->fail(s, why);
           if (bb < 0.0) {
             know_bb();
             maxrr = bb;

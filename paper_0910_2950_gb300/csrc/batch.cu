@@ -279,6 +279,7 @@ struct fg_batch {
   bool own_stream = false;
   std::string err;
   long long launches = 0;
+  double wait_limit_s = 0.0;   // limit on host waits (0: none), fg_batch_set_wait_limit
   std::unique_ptr<fg::IBatch> impl;
   fg_status fail(fg_status s, const std::string& m) {
     err = m;
@@ -588,8 +589,9 @@ class Batch final : public IBatch {
     return b_->fail(FG_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
   }
   fg_status sync() {
-    cudaError_t e = cudaStreamSynchronize(st_);
-    if (e != cudaSuccess) return b_->fail(FG_ECUDA, cudaGetErrorString(e));
+    std::string why;
+    const fg_status s = host_wait_stream(st_, b_->wait_limit_s, &why);
+    if (s != FG_OK) return b_->fail(s, why);
     return FG_OK;
   }
   template <class Fn>
@@ -798,7 +800,12 @@ class Batch final : public IBatch {
           return s;
         }
         cudaEventRecord(b, st_);
-        if (cudaEventSynchronize(b) != cudaSuccess) return cuda_fail("autotune sync");
+        std::string why;
+        if ((s = host_wait_event(b, b_->wait_limit_s, &why)) != FG_OK) {
+          cudaEventDestroy(a);
+          cudaEventDestroy(b);
+          return b_->fail(s, why);
+        }
         float ms = 0;
         cudaEventElapsedTime(&ms, a, b);
         if (rep > 0) tmin = std::min(tmin, ms);  // first repetition warms up
@@ -945,5 +952,11 @@ fg_status fg_batch_tile(const fg_batch* b, int* tile) {
   return FG_OK;
 }
 long long fg_batch_launch_count(const fg_batch* b) { return b ? b->launches : -1; }
+fg_status fg_batch_set_wait_limit(fg_batch* b, double seconds) {
+  if (!b) return FG_EINVAL;
+  if (!(seconds >= 0.0)) return b->fail(FG_EINVAL, "wait limit must be >= 0");
+  b->wait_limit_s = seconds;
+  return FG_OK;
+}
 
 }  // extern "C"

@@ -54,9 +54,15 @@ __device__ __forceinline__ DF operator+(DF a, DF b) {
 __device__ __forceinline__ DF& operator+=(DF& a, DF b) { return a = a + b; }
 __device__ __forceinline__ DF operator-(DF a) { return DF(-a.hi, -a.lo); }
 __device__ __forceinline__ DF operator-(DF a, DF b) { return a + (-b); }
+// Products keep the lo * lo term: it is ~2^-48 of the result, but for a
+// square it is never negative, so dropping it (the usual "sloppy" product)
+// biases every x * x low by ~6e-16 on average; in the exponential of the
+// link update that made each drift shrink |U|^2 by ~4e-15, which moved the
+// dH of a 32^4 trajectory by ~7e-7.
 __device__ __forceinline__ DF operator*(DF a, DF b) {
   const float p = __fmul_rn(a.hi, b.hi);
   float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.lo, b.lo, e);
   e = __fmaf_rn(a.hi, b.lo, e);
   e = __fmaf_rn(a.lo, b.hi, e);
   return df_fast_two_sum(p, e);
@@ -73,6 +79,7 @@ __device__ __forceinline__ DF fma(DF a, DF b, DF c) {
   const float p = __fmul_rn(a.hi, b.hi);
   float e = __fmaf_rn(a.hi, b.hi, -p);
   const DF s = df_two_sum(p, c.hi);
+  e = __fmaf_rn(a.lo, b.lo, e);
   e = __fmaf_rn(a.hi, b.lo, e);
   e = __fmaf_rn(a.lo, b.hi, e);
   e = __fadd_rn(e, __fadd_rn(s.lo, c.lo));
@@ -92,27 +99,39 @@ __device__ __forceinline__ DF operator*(DF a, float f) {
   e = __fmaf_rn(a.lo, f, e);
   return df_fast_two_sum(p, e);
 }
-// Quotient by one correction step: q1 = a.hi / b.hi, then the remainder
-// a - q1 b in double-float divided by b.hi gives the low part (~2^-47 relative).
+// Quotient by two correction steps: q1 = a.hi / b.hi, q2 = r1.hi / b.hi
+// with the remainder r1 = a - q1 b, q3 = r2.hi / b.hi with r2 = r1 - q2 b.
+// One step is accurate to ~2^-47 but not unbiased: dividing r1 (which
+// contains -q1 b.lo) by b.hi instead of b leaves -q (b.lo / b.hi)^2, never
+// positive, so 1/x came out low by 6.5e-16 on average and every exp(iA)
+// (its coefficients divide by 9u^2 - w^2) shrank the links.  The second
+// step's own error is ~2^-72.
 __device__ __forceinline__ DF operator/(DF a, DF b) {
   const float q1 = __fdiv_rn(a.hi, b.hi);
-  const DF r = a - b * q1;
-  return df_fast_two_sum(q1, __fdiv_rn(r.hi, b.hi));
+  const DF r1 = a - b * q1;
+  const float q2 = __fdiv_rn(r1.hi, b.hi);
+  const DF r2 = r1 - b * q2;
+  const DF q = df_fast_two_sum(q1, q2);
+  return df_add_f(q, __fdiv_rn(r2.hi, b.hi));
 }
 // Ordering of normalised double-floats (|lo| <= ulp(hi) / 2).
 __device__ __forceinline__ bool operator<(DF a, DF b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
 __device__ __forceinline__ bool operator>(DF a, DF b) { return b < a; }
 __device__ __forceinline__ DF fabs(DF a) { return (a.hi < 0.0f || (a.hi == 0.0f && a.lo < 0.0f)) ? -a : a; }
-// Square root: s = sqrt(a.hi) in FP32, then one Newton step on s^2 = a with
+// Square root: s = sqrt(a.hi) in FP32, then a Newton step on s^2 = a with
 // the residual a - s^2 formed exactly (s^2 = p + e by the FMA product, and
-// a.hi - p is exact by Sterbenz's lemma).
+// a.hi - p is exact by Sterbenz's lemma), then a second one in double-float.
+// One step leaves an error of one sign (a Newton step for sqrt always lands
+// above the root, here by ~2^-49 relative); the second removes it.
 __device__ __forceinline__ DF sqrt(DF a) {
   if (!(a.hi > 0.0f)) return DF(0.0f);
   const float s = __fsqrt_rn(a.hi);
   const float p = __fmul_rn(s, s);
   const float e = __fmaf_rn(s, s, -p);
   const float d = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, p), e), a.lo);
-  return df_fast_two_sum(s, __fdiv_rn(d, __fadd_rn(s, s)));
+  const DF y = df_fast_two_sum(s, __fdiv_rn(d, __fadd_rn(s, s)));
+  const DF r = a - y * y;
+  return y + DF(__fdiv_rn(r.hi, __fadd_rn(y.hi, y.hi)));
 }
 
 // sin and cos of a double-float argument.  Arguments beyond pi/4 are first
@@ -120,11 +139,15 @@ __device__ __forceinline__ DF sqrt(DF a) {
 // into three floats; the first two products are formed exactly), then the
 // Taylor series run on y / 2^k, |y / 2^k| <= 1/8, followed by k double-angle
 // steps (sin 2y = 2 sin y cos y, cos 2y = 1 - 2 sin^2 y), and the quadrant
-// n mod 4 permutes the result.  The series stop at y^9 and y^8: the first
-// omitted terms are below 3e-16 of the result.  Each doubling at most
-// doubles the absolute error and k <= 3 after the reduction, so the error
-// stays near 3e-14 plus the 2^-48 |x| that the argument itself carries.
-// Arguments here are rotation angles of link updates, usually below 1.
+// n mod 4 permutes the result.  The series stop at y^11 and y^10: the first
+// omitted terms are below 3e-20 of the result.  A truncation error has one
+// sign, so it must stay far below the rounding: stopping one term earlier
+// (cos short by up to 2.6e-16) made every exp(iA) shrink the links by
+// ~1e-15, and over 16 drifts of 4.2 M links that moved S by ~1e-6 on 32^4.
+// Each doubling at most doubles the absolute rounding error and k <= 3
+// after the reduction, so the error stays near 3e-14 plus the 2^-48 |x| that
+// the argument itself carries.  Arguments here are rotation angles of link
+// updates, usually below 1.
 __device__ __forceinline__ void sincos(DF x, DF* s, DF* c) {
   int quadrant = 0;
   if (fabsf(x.hi) > 0.785398163f) {
@@ -143,13 +166,15 @@ __device__ __forceinline__ void sincos(DF x, DF* s, DF* c) {
   const float sc = __uint_as_float((uint32_t)(127 - k) << 23);  // 2^-k, exact scaling
   const DF y(__fmul_rn(x.hi, sc), __fmul_rn(x.lo, sc));
   const DF z = y * y;
-  constexpr DF s3(-1.0 / 6.0), s5(1.0 / 120.0), s7(-1.0 / 5040.0), s9(1.0 / 362880.0);
-  constexpr DF c4(1.0 / 24.0), c6(-1.0 / 720.0), c8(1.0 / 40320.0);
-  DF ps = fma(z, s9, s7);
+  constexpr DF s3(-1.0 / 6.0), s5(1.0 / 120.0), s7(-1.0 / 5040.0), s9(1.0 / 362880.0), s11(-1.0 / 39916800.0);
+  constexpr DF c4(1.0 / 24.0), c6(-1.0 / 720.0), c8(1.0 / 40320.0), c10(-1.0 / 3628800.0);
+  DF ps = fma(z, s11, s9);
+  ps = fma(z, ps, s7);
   ps = fma(z, ps, s5);
   ps = fma(z, ps, s3);
   DF sn = fma(y * z, ps, y);
-  DF pc = fma(z, c8, c6);
+  DF pc = fma(z, c10, c8);
+  pc = fma(z, pc, c6);
   pc = fma(z, pc, c4);
   DF cs = fma(z * z, pc, DF(1.0f) - z * 0.5f);
   for (int i = 0; i < k; ++i) {
@@ -286,7 +311,7 @@ __device__ __forceinline__ M3<DF> expi_herm<DF>(const M3<DF>& a) {
     DF xi0;
     if (w2.hi < 0.0025f) {
       // |w| < 0.05: sin(w)/w from its series in w^2 (first omitted term
-      // below 1e-16), not from a quotient of small numbers
+      // below 3e-21), not from a quotient of small numbers
       constexpr DF x2(-1.0 / 6.0), x4(1.0 / 120.0), x6(-1.0 / 5040.0), x8(1.0 / 362880.0);
       DF q = fma(w2, x8, x6);
       q = fma(w2, q, x4);

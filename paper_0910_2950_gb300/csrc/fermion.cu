@@ -725,6 +725,17 @@ __global__ void __launch_bounds__(kVecThreads) scale_to_h16_kernel(__half2* __re
   }
 }
 
+// dst (FP64) = sigma src (half-precision inner vector in scaled units).
+__global__ void __launch_bounds__(kVecThreads) h16_to_double_scaled_kernel(double2* __restrict__ dst,
+                                                                          const __half2* __restrict__ src,
+                                                                          const CgDev* __restrict__ cgd, int n) {
+  const double sg = sqrt(cgd->sigma2);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float2 v = __half22float2(src[i]);
+    dst[i] = make_double2(sg * (double)v.x, sg * (double)v.y);
+  }
+}
+
 __global__ void __launch_bounds__(kVecThreads) ru_accumulate_df_scaled_kernel(float4* __restrict__ x,
                                                                               float2* __restrict__ xs,
                                                                               const CgDev* __restrict__ cgd,
@@ -1087,6 +1098,10 @@ cudaError_t launch_cg_init_h16(const double* part, int nparts, CgDev* cgd, doubl
 }
 cudaError_t launch_scale_to_h16(void* rs, const void* b64, const CgDev* cgd, int n, cudaStream_t st) {
   scale_to_h16_kernel<<<vec_blocks(n), kVecThreads, 0, st>>>((__half2*)rs, (const double2*)b64, cgd, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_h16_to_double_scaled(void* dst64, const void* src16, const CgDev* cgd, int n, cudaStream_t st) {
+  h16_to_double_scaled_kernel<<<vec_blocks(n), kVecThreads, 0, st>>>((double2*)dst64, (const __half2*)src16, cgd, n);
   return cudaGetLastError();
 }
 cudaError_t launch_ru_accumulate_df_scaled(void* xdf, void* xs, const CgDev* cgd, int n, cudaStream_t st) {

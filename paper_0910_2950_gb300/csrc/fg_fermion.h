@@ -96,6 +96,8 @@ cudaError_t launch_cg_init_h16(const double* part, int nparts, CgDev* cgd, doubl
                                cudaStream_t st);
 // rs = b / sigma (b FP64).
 cudaError_t launch_scale_to_h16(void* rs, const void* b64, const CgDev* cgd, int n, cudaStream_t st);
+// dst (FP64) = sigma src (half-precision vector in scaled units).
+cudaError_t launch_h16_to_double_scaled(void* dst64, const void* src16, const CgDev* cgd, int n, cudaStream_t st);
 // x (double-float) += sigma x_s; x_s = 0.
 cudaError_t launch_ru_accumulate_df_scaled(void* xdf, void* xs, const CgDev* cgd, int n, cudaStream_t st);
 // r = b - Ax written over Ax (double-float), partials of |r|^2.

@@ -12,6 +12,7 @@
 // with the force at the displaced links (then drifts, if a drift follows).
 #include <cuda_runtime.h>
 
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -19,12 +20,14 @@
 #include <memory>
 #include <new>
 #include <string>
+#include <thread>
 #include <utility>
 #include <vector>
 
 #include "../../include/fg_lattice.h"
 #include "fg_kernels.h"
 #include "fg_runtime.h"
+#include "host_wait.h"
 
 namespace fg {
 
@@ -176,6 +179,52 @@ bool Timer::total(int cls, double* ms, long long* n) {
 }  // namespace fg
 
 using namespace fg;
+
+// ---------------------------------------------------------------------------
+// Bounded host waits (polling in host_wait.h).
+namespace fg {
+namespace {
+double steady_seconds() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+void pause_us(double us) { std::this_thread::sleep_for(std::chrono::duration<double, std::micro>(us)); }
+template <class QueryFn, class SyncFn>
+fg_status wait_bounded(QueryFn query, SyncFn sync, double limit_s, std::string* why) {
+  cudaError_t e = cudaSuccess;
+  if (!(limit_s > 0.0)) {
+    e = sync();
+  } else {
+    const WaitResult w = wait_limited(
+        [&] {
+          e = query();
+          if (e == cudaErrorNotReady) {
+            cudaGetLastError();   // not an error: clear it
+            return 1;
+          }
+          return e == cudaSuccess ? 0 : 2;
+        },
+        steady_seconds, pause_us, limit_s);
+    if (w == WAIT_TIMEOUT) {
+      *why = "a host wait exceeded its limit of " + std::to_string(limit_s) + " s (work left queued)";
+      return FG_ETIMEOUT;
+    }
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *why = cudaGetErrorString(e);
+    return FG_ECUDA;
+  }
+  return FG_OK;
+}
+}  // namespace
+
+fg_status host_wait_stream(cudaStream_t st, double limit_s, std::string* why) {
+  return wait_bounded([&] { return cudaStreamQuery(st); }, [&] { return cudaStreamSynchronize(st); }, limit_s, why);
+}
+fg_status host_wait_event(cudaEvent_t ev, double limit_s, std::string* why) {
+  return wait_bounded([&] { return cudaEventQuery(ev); }, [&] { return cudaEventSynchronize(ev); }, limit_s, why);
+}
+}  // namespace fg
 
 // ---------------------------------------------------------------------------
 // C ABI.
@@ -357,6 +406,12 @@ fg_status fg_apply_mhat(fg_lattice* h, const double* in, double* out, int dagger
   if (h->prm.kappa == 0.0) return h->fail(FG_ESTATE, "pure-gauge handle has no fermions");
   return h->be->apply_mhat(in, out, dagger);
 }
+fg_status fg_apply_mhat_inner(fg_lattice* h, const double* in, double* out, int dagger) {
+  FG_CHECK_HANDLE(h);
+  if (!in || !out) return h->fail(FG_EINVAL, "null spinor pointer");
+  if (h->prm.kappa == 0.0) return h->fail(FG_ESTATE, "pure-gauge handle has no fermions");
+  return h->be->apply_mhat_inner(in, out, dagger);
+}
 fg_status fg_cg_solve(fg_lattice* h, const double* b, double* x, fg_cg_result* res) {
   FG_CHECK_HANDLE(h);
   if (!b || !x) return h->fail(FG_EINVAL, "null spinor pointer");
@@ -386,7 +441,9 @@ fg_status fg_timing_enable(fg_lattice* h, int on) {
 }
 fg_status fg_timing_reset(fg_lattice* h) {
   FG_CHECK_HANDLE(h);
-  if (cudaStreamSynchronize(h->st) != cudaSuccess) return h->fail(FG_ECUDA, "sync failed");
+  std::string why;
+  const fg_status s = host_wait_stream(h->st, h->wait_limit_s, &why);
+  if (s != FG_OK) return h->fail(s, why);
   h->timer.reset();
   return FG_OK;
 }
@@ -397,16 +454,24 @@ fg_status fg_kernel_time(fg_lattice* h, const char* cls, double* ms, long long* 
   for (int i = 0; i < kNumKernelClasses; ++i)
     if (std::strcmp(cls, kKernelClasses[i]) == 0) id = i;
   if (id < 0) return h->fail(FG_EINVAL, "unknown kernel class");
-  cudaError_t e = cudaStreamSynchronize(h->st);
-  if (e != cudaSuccess) return h->fail(FG_ECUDA, cudaGetErrorString(e));
+  std::string why;
+  const fg_status s = host_wait_stream(h->st, h->wait_limit_s, &why);
+  if (s != FG_OK) return h->fail(s, why);
   if (!h->timer.total(id, ms, n)) return h->fail(FG_ECUDA, "event timing failed");
   return FG_OK;
 }
 long long fg_launch_count(const fg_lattice* h) { return h ? h->launches : -1; }
 fg_status fg_sync(fg_lattice* h) {
   FG_CHECK_HANDLE(h);
-  cudaError_t e = cudaStreamSynchronize(h->st);
-  if (e != cudaSuccess) return h->fail(FG_ECUDA, cudaGetErrorString(e));
+  std::string why;
+  const fg_status s = host_wait_stream(h->st, h->wait_limit_s, &why);
+  if (s != FG_OK) return h->fail(s, why);
+  return FG_OK;
+}
+fg_status fg_set_wait_limit(fg_lattice* h, double seconds) {
+  FG_CHECK_HANDLE(h);
+  if (!(seconds >= 0.0)) return h->fail(FG_EINVAL, "wait limit must be >= 0");
+  h->wait_limit_s = seconds;
   return FG_OK;
 }
 unsigned long long fg_device_bytes(const fg_lattice* h) { return h ? h->dev_bytes : 0ULL; }

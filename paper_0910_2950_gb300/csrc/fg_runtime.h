@@ -86,6 +86,7 @@ struct IBackend {
   virtual fg_status trajectories_host_momenta(int integ, double dt, int nsteps, int n, const double* const* host_p8,
                                               const double* u_accept, fg_traj_result* out) = 0;
   virtual fg_status apply_mhat(const double* in, double* out, int dagger) = 0;
+  virtual fg_status apply_mhat_inner(const double* in, double* out, int dagger) = 0;
   virtual fg_status cg_solve(const double* b, double* x, fg_cg_result* r) = 0;
   virtual fg_status reunitarize_all() = 0;
   virtual fg_status random_gauge() = 0;
@@ -105,6 +106,7 @@ struct fg_lattice {
   long long launches = 0;
   unsigned long long dev_bytes = 0;
   unsigned long long accept_draws = 0;
+  double wait_limit_s = 0.0;   // limit on host waits (0: none), fg_set_wait_limit
   fg_status fail(fg_status s, const std::string& m) {
     err = m;
     return s;
@@ -115,4 +117,9 @@ struct fg_lattice {
 namespace fg {
 // Creates the stream and the backend for h->prm (defined in backend.cu).
 fg_status lattice_init(fg_lattice* h);
+// Host waits for a stream or an event, bounded by limit_s seconds (0 or
+// less: unbounded): FG_OK, FG_ETIMEOUT (work left queued) or FG_ECUDA, with
+// a description in *why (defined in fg_lattice.cu).
+fg_status host_wait_stream(cudaStream_t st, double limit_s, std::string* why);
+fg_status host_wait_event(cudaEvent_t ev, double limit_s, std::string* why);
 }  // namespace fg

@@ -109,17 +109,25 @@ __global__ void __launch_bounds__(1024) noalloc_reduce_kernel(const double* __re
   }
 }
 
-// Device address of g_noalloc_partials on the current device, looked up once
-// per device.  In host code the symbol itself is only a stand-in for the
-// device array, so kernels must be given this address instead.
-fg_status partials_address(double** out) {
+// Device address of g_noalloc_partials on the current device.  In host code
+// the symbol itself is only a stand-in for the device array, so kernels must
+// be given this address instead.  It is looked up again on every call made
+// outside stream capture (a device reset reloads the module and may move
+// the array); during a capture the address cached by an earlier call on the
+// device is used.
+fg_status partials_address(cudaStream_t st, double** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
     cudaGetLastError();
     return FG_ECUDA;
   }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    return FG_ECUDA;
+  }
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (g_partials_addr[dev] == nullptr) {
+  if (g_partials_addr[dev] == nullptr || cap == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_partials) != cudaSuccess || p == nullptr) {
       cudaGetLastError();
@@ -140,12 +148,14 @@ extern "C" fg_status fg_action_sums_noalloc(const double* dev_links, const doubl
   for (int i = 0; i < 4; ++i) {
     if (dims[i] < 2 || (dims[i] & 1)) return FG_EINVAL;
     V *= dims[i];
+    // checked after every factor: V <= 2^24 before the next multiply, so the
+    // product cannot overflow
+    if (V > kMaxSites) return FG_EINVAL;
   }
-  if (V > kMaxSites) return FG_EINVAL;
-  double* partials = nullptr;
-  fg_status s = partials_address(&partials);
-  if (s != FG_OK) return s;
   cudaStream_t st = (cudaStream_t)cuda_stream;
+  double* partials = nullptr;
+  fg_status s = partials_address(st, &partials);
+  if (s != FG_OK) return s;
   const int nb = (int)((V + kThreads - 1) / kThreads);
   noalloc_energy_kernel<<<nb, kThreads, 0, st>>>(dev_links, dev_momenta, dims[0], dims[1], dims[2], dims[3], beta,
                                                  partials);

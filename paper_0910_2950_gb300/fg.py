@@ -78,6 +78,7 @@ SIGNATURES = {
     "fg_fg_step": (_i, [_vp, _d]),
     "fg_trajectory": (_i, [_vp, _i, _d, _d, _i, _d, C.POINTER(FgTrajResult)]),
     "fg_apply_mhat": (_i, [_vp, _dp, _dp, _i]),
+    "fg_apply_mhat_inner": (_i, [_vp, _dp, _dp, _i]),
     "fg_cg_solve": (_i, [_vp, _dp, _dp, C.POINTER(FgCgResult)]),
     "fg_reunitarize": (_i, [_vp]),
     "fg_random_gauge": (_i, [_vp]),
@@ -90,6 +91,7 @@ SIGNATURES = {
                                          C.POINTER(FgTrajResult)]),
     "fg_launch_count": (C.c_longlong, [_vp]),
     "fg_sync": (_i, [_vp]),
+    "fg_set_wait_limit": (_i, [_vp, _d]),
     "fg_device_bytes": (C.c_ulonglong, [_vp]),
     "fg_action_sums_noalloc": (_i, [_vp, _vp, C.POINTER(C.c_int), _d, _vp, _vp]),
     "fg_batch_params_default": (_i, [C.POINTER(FgBatchParams)]),
@@ -103,6 +105,7 @@ SIGNATURES = {
     "fg_batch_trajectory": (_i, [_vp, _i, _d, _d, _i, _i, C.POINTER(FgTrajResult)]),
     "fg_batch_tile": (_i, [_vp, C.POINTER(_i)]),
     "fg_batch_launch_count": (C.c_longlong, [_vp]),
+    "fg_batch_set_wait_limit": (_i, [_vp, _d]),
 }
 
 _lib = None
@@ -289,6 +292,12 @@ class Lattice:
         self._call("fg_apply_mhat", _ptr(a), _ptr(out), int(bool(dagger)))
         return out.view(np.complex128).reshape(self.V // 2, 4, 3)
 
+    def apply_mhat_inner(self, x_even, dagger=False):
+        a = _f64(x_even, (self.V // 2, 24))
+        out = np.empty(self.V // 2 * 24, dtype=np.float64)
+        self._call("fg_apply_mhat_inner", _ptr(a), _ptr(out), int(bool(dagger)))
+        return out.view(np.complex128).reshape(self.V // 2, 4, 3)
+
     def cg_solve(self, b_even):
         a = _f64(b_even, (self.V // 2, 24))
         out = np.empty(self.V // 2 * 24, dtype=np.float64)
@@ -320,6 +329,9 @@ class Lattice:
 
     def launch_count(self):
         return int(self._lib.fg_launch_count(self._h))
+
+    def set_wait_limit(self, seconds):
+        self._call("fg_set_wait_limit", float(seconds))
 
     def sync(self):
         self._call("fg_sync")
@@ -406,6 +418,9 @@ class Batch:
         self._call("fg_batch_trajectory", INTEGRATORS[integrator], float(dt), float(tau), int(bool(refresh)),
                    int(bool(always_accept)), res)
         return [{k: getattr(r, k) for k, _ in FgTrajResult._fields_} for r in res]
+
+    def set_wait_limit(self, seconds):
+        self._call("fg_batch_set_wait_limit", float(seconds))
 
     def tile(self):
         t = C.c_int()

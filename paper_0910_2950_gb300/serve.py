@@ -56,6 +56,16 @@ class Request:
     dt: float = 0.125
     tau: float = 1.0
     arrival: float = 0.0          # seconds after the start of the stream
+    # Optional inputs supplied by the client (host arrays in the library's
+    # canonical layouts): `links` replace the chain's links before the
+    # trajectory; `momenta` replace the device momentum refresh, and then
+    # `chi` (Nf = 2 chains) sets the pseudofermion heat bath (without it the
+    # chain keeps its current pseudofermion); `u_accept` in [0, 1) is the
+    # Metropolis uniform, < 0 the chain's own random stream.
+    links: object = None
+    momenta: object = None
+    chi: object = None
+    u_accept: float = -1.0
 
 
 @dataclass
@@ -120,17 +130,18 @@ class TrajectoryServer:
     """Continuous-batching server over resident chains (see the module doc)."""
 
     def __init__(self, slots: int = 4, hbm_budget_bytes: int = 8 << 30, precision: str = "fp32",
-                 cg_tol: float = 1e-10, clock=time.perf_counter, lattice_factory=None):
+                 cg_tol: float = 1e-10, clock=time.perf_counter, lattice_factory=None, cg_tol_action: float = 1e-12):
         if slots < 1:
             raise ValueError("slots must be >= 1")
         self.slots = slots
         self.budget = int(hbm_budget_bytes)
         self.precision = precision
         self.cg_tol = cg_tol
+        self.cg_tol_action = cg_tol_action
         self.clock = clock
         self.lattice_factory = lattice_factory or (
             lambda spec: _fg.Lattice(spec.dims, spec.beta, kappa=spec.kappa, precision=self.precision,
-                                     cg_tol=self.cg_tol, seed=spec.seed))
+                                     cg_tol=self.cg_tol, cg_tol_action=self.cg_tol_action, seed=spec.seed))
         self.chains = {}
         self.resident_bytes = 0
         self.evictions = 0
@@ -193,7 +204,14 @@ class TrajectoryServer:
         lat = ch.lat
         k = ch.traj_index
         lat.set_rng_position(k)
-        r = lat.trajectory(req.integrator, req.dt, req.tau, refresh=True, u_accept=-1.0)
+        if req.links is not None:
+            lat.set_gauge(req.links)
+        refresh = req.momenta is None
+        if not refresh:
+            lat.set_momenta(req.momenta)
+            if req.chi is not None:
+                lat.set_pseudofermion(req.chi)
+        r = lat.trajectory(req.integrator, req.dt, req.tau, refresh=refresh, u_accept=req.u_accept)
         plaq = lat.plaquette()
         end = self.clock() - t0
         with self._lock:

@@ -81,6 +81,60 @@ def test_double_float_handles_are_pure_gauge(lib):
     assert not h.value
 
 
+def test_noalloc_rejects_oversized_extents_before_touching_the_device(lib):
+    # the site count is checked after every factor, so huge extents cannot
+    # overflow the product into an accepted size
+    for dims in ([1 << 30] * 4, [2, 2, 1 << 30, 1 << 30], [1 << 24, 2, 2, 2], [4096, 4096, 2, 2]):
+        d = (C.c_int * 4)(*dims)
+        assert lib.fg_action_sums_noalloc(C.c_void_p(256), None, d, 6.0, C.c_void_p(256), None) == fg.FG_EINVAL
+
+
+def test_wait_limit_validation(lib):
+    assert lib.fg_set_wait_limit(None, 1.0) == fg.FG_EINVAL
+    assert lib.fg_batch_set_wait_limit(None, 1.0) == fg.FG_EINVAL
+
+
+def test_bounded_host_wait_logic(tmp_path):
+    """The polling loop behind fg_set_wait_limit (csrc/host_wait.h), built as
+    plain C++ and driven by a fake clock: work that never finishes times out
+    once the limit has passed, work that finishes or fails is reported as
+    such, and the pause between polls grows to 1 ms."""
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no C++ compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = tmp_path / "wait.cpp"
+    src.write_text(r'''
+#include <cstdio>
+#include "host_wait.h"
+int main() {
+  using namespace fg;
+  double t = 0.0, slept = 0.0, last = 0.0;
+  int polls = 0;
+  auto now = [&] { return t; };
+  auto pause = [&](double us) { t += us * 1e-6; slept += us; last = us; };
+  // never finishes: times out after the limit
+  WaitResult w = wait_limited([&] { ++polls; return 1; }, now, pause, 0.05);
+  if (w != WAIT_TIMEOUT || t < 0.05 || t > 0.052 || last != 1000.0) { std::printf("timeout %d %g %g\n", w, t, last); return 1; }
+  // finishes at the fourth poll
+  t = 0.0; polls = 0;
+  w = wait_limited([&] { return ++polls >= 4 ? 0 : 1; }, now, pause, 0.05);
+  if (w != WAIT_DONE || polls != 4) { std::printf("done %d %d\n", w, polls); return 1; }
+  // an error is reported at once
+  t = 0.0; polls = 0;
+  w = wait_limited([&] { ++polls; return 7; }, now, pause, 0.05);
+  if (w != WAIT_ERROR || polls != 1) { std::printf("error %d %d\n", w, polls); return 1; }
+  std::printf("ok\n");
+  return 0;
+}
+''')
+    exe = tmp_path / "wait"
+    subprocess.run([cxx, "-std=c++17", "-O1", "-I", os.path.join(root, "paper_0910_2950_gb300", "csrc"), str(src),
+                    "-o", str(exe)], check=True)
+    res = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert res.returncode == 0 and res.stdout.strip() == "ok", res.stdout
+
+
 def test_null_handle_calls_fail_cleanly(lib):
     assert lib.fg_refresh_momenta(None) == fg.FG_EINVAL
     assert lib.fg_sync(None) == fg.FG_EINVAL

@@ -67,6 +67,72 @@ def test_apply_mhat_fp32_links_in_fp64_arithmetic(fgmod):
     assert _rel(out, ref) < 1e-13
 
 
+_INNER_CACHE = {}
+
+
+def _inner_case(dims):
+    """Links, an even spinor and the oracle's Mhat / Mhat^dag of it, with the
+    links and spinor also rounded to FP32 (what the FP32 inner operator
+    receives)."""
+    if dims not in _INNER_CACHE:
+        u = inputs.hot_start(dims, 31)
+        psi = _rand_even(dims, 32)
+        u32 = u.astype(np.complex64).astype(np.complex128)
+        psi32 = psi.astype(np.complex64).astype(np.complex128)
+        full, full32 = inputs.unpack_even(psi, dims), inputs.unpack_even(psi32, dims)
+        ref = {d: inputs.pack_even((fe.mhat_dag if d else fe.mhat)(u, KAPPA, full), dims) for d in (0, 1)}
+        ref32 = {d: inputs.pack_even((fe.mhat_dag if d else fe.mhat)(u32, KAPPA, full32), dims) for d in (0, 1)}
+        _INNER_CACHE[dims] = (u, psi, ref, ref32)
+    return _INNER_CACHE[dims]
+
+
+INNER_DIMS = [(6, 4, 2, 6), (4, 4, 4, 4), (16, 16, 16, 32), (24, 24, 24, 48)]
+
+
+@pytest.mark.parametrize("dims", INNER_DIMS)
+@pytest.mark.parametrize("link_reals", [18, 12])
+@pytest.mark.parametrize("dagger", [0, 1])
+def test_inner_dslash_fp32_element_by_element(fgmod, dims, link_reals, dagger):
+    """The FP32 operator of the inner CG iterations (two Dslash launches in
+    FP32 on FP32 spinors) against the oracle's Mhat on the same FP32-rounded
+    links and input: only the arithmetic's rounding differs, ~1e-7 per term
+    over the ~60 terms of a site (bound 2e-6 of the largest entry)."""
+    u, psi, ref, ref32 = _inner_case(dims)
+    with fgmod.Lattice(dims, BETA, kappa=KAPPA, precision="fp32", link_reals=link_reals) as lat:
+        lat.set_gauge(u)
+        out = lat.apply_mhat_inner(psi, dagger=bool(dagger))
+    assert _rel(out, ref32[dagger]) < 2e-6
+    # and against the exact operator on the unrounded inputs
+    assert _rel(out, ref[dagger]) < 5e-6
+
+
+@pytest.mark.parametrize("dims", INNER_DIMS)
+@pytest.mark.parametrize("link_reals", [18, 12])
+@pytest.mark.parametrize("dagger", [0, 1])
+def test_inner_dslash_half_element_by_element(fgmod, dims, link_reals, dagger):
+    """The half-precision inner operator (FG_FP32_FP16CG: half links, half
+    spinors scaled to unit rms, FP32 arithmetic) against the oracle: half
+    precision keeps 11 significant bits (unit roundoff 4.9e-4) in the links,
+    the input and the intermediate vector, bound 5e-3 of the largest entry;
+    a defect in a hop would show at O(1)."""
+    u, psi, ref, _ = _inner_case(dims)
+    with fgmod.Lattice(dims, BETA, kappa=KAPPA, precision="fp32_fp16cg", link_reals=link_reals) as lat:
+        lat.set_gauge(u)
+        out = lat.apply_mhat_inner(psi, dagger=bool(dagger))
+    err = _rel(out, ref[dagger])
+    assert 1e-5 < err < 5e-3, err    # half-precision rounding is visible, and bounded
+
+
+def test_inner_dslash_fp64_is_apply_mhat(fgmod):
+    dims = (6, 4, 2, 6)
+    u, psi, ref, _ = _inner_case(dims)
+    with fgmod.Lattice(dims, BETA, kappa=KAPPA, precision="fp64") as lat:
+        lat.set_gauge(u)
+        out = lat.apply_mhat_inner(psi)
+        assert np.array_equal(out, lat.apply_mhat(psi))
+    assert _rel(out, ref[0]) < 1e-13
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_fp16cg"])
 @pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 2, 6)])
 def test_cg_solve(fgmod, precision, dims):

@@ -223,6 +223,39 @@ def test_fp32_trajectory_dh_close_to_fp64(fgmod, config1_oracle):
     assert abs(r["dH"] - dh_o) < 2e-3, (r["dH"], dh_o)
 
 
+def test_wait_limit_reports_timeout(fgmod):
+    """A host wait limit far below a trajectory's run time: the trajectory
+    call returns FG_ETIMEOUT with its work still queued; without the limit
+    the queue drains and, with its fields set again, the handle gives the
+    same result as a fresh one."""
+    dims = (24, 24, 24, 24)
+    u = inputs.hot_start(dims, 5)
+    p = inputs.gaussian_momenta(dims, 6)
+    with fgmod.Lattice(dims, BETA, precision="fp32") as fresh:
+        fresh.set_gauge(u)
+        fresh.set_momenta(p)
+        ref = fresh.trajectory("fg", 0.125, 1.0, refresh=False, u_accept=0.0)
+    with fgmod.Lattice(dims, BETA, precision="fp32") as lat:
+        lat.set_gauge(u)
+        lat.set_momenta(p)
+        lat.set_wait_limit(1e-6)
+        with pytest.raises(fgmod.FgError) as e:
+            lat.trajectory("fg", 0.125, 1.0, refresh=False, u_accept=0.0)
+        assert e.value.status == fgmod.FG_ETIMEOUT
+        lat.set_wait_limit(0.0)
+        lat.sync()
+        lat.set_gauge(u)
+        lat.set_momenta(p)
+        r = lat.trajectory("fg", 0.125, 1.0, refresh=False, u_accept=0.0)
+    assert r["dH"] == ref["dH"]
+    with pytest.raises(fgmod.FgError):
+        lat2 = fgmod.Lattice((4, 4, 4, 4), BETA)
+        try:
+            lat2.set_wait_limit(-1.0)
+        finally:
+            lat2.close()
+
+
 def test_timing_and_launch_count(fgmod):
     dims = (4, 4, 4, 4)
     with fgmod.Lattice(dims, BETA) as lat:

@@ -1,4 +1,5 @@
-"""Trajectory server on the GPU: each result is the same alone and in the mix.
+"""Trajectory server on the GPU: each result is the same alone and in the mix,
+and the served trajectories agree with the oracle on client-supplied inputs.
 
 The same requests run (a) one at a time, (b) four at a time overlapping on
 the device, and (c) three at a time under an HBM budget that forces chains
@@ -10,7 +11,8 @@ on its own stream with its random streams set to its trajectory index.
 import numpy as np
 import pytest
 
-from paper_0910_2950_gb300 import serve
+from oracle import fermion as fe, integrators as it
+from paper_0910_2950_gb300 import inputs, serve
 
 pytestmark = pytest.mark.gpu
 
@@ -65,6 +67,80 @@ def test_alone_and_in_the_mix_gpu(fgmod):
         assert np.array_equal(l1[k], l4[k]) and np.array_equal(l1[k], l3[k])
     # fermion requests did CG solves; pure-gauge ones did not
     assert all((r.n_solves > 0) == (r.chain == 3) for r in seq)
+
+
+ORACLE_CHAINS = {
+    0: serve.ChainSpec((4, 4, 4, 4), 6.0, 0.0, 21),
+    1: serve.ChainSpec((4, 4, 2, 6), 5.8, 0.0, 22),
+    2: serve.ChainSpec((4, 4, 2, 4), 5.6, 0.13, 23),
+}
+
+
+def _oracle_workload():
+    """Requests with client-supplied inputs: each chain's first request brings
+    its start links, every request its momenta (and chi for the Nf = 2
+    chain); the Metropolis uniform 0 accepts every finite dH."""
+    rng = np.random.default_rng(9)
+    reqs, first = [], set()
+    for i in range(12):
+        c = int(rng.integers(3))
+        spec = ORACLE_CHAINS[c]
+        links = inputs.hot_start(spec.dims, spec.seed) if c not in first else None
+        first.add(c)
+        chi = inputs.gaussian_spinor_even(spec.dims, 300 + i) if spec.kappa > 0 else None
+        reqs.append(serve.Request(i, c, spec, ["omelyan", "fg", "leapfrog"][int(rng.integers(3))],
+                                  [1 / 4, 1 / 8][int(rng.integers(2))], links=links,
+                                  momenta=inputs.gaussian_momenta(spec.dims, 200 + i), chi=chi, u_accept=0.0))
+    return reqs
+
+
+def _oracle_results(reqs):
+    """The oracle's trajectories, each chain's requests in order."""
+    links, out = {}, {}
+    for r in sorted(reqs, key=lambda r: r.rid):
+        spec = r.spec
+        u = r.links if r.links is not None else links[r.chain]
+        if spec.kappa > 0:
+            phi = fe.heatbath_phi(u, spec.kappa, inputs.unpack_even(r.chi, spec.dims))
+            system = fe.FermionSystem(spec.beta, spec.kappa, phi, tol=1e-13)
+        else:
+            system = it.GaugeSystem(spec.beta)
+        u1, _, h0, h1 = it.trajectory(system, it.Integrator(r.integrator), u, r.momenta, r.dt, r.tau)
+        out[r.rid] = (h1 - h0, h0)
+        links[r.chain] = u1
+    return out, links
+
+
+def test_served_results_match_the_oracle(fgmod):
+    """Served requests (FP64) against the oracle on the same inputs, one slot
+    at a time and four at a time, and under a budget that evicts chains to
+    the host: every dH within the FP64 tolerances (1e-12 |H| for pure gauge,
+    1e-6 absolute) and every chain's final links within 1e-10."""
+    reqs = _oracle_workload()
+    ref, ref_links = _oracle_results(reqs)
+    tight = max(serve.footprint_bytes(s, "fp64") for s in ORACLE_CHAINS.values()) * 2 + 4096
+    runs = []
+    for slots, budget in ((1, 8 << 30), (4, 8 << 30), (2, tight)):
+        srv = serve.TrajectoryServer(slots=slots, hbm_budget_bytes=budget, precision="fp64", cg_tol=1e-13,
+                                     cg_tol_action=1e-13)
+        res, _, _ = srv.serve(reqs, realtime=False)
+        links = {c: srv.final_links(c) for c in ORACLE_CHAINS}
+        runs.append((res, links, srv.evictions))
+        srv.close()
+    assert runs[2][2] > 0
+    for res, links, _ in runs:
+        for r in res:
+            dh_o, h0_o = ref[r.rid]
+            tol = 1e-6 if ORACLE_CHAINS[r.chain].kappa > 0 else min(1e-6, 1e-12 * abs(h0_o))
+            assert abs(r.dH - dh_o) <= tol, (r.rid, r.chain, r.dH, dh_o)
+            assert r.accepted == 1
+        for c, u in links.items():
+            assert float(np.max(np.abs(u - ref_links[c]))) < 1e-10, c
+    # alone and in the mix: the same bits
+    for a, b in zip(runs[0][0], runs[1][0]):
+        assert a.dH == b.dH
+    for c in ORACLE_CHAINS:
+        assert np.array_equal(runs[0][1][c], runs[1][1][c])
 
 
 @pytest.mark.parametrize("spec", [serve.ChainSpec((8, 8, 8, 8), 6.0, 0.0, 1),
