@@ -82,6 +82,8 @@ def parse():
     ap.add_argument("--dt", type=float, default=DT)
     ap.add_argument("--link-reals", type=int, default=18)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-full", action="store_true",
+                    help="also time 3 oracle forces and whole oracle trajectories at the benchmark lattice (minutes)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fermion", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
@@ -130,22 +132,6 @@ def rank_seeds(rank: int) -> dict:
 
 
 # ----------------------------------------------------------------------------- oracle legs
-def oracle_trajectory_rate(sample_l: int, target_l: int, integrator: str, dt: float, seed: int):
-    """Time the FP64 CPU oracle on one trajectory of a sample_l^4 lattice and
-    scale it to target_l^4 by the volume ratio (work per trajectory is linear
-    in V).  Returns (trajectories/s at target volume, seconds, description)."""
-    from oracle import integrators as it
-    dims = (sample_l,) * 4
-    u = inputs.hot_start(dims, seed)
-    p = inputs.gaussian_momenta(dims, seed)
-    t0 = time.perf_counter()
-    it.trajectory(it.GaugeSystem(BETA), it.Integrator(integrator), u, p, dt, TAU)
-    secs = time.perf_counter() - t0
-    scale = (sample_l / target_l) ** 4
-    return scale / secs, secs, (f"one {integrator} trajectory (tau={TAU}, dt={dt}) on {sample_l}^4 in "
-                                f"FP64 numpy, {secs:.2f} s, scaled by V ratio ({sample_l}/{target_l})^4")
-
-
 def oracle_unit_times(seed: int = 3):
     """The oracle's per-unit costs on one host core (seconds): a gauge force
     evaluation on 16^4, and on 8^3 x 16 with kappa = 0.158 a full-lattice
@@ -176,27 +162,201 @@ def cpu_cores_used():
     return 1  # numpy batched 3x3 products and eigh run on one thread
 
 
+def cpu_model():
+    """The host CPU's model name and logical core count."""
+    name = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu model")):
+                    name = ln.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if name is None:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+            for ln in out.splitlines():
+                if ln.startswith("Model name"):
+                    name = ln.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return {"model": name or "unknown", "logical_cores": os.cpu_count()}
+
+
+def _single_thread_env():
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+
+
+def _oracle_traj_worker(job):
+    """One oracle trajectory (separate process): returns its wall seconds."""
+    _single_thread_env()
+    sys.path.insert(0, ROOT)
+    from oracle import integrators as it
+    L, integ, dt, seed = job
+    dims = (L,) * 4
+    u = inputs.hot_start(dims, seed)
+    p = inputs.gaussian_momenta(dims, seed)
+    t0 = time.perf_counter()
+    it.trajectory(it.GaugeSystem(BETA), it.Integrator(integ), u, p, dt, TAU)
+    return time.perf_counter() - t0
+
+
+class _OraclePool:
+    """Processes for independent oracle chains, started with spawn (never
+    forked from a process that may hold a CUDA context); a worker that dies
+    raises instead of hanging the pool."""
+
+    def __init__(self, n):
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        self._ex = cf.ProcessPoolExecutor(max_workers=n, mp_context=mp.get_context("spawn"))
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self._ex.shutdown(wait=True)
+        return False
+
+    def map(self, fn, jobs):
+        return list(self._ex.map(fn, jobs))
+
+
+def oracle_pool(n):
+    return _OraclePool(n)
+
+
+def oracle_units_at(L, seed=7):
+    """Measured single-thread oracle costs at L^4 (seconds): one gauge force,
+    one exponential drift of every link and one Wilson action."""
+    from oracle import gauge, integrators as it
+    dims = (L,) * 4
+    # the oracle's cost does not depend on the link values: a cold start
+    # saves drawing 4 V Haar matrices
+    u = inputs.cold_start(dims)
+    p = inputs.gaussian_momenta(dims, seed)
+    out = {}
+    t0 = time.perf_counter()
+    gauge.gauge_force(u, BETA)
+    out["force_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    it.drift(u, p, 0.1)
+    out["drift_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    gauge.wilson_action(u, BETA)
+    out["action_s"] = time.perf_counter() - t0
+    return out
+
+
+def fg_trajectory_units(dt):
+    """Forces, exponentials (drifts and FG displacements) and actions of one
+    FG trajectory of length TAU as the oracle runs it (no merged kicks)."""
+    n = int(round(TAU / dt))
+    return {"force": 4 * n, "exp": 3 * n, "action": 2}
+
+
+def cpu_baseline_measurement(args, pool_procs=None):
+    """The oracle on the host's cores, bounded to ~a minute: (a) one force,
+    one drift and one action measured at the benchmark's lattice on one
+    thread, composed into the FG trajectory's unit counts; (b) independent
+    FG trajectories on a 8^4 sample, one per process across all cores,
+    measured, with their volume-scaled rate at the benchmark lattice
+    labelled as scaled."""
+    units = oracle_units_at(args.lattice)
+    cnt = fg_trajectory_units(args.dt)
+    traj_s = cnt["force"] * units["force_s"] + cnt["exp"] * units["drift_s"] + cnt["action"] * units["action_s"]
+    nproc = pool_procs or os.cpu_count() or 1
+    sample_l = 8
+    with oracle_pool(nproc) as pool:
+        pool.map(_oracle_traj_worker, [(4, args.integrator, args.dt, 1)] * nproc)   # import warm-up
+        t0 = time.perf_counter()
+        per = pool.map(_oracle_traj_worker, [(sample_l, args.integrator, args.dt, 50 + k) for k in range(nproc)])
+        wall = time.perf_counter() - t0
+    all_core_rate = nproc / wall
+    scale = (sample_l / args.lattice) ** 4
+    return {"value": 1.0 / traj_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one gauge force ({units['force_s']:.1f} s), one exponential drift ({units['drift_s']:.1f} s) "
+                      f"and one Wilson action ({units['action_s']:.1f} s) measured at {args.lattice}^4 on one "
+                      f"thread, composed into an FG trajectory (dt={args.dt}): {cnt['force']} forces, "
+                      f"{cnt['exp']} exponentials, {cnt['action']} actions = {traj_s:.0f} s",
+            "unit_times_s": units, "cpu": cpu_model(),
+            "all_cores": {"processes": nproc, "sample": f"{nproc} independent FG trajectories (dt={args.dt}) on "
+                                                        f"{sample_l}^4, one per process, measured",
+                          "trajectories_per_s_measured": all_core_rate, "wall_s": wall,
+                          "mean_trajectory_s": float(np.mean(per)),
+                          "scaled_to_benchmark_lattice": all_core_rate * scale,
+                          "scaling_note": f"x ({sample_l}/{args.lattice})^4: oracle work per trajectory is "
+                                          "linear in the volume"},
+            "unit_times": oracle_unit_times()}
+
+
+def cpu_full_measurement(args):
+    """Section 8(d)'s full oracle timing at the benchmark lattice (minutes):
+    three force evaluations and one whole FG trajectory on one thread, and
+    one trajectory per process on every core at once."""
+    from oracle import gauge, integrators as it
+    dims = (args.lattice,) * 4
+    u = inputs.hot_start(dims, 3)
+    forces = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        gauge.gauge_force(u, BETA)
+        forces.append(time.perf_counter() - t0)
+    one = _oracle_traj_worker((args.lattice, args.integrator, args.dt, 5))
+    nproc = os.cpu_count() or 1
+    with oracle_pool(nproc) as pool:
+        t0 = time.perf_counter()
+        per = pool.map(_oracle_traj_worker, [(args.lattice, args.integrator, args.dt, 60 + k) for k in range(nproc)])
+        wall = time.perf_counter() - t0
+    return {"lattice": args.lattice, "cpu": cpu_model(), "force_s": forces, "trajectory_s_one_thread": one,
+            "trajectories_per_s_one_thread": 1.0 / one,
+            "all_cores": {"processes": nproc, "wall_s": wall, "trajectory_s": per,
+                          "trajectories_per_s": nproc / wall}}
+
+
 def run_reference(args):
+    """The oracle as the reference arm: each step runs one FG trajectory on
+    an 8^4 sample in every host core at once (independent chains, one per
+    process); ms_per_step is that step's measured wall time.  `value` is the
+    measured sample rate scaled to the benchmark lattice by the volume ratio
+    (labelled in `scaled_from`); the measured rate is reported beside it."""
     rank, world, _ = dist_info()
     if rank != 0:
         return 0
-    sample_l = 12
-    rates, secs = [], []
-    for k in range(args.warmup + args.steps):
-        r, s, desc = oracle_trajectory_rate(sample_l, args.lattice, args.integrator, args.dt, 100 + k)
-        if k >= args.warmup:
-            rates.append(r)
-            secs.append(s)
-    value = len(rates) / sum(1.0 / r for r in rates)
+    sample_l = 8
+    nproc = os.cpu_count() or 1
+    walls = []
+    t_run = time.perf_counter()
+    with oracle_pool(nproc) as pool:
+        for k in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            pool.map(_oracle_traj_worker, [(sample_l, args.integrator, args.dt, 100 + k * nproc + j)
+                                           for j in range(nproc)])
+            w = time.perf_counter() - t0
+            if k >= args.warmup:
+                walls.append(w)
+    run_s = time.perf_counter() - t_run
+    step_s = float(np.mean(walls))
+    measured = nproc / step_s
+    scale = (sample_l / args.lattice) ** 4
+    value = measured * scale
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": 1000.0 * step_s, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_config(args),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
-                         "sample": f"each step: {desc}"},
+        "scaled_from": {"sample_lattice": [sample_l] * 4, "trajectories_per_s_measured": measured,
+                        "factor": scale, "note": f"value = measured sample rate x ({sample_l}/{args.lattice})^4 "
+                                                 "(oracle work per trajectory is linear in the volume)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": nproc, "kind": "oracle", "cpu": cpu_model(),
+                         "sample": f"each step: {nproc} independent FG trajectories (dt={args.dt}, tau={TAU}) on "
+                                   f"{sample_l}^4, one per process on {nproc} host cores"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "run_s": run_s,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -733,10 +893,10 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world >= 1 and not args.no_cpu_baseline:
-        # oracle first, before this process touches the GPU
-        r, s, desc = oracle_trajectory_rate(16, args.lattice, args.integrator, args.dt, 7)
-        cpu = {"value": r, "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle", "sample": desc,
-               "unit_times": oracle_unit_times()}
+        # oracle first, before this process touches the GPU (its process pool is spawned)
+        cpu = cpu_baseline_measurement(args)
+        if args.cpu_full:
+            cpu["full_8d"] = cpu_full_measurement(args)
 
     if world > 1:
         dist.init_process_group("nccl", rank=rank, world_size=world)

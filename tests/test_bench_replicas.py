@@ -80,8 +80,23 @@ def test_reference_arm_prints_the_contract_line(monkeypatch, capsys):
     import json
     monkeypatch.setenv("RANK", "0")
     monkeypatch.setenv("WORLD_SIZE", "1")
-    monkeypatch.setattr(bench, "oracle_trajectory_rate",
-                        lambda sample_l, target_l, integ, dt, seed: (0.004, 250.0, "stub sample"))
+    import time
+
+    class FakePool:
+        """Stands in for the spawned process pool: each oracle trajectory
+        'takes' 10 ms of wall time."""
+        def __enter__(self):
+            return self
+
+        def __exit__(self, *a):
+            return False
+
+        def map(self, fn, jobs):
+            jobs = list(jobs)
+            time.sleep(0.01)
+            return [0.01] * len(jobs)
+
+    monkeypatch.setattr(bench, "oracle_pool", lambda n: FakePool())
 
     class A:
         steps, warmup, lattice, integrator, dt, gpus, link_reals, precision = 2, 1, 32, "fg", 0.25, 1, 18, "fp32"
@@ -90,7 +105,12 @@ def test_reference_arm_prints_the_contract_line(monkeypatch, capsys):
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
-    assert d["value"] == pytest.approx(0.004) and d["higher_is_better"] is True
+    assert d["higher_is_better"] is True
+    # only timings that ran: ms_per_step x steps fits the run; the volume scaling is labelled apart
+    assert d["ms_per_step"] * d["steps"] / 1000.0 <= d["run_s"]
+    sf = d["scaled_from"]
+    assert d["value"] == pytest.approx(sf["trajectories_per_s_measured"] * sf["factor"])
+    assert sf["factor"] == pytest.approx((8 / 32) ** 4)
     assert d["steps"] == 2 and d["warmup"] == 1 and d["n_gpus"] == 1
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
