@@ -795,7 +795,9 @@ def fixed_acceptance_comparison(lat, torch, n_stat=200, n_tune=30, target=0.75):
     evaluations), and the FG / Omelyan ratio of accepted trajectories/s with
     its error from the two acceptances."""
     out = {}
-    for integ, steps in (("fg", (5, 6, 7, 8, 10)), ("omelyan", (20, 24, 28, 32, 40))):
+    order = {"fg": 4, "omelyan": 2}
+    dh75 = 4.0 * erfcinv(target) ** 2            # <dH> at which erfc(sqrt(<dH>) / 2) = target
+    for integ, steps in (("fg", (5, 6, 7, 8, 10)), ("omelyan", (20, 24, 28, 32, 36, 40))):
         chosen, tune = steps[-1], {}
         for n in steps:
             rs = [lat.trajectory(integ, 1.0 / n, TAU, refresh=True, u_accept=-1.0) for _ in range(n_tune)]
@@ -811,10 +813,19 @@ def fixed_acceptance_comparison(lat, torch, n_stat=200, n_tune=30, target=0.75):
         torch.cuda.synchronize()
         secs = time.perf_counter() - c0
         acc = np.array([r["accepted"] for r in rs], dtype=float)
-        e = np.exp(-np.array([r["dH"] for r in rs]))
+        dh = np.array([r["dH"] for r in rs])
+        e = np.exp(-dh)
         a = float(acc.mean())
         a_err = float(np.sqrt(max(a * (1 - a), 1e-12) / len(rs)))
+        # the steps per unit trajectory that would give the target acceptance,
+        # from <dH> ~ dt^(2 p) for an integrator of order p
+        mdh = float(dh.mean())
+        n75 = chosen * (max(mdh, 1e-12) / dh75) ** (1.0 / (2 * order[integ]))
+        forces75 = (3 if integ == "fg" else 2) * n75 + 1
         out[integ] = {"md_steps": chosen, "dt": dt, "forces_per_trajectory": rs[0]["n_force"],
+                      "mean_dH": mdh, "mean_dH_err": float(dh.std(ddof=1) / np.sqrt(len(dh))),
+                      "model_md_steps_at_target": n75,
+                      "model_forces_per_accepted_at_target": forces75 / target,
                       "trajectories": len(rs), "acceptance": a, "acceptance_err": a_err,
                       "mean_exp_minus_dH": float(e.mean()), "mean_exp_minus_dH_err": float(e.std(ddof=1) / np.sqrt(len(e))),
                       "trajectories_per_s": len(rs) / secs, "accepted_per_s": a * len(rs) / secs,
@@ -827,8 +838,20 @@ def fixed_acceptance_comparison(lat, torch, n_stat=200, n_tune=30, target=0.75):
     out["fg_over_omelyan_accepted_per_s"] = {"ratio": ratio, "err": float(ratio * rel)}
     cost = o["forces_per_accepted_trajectory"] / f["forces_per_accepted_trajectory"]
     out["omelyan_over_fg_forces_per_accepted"] = {"ratio": cost, "err": float(cost * rel)}
+    out["model_omelyan_over_fg_forces_per_accepted_at_target"] = {
+        "ratio": o["model_forces_per_accepted_at_target"] / f["model_forces_per_accepted_at_target"],
+        "model": "acceptance = erfc(sqrt(<dH>) / 2) and <dH> ~ dt^(2 p) (p = 4 for FG, 2 for Omelyan), from each "
+                 "integrator's measured <dH>; forces per trajectory 3 n + 1 (FG) and 2 n + 1 (Omelyan) at the "
+                 "step count n that gives the target acceptance (section 5's cost model counts force "
+                 "evaluations, Fig. 2 compares at 75% acceptance)"}
     out["target_acceptance"] = target
     return out
+
+
+def erfcinv(y):
+    """Inverse complementary error function (scipy)."""
+    from scipy.special import erfcinv as _e
+    return float(_e(y))
 
 
 def headline_precision_check(fg, lat, stream, args, seed=91):

@@ -113,12 +113,18 @@ typedef enum {
  * a trajectory (section 5, Fig. 1), whose error against FP64 arithmetic
  * grows with the rounding of every MD operation: ~2^-47 relative here, 2^-24
  * with FP32 fields.  Momentum refreshes draw FP32 Gaussians (exact as
- * double-floats).  Pure gauge only: kappa must be 0. */
+ * double-floats).  Pure gauge only: kappa must be 0.
+ * FG_FP32_AUTOCG is FG_FP32_FP16CG when the FP32 inner solver's working set
+ * (links and six half-lattice spinors, (4 NC 8 + 6 48) V bytes for NC
+ * complex entries per link) exceeds the GPU's L2 cache, and FG_FP32
+ * otherwise: below that size the fields stay in L2, half precision saves no
+ * memory traffic and its extra reliable updates cost time. */
 typedef enum {
   FG_FP64 = 0,
   FG_FP32 = 1,
   FG_FP32_FP16CG = 2,
-  FG_DF64 = 3
+  FG_DF64 = 3,
+  FG_FP32_AUTOCG = 4
 } fg_precision;
 
 typedef struct {

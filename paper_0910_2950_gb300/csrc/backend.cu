@@ -450,10 +450,23 @@ class Backend final : public IBackend {
   // Double-float handles are pure gauge (fg_lattice_create rejects kappa > 0):
   // their fermion entry points are not compiled.
   static constexpr bool kFerm = !std::is_same<R, DF>::value;
-  fg_status no_fermions() { return h_->fail(FG_ESTATE, "fermions need FG_FP64, FG_FP32 or FG_FP32_FP16CG"); }
-  // inner CG Dslash on a half-precision copy of the links (FG_FP32_FP16CG)
+  fg_status no_fermions() { return h_->fail(FG_ESTATE, "fermions need FG_FP64, FG_FP32, FG_FP32_FP16CG or FG_FP32_AUTOCG"); }
+  // inner CG Dslash on a half-precision copy of the links (FG_FP32_FP16CG,
+  // and FG_FP32_AUTOCG above the L2 size)
   void* U16_ = nullptr;
-  const bool half_links_ = kMixed && h_->prm.precision == FG_FP32_FP16CG;
+  const bool half_links_ = kMixed && (h_->prm.precision == FG_FP32_FP16CG ||
+                                      (h_->prm.precision == FG_FP32_AUTOCG && inner_exceeds_l2()));
+  // The FP32 inner solver's working set (links and six half-lattice spinor
+  // vectors) against the GPU's L2 cache.
+  bool inner_exceeds_l2() const {
+    int dev = 0, l2 = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess) {
+      cudaGetLastError();
+      return true;
+    }
+    const double bytes = (double)g_.V * (4.0 * NC * 8.0 + 6.0 * 48.0);
+    return bytes > (double)l2;
+  }
   void *xs_ = nullptr, *rs_ = nullptr, *p_ = nullptr, *ap_ = nullptr, *te_ = nullptr, *to_ = nullptr;
   void *Xe_ = nullptr, *Xo_ = nullptr, *Ye_ = nullptr, *Yo_ = nullptr, *FF_ = nullptr;
   CgDev* cgd_ = nullptr;

@@ -216,12 +216,10 @@ template <typename R> __device__ __forceinline__ M3<R> herm_sq(const M3<R>& a) {
   return s;
 }
 
-// Requires A exactly Hermitian (as alg_to_mat builds it).
-template <typename R> __device__ __forceinline__ M3<R> expi_herm(const M3<R>& a) {
-  M3<R> a2 = herm_sq(a);
-  R c0 = re_tr_mul(a, a2) * R(1.0 / 3.0);
-  R c1 = R(0.5) * (a2.e[0][0].re + a2.e[1][1].re + a2.e[2][2].re);
-  Cx<R> f0, f1, f2;
+// The coefficients f0, f1, f2 of exp(i A) = f0 + f1 A + f2 A^2 from
+// c0 = det A and c1 = Tr A^2 / 2 (scalar part of the closed form).
+template <typename R>
+__device__ __forceinline__ void expi_coeffs(R c0, R c1, Cx<R>& f0, Cx<R>& f1, Cx<R>& f2) {
   if (c1 < ExpSmall<R>::c1_min) {
     // |A| ~ sqrt(c1): exp(iA) = 1 + iA - A^2/2 + O(|A|^3)
     f0 = cx<R>(1, 0); f1 = cx<R>(0, 1); f2 = cx<R>(R(-0.5), 0);
@@ -256,6 +254,15 @@ template <typename R> __device__ __forceinline__ M3<R> expi_herm(const M3<R>& a)
     f0 = inv * h0; f1 = inv * h1; f2 = inv * h2;
     if (neg) { f0 = conj(f0); f1 = cx<R>(-f1.re, f1.im); f2 = conj(f2); }
   }
+}
+
+// Requires A exactly Hermitian (as alg_to_mat builds it).
+template <typename R> __device__ __forceinline__ M3<R> expi_herm(const M3<R>& a) {
+  M3<R> a2 = herm_sq(a);
+  R c0 = re_tr_mul(a, a2) * R(1.0 / 3.0);
+  R c1 = R(0.5) * (a2.e[0][0].re + a2.e[1][1].re + a2.e[2][2].re);
+  Cx<R> f0, f1, f2;
+  expi_coeffs(c0, c1, f0, f1, f2);
   M3<R> e;
 #pragma unroll
   for (int i = 0; i < 3; ++i)

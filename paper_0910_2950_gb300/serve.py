@@ -88,7 +88,8 @@ class Result:
         return self.end - self.arrival
 
 
-def footprint_bytes(spec: ChainSpec, precision: str = "fp32", link_reals: int = 18) -> int:
+def footprint_bytes(spec: ChainSpec, precision: str = "fp32", link_reals: int = 18,
+                    l2_bytes: int = 126 << 20) -> int:
     """Device bytes a chain holds, from the library's allocation plan: three
     link buffers, momenta and force, per-site energies and the stored per-site
     gauge actions, block partials and
@@ -97,7 +98,9 @@ def footprint_bytes(spec: ChainSpec, precision: str = "fp32", link_reals: int = 
     FP32 solver's reliable updates), the pseudofermion force, the CG scalars
     and the Dslash / vector block partials.  4 KiB are added for allocator
     rounding of the small buffers.  (The closed-form force gradient's
-    buffers are not included: the server does not offer that integrator.)"""
+    buffers are not included: the server does not offer that integrator.)
+    `l2_bytes` is the GPU's L2 size, which decides FG_FP32_AUTOCG's inner
+    precision."""
     v = int(np.prod(spec.dims))
     r = 8 if precision in ("fp64", "df64") else 4     # bytes per real (double-float: two floats)
     gauge = 4 * v * link_reals * r
@@ -110,7 +113,9 @@ def footprint_bytes(spec: ChainSpec, precision: str = "fp32", link_reals: int = 
         dslash_blocks = (vh + 127) // 128
         vec_blocks = min((nvec + 255) // 256, 152 * 8)
         total += n64 * nvec * 16 + 10 * nvec * 2 * r + mom + 128 + 8 * (dslash_blocks + vec_blocks + 2)
-        if precision == "fp32_fp16cg":
+        half = precision == "fp32_fp16cg" or (
+            precision == "fp32_autocg" and v * (4 * (link_reals // 2) * 8 + 6 * 48) > l2_bytes)
+        if half:
             total += 4 * v * link_reals * 2      # half-precision links of the inner solver
     return total + 4096
 

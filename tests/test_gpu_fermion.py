@@ -123,6 +123,22 @@ def test_inner_dslash_half_element_by_element(fgmod, dims, link_reals, dagger):
     assert 1e-5 < err < 5e-3, err    # half-precision rounding is visible, and bounded
 
 
+@pytest.mark.parametrize("dims,same_as", [((16, 16, 16, 32), "fp32"), ((24, 24, 24, 48), "fp32_fp16cg")])
+def test_autocg_follows_the_l2_size(fgmod, dims, same_as):
+    """FG_FP32_AUTOCG runs the FP32 inner solver while its working set fits
+    the L2 cache (16^3 x 32: ~75 MB) and the half-precision one above it
+    (24^3 x 48: ~380 MB): the solutions are those of the chosen mode, bit
+    for bit."""
+    u, psi, _, _ = _inner_case(dims)
+    out = {}
+    for prec in ("fp32_autocg", same_as):
+        with fgmod.Lattice(dims, BETA, kappa=KAPPA, precision=prec) as lat:
+            lat.set_gauge(u)
+            out[prec] = lat.cg_solve(psi)
+    assert np.array_equal(out["fp32_autocg"][0], out[same_as][0])
+    assert out["fp32_autocg"][1]["iterations"] == out[same_as][1]["iterations"]
+
+
 def test_inner_dslash_fp64_is_apply_mhat(fgmod):
     dims = (6, 4, 2, 6)
     u, psi, ref, _ = _inner_case(dims)
