@@ -468,6 +468,17 @@ class Backend final : public IBackend {
     return bytes > (double)l2;
   }
   void *xs_ = nullptr, *rs_ = nullptr, *p_ = nullptr, *ap_ = nullptr, *te_ = nullptr, *to_ = nullptr;
+  // the folded iteration writes r' and p' to the other buffer of a pair;
+  // rs_ and p_ always name the current ones
+  void *rs2_ = nullptr, *p2_ = nullptr;
+  // Folded CG iterations (four launches, vector updates inside the Dslash
+  // launches) for FP32 and FP64 inner vectors; the half-precision solver
+  // keeps its six launches.  FG_CG_FOLD=0 in the environment selects the six
+  // launches everywhere (tuning and comparison).
+  const bool fold_ = [] {
+    const char* e = std::getenv("FG_CG_FOLD");
+    return !(e && e[0] == '0');
+  }() && !half_links_;
   void *Xe_ = nullptr, *Xo_ = nullptr, *Ye_ = nullptr, *Yo_ = nullptr, *FF_ = nullptr;
   CgDev* cgd_ = nullptr;
   double* part_pap_ = nullptr;
@@ -873,10 +884,11 @@ class Backend final : public IBackend {
       void** dR[] = {&xs_, &rs_, &p_, &ap_, &te_, &to_, &Xe_, &Xo_, &Ye_, &Yo_};
       for (void** p : dR)
         if ((s = alloc(p, bR)) != FG_OK) return s;
+      if (fold_ && ((s = alloc(&rs2_, bR)) != FG_OK || (s = alloc(&p2_, bR)) != FG_OK)) return s;
       if ((s = alloc(&FF_, (size_t)4 * 4 * g_.V * sizeof(C2))) != FG_OK) return s;
       if ((s = alloc((void**)&cgd_, sizeof(CgDev))) != FG_OK) return s;
       if (cudaMemsetAsync(cgd_, 0, sizeof(CgDev), st_) != cudaSuccess) return cuda_fail("cg state init");
-      if ((s = alloc((void**)&part_pap_, (dslash_blocks(g_.Vh) + 1) * sizeof(double))) != FG_OK) return s;
+      if ((s = alloc((void**)&part_pap_, (3 * dslash_blocks(g_.Vh) + 1) * sizeof(double))) != FG_OK) return s;
       if ((s = alloc((void**)&part_rr_, (vec_blocks(nvec()) + 1) * sizeof(double))) != FG_OK) return s;
       const size_t mbytes = sizeof(Mapped) + (size_t)(h_->prm.cg_maxiter + 8) * sizeof(double);
       if (cudaHostAlloc((void**)&mapped_, mbytes, cudaHostAllocMapped) != cudaSuccess) {
@@ -1025,6 +1037,33 @@ class Backend final : public IBackend {
     return launch_dslash<R, NC, R>(g_, out, in, x, pdot, U, out_par, dag, mode, b, partial, cgd, st_);
   }
 
+  // Folded iteration, launches D and A (B and C are plain Dslash launches).
+  // A swaps the current and other buffers of r and p.
+  cudaError_t fold_apdot(const void* U) {
+    if constexpr (kMixed || std::is_same<R, double>::value) {
+      const double k2 = h_->prm.kappa * h_->prm.kappa;
+      return launch_cg_apdot<R, NC>(g_, ap_, to_, te_, p_, rs_, U, k2, part_pap_, cgd_, st_);
+    } else {
+      return cudaErrorNotSupported;
+    }
+  }
+  cudaError_t fold_update(const void* U) {
+    if constexpr (kMixed || std::is_same<R, double>::value) {
+      const cudaError_t e = launch_cg_fold<R, NC>(g_, to_, xs_, rs_, ap_, p_, rs2_, p2_, U, part_rr_, cgd_,
+                                                  mapped_->hist, &mapped_->dev_iter, h_->prm.cg_maxiter, st_);
+      std::swap(rs_, rs2_);
+      std::swap(p_, p2_);
+      return e;
+    } else {
+      return cudaErrorNotSupported;
+    }
+  }
+  // t_o = D_oe p, which the folded iteration expects on entry (after the
+  // setup and after every reliable update, which may replace p).
+  fg_status fold_prime(const void* U) {
+    return run(KC_DSLASH, [&] { return inner_dslash(to_, p_, nullptr, nullptr, U, 1, 0, 0, 1.0, nullptr); });
+  }
+
   // One CG iteration in the inner precision R: 4 Dslash + 2 vector kernels,
   // which all return at once after convergence (cgd_->done).  Raw launches,
   // usable inside stream capture.
@@ -1032,6 +1071,12 @@ class Backend final : public IBackend {
     const double k2 = h_->prm.kappa * h_->prm.kappa;
     const int n = nvec();
     cudaError_t e;
+    if (fold_) {
+      if ((e = inner_dslash(te_, to_, p_, nullptr, U, 0, 0, 1, -k2, nullptr)) != cudaSuccess) return e;
+      if ((e = inner_dslash(to_, te_, nullptr, nullptr, U, 1, 1, 0, 1.0, nullptr)) != cudaSuccess) return e;
+      if ((e = fold_apdot(U)) != cudaSuccess) return e;
+      return fold_update(U);
+    }
     if ((e = inner_dslash(to_, p_, nullptr, nullptr, U, 1, 0, 0, 1.0, nullptr)) != cudaSuccess) return e;
     if ((e = inner_dslash(te_, to_, p_, nullptr, U, 0, 0, 1, -k2, nullptr)) != cudaSuccess) return e;
     if ((e = inner_dslash(to_, te_, nullptr, nullptr, U, 1, 1, 0, 1.0, nullptr)) != cudaSuccess) return e;
@@ -1053,6 +1098,16 @@ class Backend final : public IBackend {
     const double k2 = h_->prm.kappa * h_->prm.kappa;
     const int n = nvec();
     fg_status s;
+    if (fold_) {
+      if ((s = run(KC_DSLASH, [&] { return inner_dslash(te_, to_, p_, nullptr, U, 0, 0, 1, -k2, nullptr); })) !=
+          FG_OK)
+        return s;
+      if ((s = run(KC_DSLASH, [&] { return inner_dslash(to_, te_, nullptr, nullptr, U, 1, 1, 0, 1.0, nullptr); })) !=
+          FG_OK)
+        return s;
+      if ((s = run(KC_DSLASH, [&] { return fold_apdot(U); })) != FG_OK) return s;
+      return run(KC_DSLASH, [&] { return fold_update(U); });
+    }
     if ((s = run(KC_DSLASH, [&] { return inner_dslash(to_, p_, nullptr, nullptr, U, 1, 0, 0, 1.0, nullptr); })) !=
         FG_OK)
       return s;
@@ -1087,6 +1142,7 @@ class Backend final : public IBackend {
   struct CgGraph {
     const void* U;
     int n;
+    const void* r;  // the current r buffer at capture (the folded iteration alternates two)
     cudaGraphExec_t exec;
   };
   std::vector<CgGraph> cg_graphs_;
@@ -1099,7 +1155,8 @@ class Backend final : public IBackend {
 
   cudaGraphExec_t cg_graph(const void* U, int n) {
     for (const CgGraph& c : cg_graphs_)
-      if (c.U == U && c.n == n) return c.exec;
+      if (c.U == U && c.n == n && c.r == rs_) return c.exec;
+    const void* r_at_capture = rs_;
     if (cg_graphs_broken_) return nullptr;
     cudaGraph_t graph = nullptr;
     if (cudaStreamBeginCapture(st_, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
@@ -1110,10 +1167,14 @@ class Backend final : public IBackend {
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < n && e == cudaSuccess; ++i) e = cg_iteration_raw(U);
     cudaError_t e2 = cudaStreamEndCapture(st_, &graph);
+    if (rs_ != r_at_capture) {  // a capture that stopped after an odd number of folded iterations
+      std::swap(rs_, rs2_);
+      std::swap(p_, p2_);
+    }
     cudaGraphExec_t exec = nullptr;
     if (e == cudaSuccess && e2 == cudaSuccess && graph != nullptr &&
         cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
-      cg_graphs_.push_back({U, n, exec});
+      cg_graphs_.push_back({U, n, r_at_capture, exec});
     } else {
       cudaGetLastError();
       exec = nullptr;
@@ -1130,7 +1191,8 @@ class Backend final : public IBackend {
       cudaGraphExec_t g = cg_graph(U, n);
       if (g != nullptr) {
         if (cudaGraphLaunch(g, st_) != cudaSuccess) return cuda_fail("cg graph launch");
-        h_->launches += 6 * n;
+        // an even number of folded iterations leaves rs_ and p_ where they were
+        h_->launches += (fold_ ? 4 : 6) * n;
         return FG_OK;
       }
     }
@@ -1255,6 +1317,7 @@ class Backend final : public IBackend {
       if ((s = run(KC_CONVERT, [&] { return launch_links_to_half<NC>(g_, U, U16_, st_); })) != FG_OK) return s;
       Uin = U16_;
     }
+    if (fold_ && (s = fold_prime(Uin)) != FG_OK) return s;
     st->iters = 0;
     st->nru = 0;
     st->true_res = 0.0;
@@ -1341,6 +1404,7 @@ class Backend final : public IBackend {
               CG_TRACE("cg reliable update after queued %d (last %.3e predicted %.3e)\n", queued, last / bb,
                        predicted / bb);
               if ((s = reliable_update(U, b64, false)) != FG_OK) return s;
+              if (fold_ && (s = fold_prime(Uin)) != FG_OK) return s;
               ++st->nru;
               maxrr = predicted;
             }
@@ -1350,6 +1414,7 @@ class Backend final : public IBackend {
       }
       if ((s = reliable_update(U, b64, true)) != FG_OK) return s;
       ++st->nru;
+      if (fold_ && (s = fold_prime(Uin)) != FG_OK) return s;
       if ((s = sync()) != FG_OK) return s;
       const double trr = mapped_->true_rr;
       st->true_res = std::sqrt(trr / bb);

@@ -17,313 +17,10 @@
 // (1 - s g_mu) psi = (h, -s A_mu^dagger h) with h = psi_up - s A_mu psi_down.
 #include <type_traits>
 
-#include "df64.cuh"
-#include "fg_common.cuh"
-#include "fg_fermion.h"
+#include "fermion_device.cuh"
 #include "fg_kernels.h"
 
 namespace fg {
-
-static inline Geom to_devg(const GeomH& h) {
-  Geom g;
-  for (int i = 0; i < 4; ++i) g.L[i] = h.L[i];
-  g.Lxh = h.Lxh; g.Vh = h.Vh; g.V = h.V;
-  g.dLxh = make_fastdiv((uint32_t)h.Lxh);
-  g.dLy = make_fastdiv((uint32_t)h.L[1]);
-  g.dLz = make_fastdiv((uint32_t)h.L[2]);
-  return g;
-}
-
-template <typename R> struct Spinor {
-  Cx<R> s[4][3];
-};
-
-// Spinor entry k = spin * 3 + colour sits in pair k / 2, slot k % 2.  ST is
-// the storage type (the arithmetic type R, or Half16 for R = float).
-template <typename R, typename ST = R>
-__device__ __forceinline__ Spinor<R> load_spinor(const typename Vec2<ST>::T* __restrict__ f, int i, int Vh) {
-  Spinor<R> x;
-#pragma unroll
-  for (int q = 0; q < 6; ++q) {
-    Cx<R> a, b;
-    Quad<ST>::load(f, (size_t)q * Vh + i, a, b);
-    x.s[(2 * q) / 3][(2 * q) % 3] = a;
-    x.s[(2 * q + 1) / 3][(2 * q + 1) % 3] = b;
-  }
-  return x;
-}
-template <typename R, typename ST = R>
-__device__ __forceinline__ void store_spinor(typename Vec2<ST>::T* __restrict__ f, int i, int Vh,
-                                             const Spinor<R>& x) {
-#pragma unroll
-  for (int q = 0; q < 6; ++q)
-    Quad<ST>::store(f, (size_t)q * Vh + i, x.s[(2 * q) / 3][(2 * q) % 3], x.s[(2 * q + 1) / 3][(2 * q + 1) % 3]);
-}
-
-template <typename RO, typename RI>
-__device__ __forceinline__ M3<RO> convert(const M3<RI>& m) {
-  M3<RO> o;
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) o.e[i][j] = cx<RO>(RO(m.e[i][j].re), RO(m.e[i][j].im));
-  return o;
-}
-
-// h_k = psi_k - S (A_mu psi_down)_k, k = 0, 1
-template <int MU, int S, typename R>
-__device__ __forceinline__ void project(const Spinor<R>& p, Cx<R> h[2][3]) {
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    Cx<R> a0, a1;  // (A_mu psi_down)_0, _1
-    if (MU == 0) { a0 = times_i(p.s[3][c]); a1 = times_i(p.s[2][c]); }
-    if (MU == 1) { a0 = cx<R>(-p.s[3][c].re, -p.s[3][c].im); a1 = p.s[2][c]; }
-    if (MU == 2) { a0 = times_i(p.s[2][c]); a1 = cx<R>(p.s[3][c].im, -p.s[3][c].re); }
-    if (MU == 3) { a0 = p.s[2][c]; a1 = p.s[3][c]; }
-    if (S > 0) { h[0][c] = p.s[0][c] - a0; h[1][c] = p.s[1][c] - a1; }
-    else { h[0][c] = p.s[0][c] + a0; h[1][c] = p.s[1][c] + a1; }
-  }
-}
-
-// (b0, b1) = A_mu^dagger (w0, w1)
-template <int MU, typename R>
-__device__ __forceinline__ void adag_mu(const Cx<R>& w0, const Cx<R>& w1, Cx<R>& b0, Cx<R>& b1) {
-  if (MU == 0) { b0 = cx<R>(w1.im, -w1.re); b1 = cx<R>(w0.im, -w0.re); }
-  if (MU == 1) { b0 = w1; b1 = cx<R>(-w0.re, -w0.im); }
-  if (MU == 2) { b0 = cx<R>(w0.im, -w0.re); b1 = times_i(w1); }
-  if (MU == 3) { b0 = w0; b1 = w1; }
-}
-
-// acc_up += sign * w, acc_down += sign * (-S) A_mu^dagger w
-template <int MU, int S, typename R>
-__device__ __forceinline__ void reconstruct_add(Spinor<R>& acc, const Cx<R> w[2][3], R sign) {
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    Cx<R> b0, b1;
-    adag_mu<MU>(w[0][c], w[1][c], b0, b1);
-    const R sd = (S > 0) ? -sign : sign;
-    acc.s[0][c] = acc.s[0][c] + sign * w[0][c];
-    acc.s[1][c] = acc.s[1][c] + sign * w[1][c];
-    acc.s[2][c] = acc.s[2][c] + sd * b0;
-    acc.s[3][c] = acc.s[3][c] + sd * b1;
-  }
-}
-
-// w = U h (ADJ = 0) or U^dagger h (ADJ = 1), for both half-spinor rows
-template <int ADJ, typename R>
-__device__ __forceinline__ void mat_half(const M3<R>& u, const Cx<R> h[2][3], Cx<R> w[2][3]) {
-#pragma unroll
-  for (int k = 0; k < 2; ++k)
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      Cx<R> s = cx<R>(0, 0);
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        if (ADJ) cmac_cj(s, u.e[b][a], h[k][b]);
-        else cmac(s, u.e[a][b], h[k][b]);
-      }
-      w[k][a] = s;
-    }
-}
-
-// Double-float versions of the two inner steps.  The links are FP32, so a
-// product of a double-float half-spinor entry h and a link entry u is the
-// exact pair (fl(h.hi u), its error) plus h.lo u; the six products of each
-// output component are summed with two_sum on the high parts and the error
-// terms collected in FP32 (a compensated dot product, Ogita, Rump and
-// Oishi 2005), normalised once at the end.
-struct DfAcc {
-  float s, c;
-};
-__device__ __forceinline__ void dfacc_add(DfAcc& a, DF h, float u) {
-  const float p = __fmul_rn(h.hi, u);
-  float e = __fmaf_rn(h.hi, u, -p);
-  e = __fmaf_rn(h.lo, u, e);
-  const DF t = df_two_sum(a.s, p);
-  a.s = t.hi;
-  a.c = __fadd_rn(a.c, __fadd_rn(t.lo, e));
-}
-template <int ADJ>
-__device__ __forceinline__ void mat_half(const M3<DF>& u, const Cx<DF> h[2][3], Cx<DF> w[2][3]) {
-#pragma unroll
-  for (int k = 0; k < 2; ++k)
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      DfAcc re = {0.0f, 0.0f}, im = {0.0f, 0.0f};
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        // u_ab h_b, or conj(u_ba) h_b
-        const float ur = ADJ ? u.e[b][a].re.hi : u.e[a][b].re.hi;
-        const float ui = ADJ ? -u.e[b][a].im.hi : u.e[a][b].im.hi;
-        dfacc_add(re, h[k][b].re, ur);
-        dfacc_add(re, h[k][b].im, -ui);
-        dfacc_add(im, h[k][b].im, ur);
-        dfacc_add(im, h[k][b].re, ui);
-      }
-      w[k][a] = cx<DF>(df_fast_two_sum(re.s, re.c), df_fast_two_sum(im.s, im.c));
-    }
-}
-// The same reconstruction with sign = +-1 applied exactly (no double-float product).
-__device__ __forceinline__ Cx<DF> df_scale_sign(const Cx<DF>& w, float sg) {
-  return cx<DF>(DF(sg * w.re.hi, sg * w.re.lo), DF(sg * w.im.hi, sg * w.im.lo));
-}
-template <int MU, int S>
-__device__ __forceinline__ void reconstruct_add(Spinor<DF>& acc, const Cx<DF> w[2][3], DF sign) {
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const Cx<DF> w0 = df_scale_sign(w[0][c], sign.hi), w1 = df_scale_sign(w[1][c], sign.hi);
-    Cx<DF> b0, b1;
-    adag_mu<MU>(w0, w1, b0, b1);
-    acc.s[0][c] = acc.s[0][c] + w0;
-    acc.s[1][c] = acc.s[1][c] + w1;
-    if (S > 0) {
-      acc.s[2][c] = acc.s[2][c] - b0;
-      acc.s[3][c] = acc.s[3][c] - b1;
-    } else {
-      acc.s[2][c] = acc.s[2][c] + b0;
-      acc.s[3][c] = acc.s[3][c] + b1;
-    }
-  }
-}
-
-// ---- runtime-direction hop (double-float): one loop body for all eight
-// hops keeps the long double-float code within the instruction cache.
-// The spin structure of each direction is a choice of component and a unit
-// factor in {1, i, -1, -i}, taken with selects.
-__device__ __forceinline__ Cx<DF> unit_mul(const Cx<DF>& x, bool is_i, bool neg) {
-  const float sg = neg ? -1.0f : 1.0f;
-  const DF re = is_i ? -x.im : x.re;
-  const DF im = is_i ? x.re : x.im;
-  return cx<DF>(DF(sg * re.hi, sg * re.lo), DF(sg * im.hi, sg * im.lo));
-}
-__device__ __forceinline__ Cx<DF> pick(bool first, const Cx<DF>& a, const Cx<DF>& b) {
-  return cx<DF>(first ? a.re : b.re, first ? a.im : b.im);
-}
-// h_k = psi_k - S (A_mu psi_down)_k: (A_mu psi_down)_0 = c0 psi_j0,
-// (A_mu psi_down)_1 = c1 psi_(5-j0); j0 = 3 for mu = x, y and 2 for z, t;
-// c0, c1 = (i, i), (-1, 1), (i, -i), (1, 1).
-__device__ __forceinline__ void project_rt(int mu, int S, const Spinor<DF>& p, Cx<DF> h[2][3]) {
-  const bool j3 = mu < 2, is_i = mu == 0 || mu == 2;
-  const bool n0 = (mu == 1) != (S > 0), n1 = (mu == 2) != (S > 0);
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    h[0][c] = p.s[0][c] + unit_mul(pick(j3, p.s[3][c], p.s[2][c]), is_i, n0);
-    h[1][c] = p.s[1][c] + unit_mul(pick(j3, p.s[2][c], p.s[3][c]), is_i, n1);
-  }
-}
-// acc_up += sign w; acc_down += sign (-S) A_mu^dagger w with
-// (A_mu^dagger w)_0 = d0 w_k0, (A_mu^dagger w)_1 = d1 w_(1-k0); k0 = 1 for
-// mu = x, y and 0 for z, t; d0, d1 = (-i, -i), (1, -1), (-i, i), (1, 1).
-__device__ __forceinline__ void reconstruct_rt(int mu, int S, float sign, const Cx<DF> w[2][3], Spinor<DF>& acc) {
-  const bool k1 = mu < 2, is_i = mu == 0 || mu == 2;
-  // w0, w1 carry `sign`; unit_mul applies d and the factor -S
-  const bool n0 = is_i != (S > 0), n1 = (mu < 2) != (S > 0);
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const Cx<DF> w0 = df_scale_sign(w[0][c], sign), w1 = df_scale_sign(w[1][c], sign);
-    acc.s[0][c] = acc.s[0][c] + w0;
-    acc.s[1][c] = acc.s[1][c] + w1;
-    acc.s[2][c] = acc.s[2][c] + unit_mul(pick(k1, w1, w0), is_i, n0);
-    acc.s[3][c] = acc.s[3][c] + unit_mul(pick(k1, w0, w1), is_i, n1);
-  }
-}
-// w = U h (adj = false) or U^dagger h, FP32 link, compensated double-float sums
-__device__ __forceinline__ void mat_half_rt(const M3<float>& u, bool adj, const Cx<DF> h[2][3], Cx<DF> w[2][3]) {
-  float ur[3][3], ui[3][3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      ur[a][b] = adj ? u.e[b][a].re : u.e[a][b].re;
-      ui[a][b] = adj ? -u.e[b][a].im : u.e[a][b].im;
-    }
-#pragma unroll
-  for (int k = 0; k < 2; ++k)
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      DfAcc re = {0.0f, 0.0f}, im = {0.0f, 0.0f};
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        dfacc_add(re, h[k][b].re, ur[a][b]);
-        dfacc_add(re, h[k][b].im, -ui[a][b]);
-        dfacc_add(im, h[k][b].im, ur[a][b]);
-        dfacc_add(im, h[k][b].re, ui[a][b]);
-      }
-      w[k][a] = cx<DF>(df_fast_two_sum(re.s, re.c), df_fast_two_sum(im.s, im.c));
-    }
-}
-template <int DAG, int NC>
-__device__ __forceinline__ void hops_rt(Spinor<DF>& acc, const float4* __restrict__ in, const Gauge<float, NC>& U,
-                                        const Geom& g, const int c[4], int s, int in_off) {
-  constexpr int SF = DAG ? -1 : 1;  // forward hop: (1 - g_mu), (1 + g_mu) for the dagger
-#pragma unroll 1
-  for (int hd = 0; hd < 8; ++hd) {
-    const int mu = hd >> 1;
-    const bool fwd = (hd & 1) == 0;
-    const int sn = cb_neighbor_rt(g, c, mu, fwd ? 1 : -1);
-    const Spinor<DF> p = load_spinor<DF>(in, sn - in_off, g.Vh);
-    const int S = fwd ? SF : -SF;
-    Cx<DF> h[2][3], w[2][3];
-    project_rt(mu, S, p, h);
-    const M3<float> u = U.load(mu, fwd ? s : sn);
-    mat_half_rt(u, !fwd, h, w);
-    const bool anti = mu == 3 && (fwd ? c[3] == g.L[3] - 1 : c[3] == 0);
-    reconstruct_rt(mu, S, anti ? -1.0f : 1.0f, w, acc);
-  }
-}
-template <int DAG, typename RL, int NC, typename RS, typename ST = RS>
-struct Hops {
-  static __device__ __forceinline__ void run(Spinor<RS>& acc, const typename Vec2<ST>::T* __restrict__ in,
-                                             const Gauge<RL, NC>& U, const Geom& g, const int c[4], int s,
-                                             int in_off);
-};
-
-template <int MU, int DAG, typename RL, int NC, typename RS, typename ST = RS>
-__device__ __forceinline__ void hop_dir(Spinor<RS>& acc, const typename Vec2<ST>::T* __restrict__ in,
-                                        const Gauge<RL, NC>& U, const Geom& g, const int c[4], int s,
-                                        int in_off) {
-  constexpr int SF = DAG ? -1 : 1;   // forward hop: (1 - g_mu), (1 + g_mu) for the dagger
-  constexpr int SB = -SF;
-  {
-    const int sn = cb_neighbor(g, c, MU, +1);
-    const Spinor<RS> p = load_spinor<RS, ST>(in, sn - in_off, g.Vh);
-    Cx<RS> h[2][3], w[2][3];
-    project<MU, SF>(p, h);
-    const M3<RS> u = convert<RS>(U.load(MU, s));
-    mat_half<0>(u, h, w);
-    const RS sign = (MU == 3 && c[3] == g.L[3] - 1) ? RS(-1) : RS(1);
-    reconstruct_add<MU, SF>(acc, w, sign);
-  }
-  {
-    const int sn = cb_neighbor(g, c, MU, -1);
-    const Spinor<RS> p = load_spinor<RS, ST>(in, sn - in_off, g.Vh);
-    Cx<RS> h[2][3], w[2][3];
-    project<MU, SB>(p, h);
-    const M3<RS> u = convert<RS>(U.load(MU, sn));
-    mat_half<1>(u, h, w);
-    const RS sign = (MU == 3 && c[3] == 0) ? RS(-1) : RS(1);
-    reconstruct_add<MU, SB>(acc, w, sign);
-  }
-}
-
-template <int DAG, typename RL, int NC, typename RS, typename ST>
-__device__ __forceinline__ void Hops<DAG, RL, NC, RS, ST>::run(Spinor<RS>& acc,
-                                                               const typename Vec2<ST>::T* __restrict__ in,
-                                                               const Gauge<RL, NC>& U, const Geom& g,
-                                                               const int c[4], int s, int in_off) {
-  hop_dir<0, DAG, RL, NC, RS, ST>(acc, in, U, g, c, s, in_off);
-  hop_dir<1, DAG, RL, NC, RS, ST>(acc, in, U, g, c, s, in_off);
-  hop_dir<2, DAG, RL, NC, RS, ST>(acc, in, U, g, c, s, in_off);
-  hop_dir<3, DAG, RL, NC, RS, ST>(acc, in, U, g, c, s, in_off);
-}
-template <int DAG, int NC>
-struct Hops<DAG, float, NC, DF, DF> {
-  static __device__ __forceinline__ void run(Spinor<DF>& acc, const float4* __restrict__ in,
-                                             const Gauge<float, NC>& U, const Geom& g, const int c[4], int s,
-                                             int in_off) {
-    hops_rt<DAG, NC>(acc, in, U, g, c, s, in_off);
-  }
-};
 
 constexpr int kDslashThreads = 128;
 
@@ -387,6 +84,163 @@ __global__ void __launch_bounds__(kDslashThreads, DslashMinBlocks<RS>::value) ds
     store_spinor<RS, ST>(out, i, g.Vh, o);
   }
   if (MODE == 2) block_reduce_total(double(dot), partial, &cgd->ticket[0], &cgd->pap);
+}
+
+// --------------------------------------------------------------------------- folded CG
+// One CG iteration on Mhat^dagger Mhat in four launches, the vector updates
+// carried by the two Dslash launches that end the operator:
+//   B  t_e = p - k2 D_eo t_o                 (dslash_kernel, mode 1)
+//   C  t_o = D_oe^dagger t_e                  (dslash_kernel, mode 0)
+//   D  Ap = t_e - k2 D_eo^dagger t_o, grand totals of <p, Ap>, Re <r, Ap>
+//      and |Ap|^2; the last block sets alpha = rr / <p, Ap> and
+//      beta = rr' / rr with rr' = |r - alpha Ap|^2 expanded as
+//      rr - 2 alpha Re <r, Ap> + alpha^2 |Ap|^2          (cg_apdot_kernel)
+//   A  x += alpha p, r' = r - alpha Ap, p' = r' + beta p at the even sites
+//      and t_o = D_oe p' at the odd ones, p' of the neighbours formed on the
+//      fly from r, Ap and p; the grand total |r'|^2 is the iteration's
+//      residual, published with the iteration count    (cg_fold_kernel)
+// r' and p' go to the other buffer of a pair (the neighbours' r and p are
+// still being read).  Only beta uses the expanded rr'; alpha of the next
+// iteration and the convergence test use the summed |r'|^2.
+
+// Block partials of NV values; the last block to finish (ticket) sums each
+// in block order into tot[] (fixed for a fixed launch) and resets the
+// ticket.  Returns true in that block.
+template <int NV>
+__device__ __forceinline__ bool block_reduce_last(double v[NV], double* __restrict__ partial,
+                                                  unsigned* __restrict__ ticket, double tot[NV]) {
+  block_reduce_store<NV>(v, partial, gridDim.x);
+  __shared__ int last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  __shared__ double sh[NV][32];
+  const int n = gridDim.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double x = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) x += __ldcg(partial + (size_t)k * n + i);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) sh[k][warp] = x;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double t = 0.0;
+    for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) t += sh[k][w];
+    tot[k] = t;
+  }
+  if (threadIdx.x == 0) *ticket = 0u;
+  return true;
+}
+
+// D: Ap = te + b D^dagger_eo to at the even sites, with the three dot products.
+template <typename R, int NC>
+__global__ void __launch_bounds__(kDslashThreads, DslashMinBlocks<R>::value) cg_apdot_kernel(
+    typename Vec2<R>::T* __restrict__ ap, const typename Vec2<R>::T* __restrict__ to,
+    const typename Vec2<R>::T* __restrict__ te, const typename Vec2<R>::T* __restrict__ p,
+    const typename Vec2<R>::T* __restrict__ r, Gauge<R, NC> U, Geom g, R b, double* __restrict__ partial,
+    CgDev* __restrict__ cgd) {
+  if (cgd->done) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  R pa = R(0), ra = R(0), aa = R(0);  // one site's 24 terms each, in R
+  if (i < g.Vh) {
+    int c[4], par;
+    cb_coords(g, i, c, par);
+    Spinor<R> acc;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) acc.s[k][cc] = cx<R>(0, 0);
+    hops_src<1, R, NC, R>(acc, FieldSrc<R, R>{to}, U, g, c, i, g.Vh);
+    const Spinor<R> tv = load_spinor<R>(te, i, g.Vh);
+    const Spinor<R> pv = load_spinor<R>(p, i, g.Vh);
+    const Spinor<R> rv = load_spinor<R>(r, i, g.Vh);
+    Spinor<R> o;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) {
+        o.s[k][cc] = tv.s[k][cc] + b * acc.s[k][cc];
+        pa += pv.s[k][cc].re * o.s[k][cc].re + pv.s[k][cc].im * o.s[k][cc].im;
+        ra += rv.s[k][cc].re * o.s[k][cc].re + rv.s[k][cc].im * o.s[k][cc].im;
+        aa += o.s[k][cc].re * o.s[k][cc].re + o.s[k][cc].im * o.s[k][cc].im;
+      }
+    store_spinor<R>(ap, i, g.Vh, o);
+  }
+  double v[3] = {double(pa), double(ra), double(aa)}, tot[3];
+  if (block_reduce_last<3>(v, partial, &cgd->ticket[0], tot) && threadIdx.x == 0) {
+    const double rr = cgd->rr[cgd->iter & 1];
+    const double alpha = tot[0] > 0.0 ? rr / tot[0] : 0.0;
+    const double rrn = rr - 2.0 * alpha * tot[1] + alpha * alpha * tot[2];
+    cgd->pap = tot[0];
+    cgd->alpha = alpha;
+    cgd->beta = (rr > 0.0 && rrn > 0.0) ? rrn / rr : 0.0;
+  }
+}
+
+// A: the vector updates of the iteration and t_o = D_oe p'.
+template <typename R, int NC>
+__global__ void __launch_bounds__(kDslashThreads, DslashMinBlocks<R>::value) cg_fold_kernel(
+    typename Vec2<R>::T* __restrict__ to, typename Vec2<R>::T* __restrict__ x,
+    const typename Vec2<R>::T* __restrict__ r, const typename Vec2<R>::T* __restrict__ ap,
+    const typename Vec2<R>::T* __restrict__ p, typename Vec2<R>::T* __restrict__ r2,
+    typename Vec2<R>::T* __restrict__ p2, Gauge<R, NC> U, Geom g, double* __restrict__ partial,
+    CgDev* __restrict__ cgd, double* __restrict__ hist, int* __restrict__ iter_out, int maxiter) {
+  if (cgd->done) return;
+  const FoldSrc<R> src{r, ap, p, R(cgd->alpha), R(cgd->beta)};
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  R acc = R(0);
+  if (i < g.Vh) {
+    // the even site i: x, r', p'
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      const size_t j = (size_t)q * g.Vh + i;
+      Cx<R> x0, x1, r0, r1, a0, a1, p0, p1;
+      Quad<R>::load(x, j, x0, x1);
+      Quad<R>::load(r, j, r0, r1);
+      Quad<R>::load(ap, j, a0, a1);
+      Quad<R>::load(p, j, p0, p1);
+      x0 = cx<R>(fma(src.alpha, p0.re, x0.re), fma(src.alpha, p0.im, x0.im));
+      x1 = cx<R>(fma(src.alpha, p1.re, x1.re), fma(src.alpha, p1.im, x1.im));
+      const Cx<R> q0 = src.fold_entry(r0, a0, p0), q1 = src.fold_entry(r1, a1, p1);
+      r0 = cx<R>(fma(-src.alpha, a0.re, r0.re), fma(-src.alpha, a0.im, r0.im));
+      r1 = cx<R>(fma(-src.alpha, a1.re, r1.re), fma(-src.alpha, a1.im, r1.im));
+      Quad<R>::store(x, j, x0, x1);
+      Quad<R>::store(r2, j, r0, r1);
+      Quad<R>::store(p2, j, q0, q1);
+      acc = fma(r0.re, r0.re, acc);
+      acc = fma(r0.im, r0.im, acc);
+      acc = fma(r1.re, r1.re, acc);
+      acc = fma(r1.im, r1.im, acc);
+    }
+    // the odd site Vh + i: D_oe p'
+    const int s = g.Vh + i;
+    int c[4], par;
+    cb_coords(g, s, c, par);
+    Spinor<R> o;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) o.s[k][cc] = cx<R>(0, 0);
+    hops_src<0, R, NC, R>(o, src, U, g, c, s, 0);
+    store_spinor<R>(to, i, g.Vh, o);
+  }
+  double v[1] = {double(acc)}, tot[1];
+  if (block_reduce_last<1>(v, partial, &cgd->ticket[1], tot) && threadIdx.x == 0) {
+    const int k = cgd->iter + 1;
+    const double rr = tot[0];
+    cgd->rr[k & 1] = rr;
+    if (k <= maxiter) hist[k] = rr;
+    cgd->iter = k;
+    *iter_out = k;
+    if (rr <= cgd->tol2bb) cgd->done = 1;
+  }
 }
 
 // --------------------------------------------------------------------------- force
@@ -1006,6 +860,28 @@ cudaError_t launch_cg_xpay(void* p, const void* r, CgDev* cgd, double* hist, int
   cg_xpay_kernel<R><<<vec_blocks(n), kVecThreads, 0, st>>>(v2<R>(p), cv2<R>(r), cgd, hist, iter_out, maxiter, n);
   return cudaGetLastError();
 }
+template <typename R, int NC>
+cudaError_t launch_cg_apdot(const GeomH& gh, void* ap, const void* to, const void* te, const void* p, const void* r,
+                            const void* U, double k2, double* partial, CgDev* cgd, cudaStream_t st) {
+  Gauge<R, NC> u;
+  u.p = const_cast<void*>(U);
+  u.V = gh.V;
+  cg_apdot_kernel<R, NC><<<dslash_blocks(gh.Vh), kDslashThreads, 0, st>>>(
+      v2<R>(ap), cv2<R>(to), cv2<R>(te), cv2<R>(p), cv2<R>(r), u, to_devg(gh), R(-k2), partial, cgd);
+  return cudaGetLastError();
+}
+template <typename R, int NC>
+cudaError_t launch_cg_fold(const GeomH& gh, void* to, void* x, const void* r, const void* ap, const void* p,
+                           void* r2, void* p2, const void* U, double* partial, CgDev* cgd, double* hist,
+                           int* iter_out, int maxiter, cudaStream_t st) {
+  Gauge<R, NC> u;
+  u.p = const_cast<void*>(U);
+  u.V = gh.V;
+  cg_fold_kernel<R, NC><<<dslash_blocks(gh.Vh), kDslashThreads, 0, st>>>(
+      v2<R>(to), v2<R>(x), cv2<R>(r), cv2<R>(ap), cv2<R>(p), v2<R>(r2), v2<R>(p2), u, to_devg(gh), partial, cgd,
+      hist, iter_out, maxiter);
+  return cudaGetLastError();
+}
 template <typename RI>
 cudaError_t launch_ru_accumulate(void* x64, void* xs, int n, cudaStream_t st) {
   ru_accumulate_kernel<RI><<<vec_blocks(n), kVecThreads, 0, st>>>((double2*)x64, v2<RI>(xs), n);
@@ -1206,6 +1082,17 @@ template cudaError_t launch_cg_axpy<float>(void*, void*, const void*, const void
                                            cudaStream_t);
 template cudaError_t launch_cg_xpay<double>(void*, const void*, CgDev*, double*, int*, int, int, cudaStream_t);
 template cudaError_t launch_cg_xpay<float>(void*, const void*, CgDev*, double*, int*, int, int, cudaStream_t);
+#define FG_INST_FOLD(R, NC)                                                                                    \
+  template cudaError_t launch_cg_apdot<R, NC>(const GeomH&, void*, const void*, const void*, const void*,      \
+                                              const void*, const void*, double, double*, CgDev*, cudaStream_t); \
+  template cudaError_t launch_cg_fold<R, NC>(const GeomH&, void*, void*, const void*, const void*, const void*, \
+                                             void*, void*, const void*, double*, CgDev*, double*, int*, int,    \
+                                             cudaStream_t);
+FG_INST_FOLD(float, 9)
+FG_INST_FOLD(float, 6)
+FG_INST_FOLD(double, 9)
+FG_INST_FOLD(double, 6)
+#undef FG_INST_FOLD
 template cudaError_t launch_cg_restart<double>(void*, const void*, const CgDev*, int, cudaStream_t);
 template cudaError_t launch_cg_restart<float>(void*, const void*, const CgDev*, int, cudaStream_t);
 template cudaError_t launch_ru_accumulate<double>(void*, void*, int, cudaStream_t);

@@ -24,6 +24,7 @@ struct CgDev {
   int restart;  // set by a reliable update whose true residual left the recursion far behind
   double pap;       // <p, Ap> of the iteration in progress (grand total of the Dslash partials)
   double rr_next;   // |r|^2 after the iteration in progress (grand total of the axpy partials)
+  double beta;      // folded iteration: beta of the update in progress
   unsigned ticket[2];  // blocks finished, for the two grand totals; the last block resets it to 0
   // half-precision inner vectors hold r / sigma and p / sigma; sigma^2 is
   // reset at every reliable update to |r|^2 / n, and rho rescales p then
@@ -118,6 +119,22 @@ cudaError_t launch_ru_publish(const double* part, int n, CgDev* cgd, double* tru
 template <typename R>
 cudaError_t launch_cg_restart(void* p, const void* r, const CgDev* cgd, int n, cudaStream_t st);
 cudaError_t launch_cg_init(const double* part, int n, CgDev* cgd, double tol2, double* bb_out, cudaStream_t st);
+
+// ---- folded CG iteration (FP32 / FP64 inner vectors, links R with NC entries)
+// Ap = te - k2 D_eo^dagger to on the even sites; grand totals of <p, Ap>,
+// Re <r, Ap>, |Ap|^2 through `partial` (3 x dslash_blocks(Vh) entries); the
+// last block sets cgd->alpha = rr / <p, Ap> and
+// cgd->beta = (rr - 2 alpha Re <r, Ap> + alpha^2 |Ap|^2) / rr, rr = cgd->rr[iter & 1].
+template <typename R, int NC>
+cudaError_t launch_cg_apdot(const GeomH& g, void* ap, const void* to, const void* te, const void* p, const void* r,
+                            const void* U, double k2, double* partial, CgDev* cgd, cudaStream_t st);
+// x += alpha p; r2 = r - alpha Ap; p2 = r2 + beta p (even sites) and
+// to = D_oe p2 (odd sites); |r2|^2 published as iteration iter + 1 (rr[],
+// hist, *iter_out, done).  r, p and r2, p2 are different buffers.
+template <typename R, int NC>
+cudaError_t launch_cg_fold(const GeomH& g, void* to, void* x, const void* r, const void* ap, const void* p,
+                           void* r2, void* p2, const void* U, double* partial, CgDev* cgd, double* hist,
+                           int* iter_out, int maxiter, cudaStream_t st);
 // dst = (RO) src, with block partials of |src|^2 if part != nullptr.
 template <typename RO, typename RI>
 cudaError_t launch_convert(void* dst, const void* src, double* part, int n, cudaStream_t st);

@@ -95,8 +95,10 @@ def footprint_bytes(spec: ChainSpec, precision: str = "fp32", link_reals: int = 
     gauge actions, block partials and
     result scalars, the FP64 host-layout staging buffer, and for fermions 8
     FP64 and 10 working half-lattice spinors (plus 2 double-float ones for the
-    FP32 solver's reliable updates), the pseudofermion force, the CG scalars
-    and the Dslash / vector block partials.  4 KiB are added for allocator
+    FP32 solver's reliable updates, and the second r and p buffers of the
+    folded CG iteration unless the inner vectors are half precision), the
+    pseudofermion force, the CG scalars and the Dslash (three values) and
+    vector block partials.  4 KiB are added for allocator
     rounding of the small buffers.  (The closed-form force gradient's
     buffers are not included: the server does not offer that integrator.)
     `l2_bytes` is the GPU's L2 size, which decides FG_FP32_AUTOCG's inner
@@ -112,9 +114,10 @@ def footprint_bytes(spec: ChainSpec, precision: str = "fp32", link_reals: int = 
         n64 = 8 + (2 if precision != "fp64" else 0)
         dslash_blocks = (vh + 127) // 128
         vec_blocks = min((nvec + 255) // 256, 152 * 8)
-        total += n64 * nvec * 16 + 10 * nvec * 2 * r + mom + 128 + 8 * (dslash_blocks + vec_blocks + 2)
         half = precision == "fp32_fp16cg" or (
             precision == "fp32_autocg" and v * (4 * (link_reals // 2) * 8 + 6 * 48) > l2_bytes)
+        n_inner = 10 if half else 12
+        total += n64 * nvec * 16 + n_inner * nvec * 2 * r + mom + 128 + 8 * (3 * dslash_blocks + vec_blocks + 2)
         if half:
             total += 4 * v * link_reals * 2      # half-precision links of the inner solver
     return total + 4096

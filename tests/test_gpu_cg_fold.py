@@ -1,0 +1,119 @@
+"""The folded CG iteration (four launches, the vector updates inside the
+Dslash launches) against the oracle and against the six-launch iteration.
+
+The solver of section 4's even-odd system Mhat^dagger Mhat x = b forms the
+next search direction p' = (r - alpha Ap) + beta p on the fly in the launch
+that applies D_oe to it, and takes beta from the expansion
+|r - alpha Ap|^2 = rr - 2 alpha Re <r, Ap> + alpha^2 |Ap|^2.  Checked here:
+* solutions against the oracle's FP64 CG (normwise relative 1e-7 at cg_tol
+  1e-10) and the certified residual against the oracle's operator on the
+  links the solver holds, from ragged lattices (one partial block) up;
+* iteration counts against the six-launch iteration (within 10% + 2);
+* the same bits with CUDA-graph batches and with single launches (timing on),
+  and on a repeated solve;
+* the launch count: four per iteration, no separate vector kernels.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import fermion as fe
+from paper_0910_2950_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+BETA, KAPPA = 5.6, 0.158
+
+
+@pytest.fixture(scope="module")
+def fgmod():
+    from paper_0910_2950_gb300 import build, fg
+    build.build()
+    fg.load()
+    return fg
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def _rand_even(dims, seed):
+    g = inputs.make_rng(seed)
+    v = inputs.volume(dims)
+    return g.standard_normal((v // 2, 4, 3)) + 1j * g.standard_normal((v // 2, 4, 3))
+
+
+def _solve(fgmod, monkeypatch, dims, precision, link_reals, u, b, fold, timing=False, repeat=1, tol=1e-10):
+    monkeypatch.setenv("FG_CG_FOLD", fold)
+    out = []
+    with fgmod.Lattice(dims, BETA, kappa=KAPPA, precision=precision, link_reals=link_reals, cg_tol=tol) as lat:
+        lat.set_gauge(u)
+        held = lat.get_gauge()  # the links the solver works with (FP32 rounding, 12-real rebuild)
+        lat.timing(timing)
+        for _ in range(repeat):
+            lat.timing_reset()
+            x, info = lat.cg_solve(b)
+            if timing:
+                info["n_dslash"] = lat.kernel_time("dslash")[1]
+                info["n_blas"] = lat.kernel_time("cg_blas")[1]
+            info["links"] = held
+            out.append((x, info))
+    return out
+
+
+@pytest.mark.parametrize("dims", [(6, 4, 2, 6), (4, 4, 4, 4), (8, 8, 8, 8), (8, 8, 8, 16)])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("link_reals", [18, 12])
+def test_folded_cg_matches_the_oracle(fgmod, monkeypatch, dims, precision, link_reals):
+    u = inputs.hot_start(dims, 11)
+    b = _rand_even(dims, 12)
+    tol = 1e-10
+    (x, info), (x2, info2) = _solve(fgmod, monkeypatch, dims, precision, link_reals, u, b, "1", repeat=2)
+    assert info["true_residual"] <= tol and info["iterations"] > 0
+    # deterministic: a repeated solve gives the same bits
+    assert np.array_equal(x, x2) and info["iterations"] == info2["iterations"]
+    res = inputs.unpack_even(b, dims) - fe.mdagm(info["links"], KAPPA, inputs.unpack_even(x, dims))
+    assert np.linalg.norm(res) <= 1.01 * tol * np.linalg.norm(b)
+    if inputs.volume(dims) <= 4096:
+        xo, _ = fe.cg(info["links"], KAPPA, inputs.unpack_even(b, dims), tol=1e-13)
+        assert _rel(x, inputs.pack_even(xo, dims)) < 1e-7
+    # the six-launch iteration on the same system
+    [(xs, infs)] = _solve(fgmod, monkeypatch, dims, precision, link_reals, u, b, "0")
+    assert abs(info["iterations"] - infs["iterations"]) <= 0.1 * infs["iterations"] + 2
+    assert _rel(x, xs) < 1e-7
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_folded_cg_graphs_and_single_launches_agree(fgmod, monkeypatch, precision):
+    """CUDA-graph batches of 2, 4 or 8 iterations (timing off) and one launch
+    at a time (timing on) run the same kernels in the same order: the same
+    bits.  With timing on, every iteration is four Dslash-class launches
+    and the vector kernels appear only in the setup and the reliable
+    updates."""
+    dims = (8, 8, 8, 16)
+    u = inputs.hot_start(dims, 13)
+    b = _rand_even(dims, 14)
+    [(xg, ig)] = _solve(fgmod, monkeypatch, dims, precision, 18, u, b, "1", timing=False)
+    [(xt, it)] = _solve(fgmod, monkeypatch, dims, precision, 18, u, b, "1", timing=True)
+    assert np.array_equal(xg, xt) and ig["iterations"] == it["iterations"]
+    n_iter, n_ru = it["iterations"], it["reliable_updates"]
+    # 4 per iteration (the host queues up to two batches of at most 8 past
+    # convergence, which return at once), one t_o = D_oe p after the setup
+    # and after each reliable update
+    assert 4 * n_iter + 1 + n_ru <= it["n_dslash"] <= 4 * (n_iter + 16) + 1 + n_ru
+    assert it["n_blas"] <= 4 + 3 * n_ru
+
+
+def test_folded_cg_larger_lattice(fgmod, monkeypatch):
+    """12^3 x 24 in FP32: the folded and six-launch solvers agree, and the
+    certified residual holds against the oracle's operator."""
+    dims = (12, 12, 12, 24)
+    u = inputs.hot_start(dims, 15)
+    b = _rand_even(dims, 16)
+    tol = 1e-10
+    [(xf, inf)] = _solve(fgmod, monkeypatch, dims, "fp32", 18, u, b, "1")
+    [(xs, ins)] = _solve(fgmod, monkeypatch, dims, "fp32", 18, u, b, "0")
+    assert abs(inf["iterations"] - ins["iterations"]) <= 0.1 * ins["iterations"] + 2
+    assert _rel(xf, xs) < 1e-7
+    res = inputs.unpack_even(b, dims) - fe.mdagm(inf["links"], KAPPA, inputs.unpack_even(xf, dims))
+    assert np.linalg.norm(res) <= 1.01 * tol * np.linalg.norm(b)
