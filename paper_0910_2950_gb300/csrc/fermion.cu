@@ -291,8 +291,12 @@ __device__ __forceinline__ void fermion_force_link(
   FF.store(MU, s, out);
 }
 
+// Resident blocks of 256 asked of the register allocator (tuning macro).
+#ifndef FG_FFORCE_MIN_BLOCKS
+#define FG_FFORCE_MIN_BLOCKS 1
+#endif
 template <typename RL, int NC, typename RS>
-__global__ void __launch_bounds__(256) fermion_force_kernel(
+__global__ void __launch_bounds__(256, FG_FFORCE_MIN_BLOCKS) fermion_force_kernel(
     Gauge<RL, NC> U, const typename Vec2<RS>::T* __restrict__ Xe, const typename Vec2<RS>::T* __restrict__ Xo,
     const typename Vec2<RS>::T* __restrict__ Ye, const typename Vec2<RS>::T* __restrict__ Yo,
     Mom<RL> FF, Geom g, RL kappa2, int accumulate) {
