@@ -69,6 +69,19 @@ template <> struct TileBounds<64> { static constexpr int min_blocks = 1; };
 template <typename R, int H>
 constexpr int kBatchMinBlocks = std::is_same<R, DF>::value ? (H == 16 ? 2 : 1) : TileBounds<H>::min_blocks;
 
+// Double-float links: a block barrier after each tile keeps the warps of an
+// SM on the same tile.  Left to drift apart, some warps run the staple
+// products while others run the exponential, and the two long code paths
+// together overflow the instruction cache: a 64-chain FG trajectory took
+// 80 ms without the barrier and 45 ms with it.  FG_BATCH_TILE_SYNC (tuning
+// macro): 0 no barrier, 1 double-float only, 2 also FP32.
+#ifndef FG_BATCH_TILE_SYNC
+#define FG_BATCH_TILE_SYNC 1
+#endif
+template <typename R>
+constexpr bool kTileSync =
+    (std::is_same<R, DF>::value && FG_BATCH_TILE_SYNC >= 1) || (std::is_same<R, float>::value && FG_BATCH_TILE_SYNC >= 2);
+
 template <typename R, int NC, int MODE, int H>
 __global__ void __launch_bounds__(8 * H, (kBatchMinBlocks<R, H>))
     batch_force_kernel(const Tile* __restrict__ tiles, int ntiles, const ChainDesc* __restrict__ chains,
@@ -80,7 +93,7 @@ __global__ void __launch_bounds__(8 * H, (kBatchMinBlocks<R, H>))
     const Geom g = cd.g;
     int s;
     const bool ok = tile_site<H>(t, g, s);
-    if (!kForceSharedT<R, NC> && !ok) continue;
+    if (!kForceSharedT<R, NC> && !kTileSync<R> && !ok) continue;
     Gauge<R, NC> u, ub, uo;
     u.p = U + cd.goff; u.V = g.V;
     ub.p = Ubase ? Ubase + cd.goff : nullptr; ub.V = g.V;
@@ -97,10 +110,13 @@ __global__ void __launch_bounds__(8 * H, (kBatchMinBlocks<R, H>))
                                          uo, g, R(cd.beta / 6.0), R(ckick), R(cdrift), R(cdisp), reunit, R(1));
       __syncthreads();   // the next tile rewrites the slots
     } else {
-      int c[4], par;
-      cb_coords(g, s, c, par);
-      force_link<R, NC, MODE>(u, p, f, ff, ub, uo, g, c, s, (int)threadIdx.y, R(cd.beta / 6.0), R(ckick),
-                              R(cdrift), R(cdisp), reunit);
+      if (ok) {
+        int c[4], par;
+        cb_coords(g, s, c, par);
+        force_link<R, NC, MODE>(u, p, f, ff, ub, uo, g, c, s, (int)threadIdx.y, R(cd.beta / 6.0), R(ckick),
+                                R(cdrift), R(cdisp), reunit);
+      }
+      if constexpr (kTileSync<R>) __syncthreads();  // every thread of the block runs the same tiles
     }
   }
 }
