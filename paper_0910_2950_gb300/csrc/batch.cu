@@ -809,7 +809,10 @@ class Batch final : public IBatch {
       float tmin = 1e30f;
       for (int rep = 0; rep < 4; ++rep) {
         cudaEventRecord(a, st_);
-        fg_status s = force(FM_STORE, buf_[cur_], nullptr, nullptr, 0, 0, 0);
+        // a displacement into a scratch buffer: the force and the exponential,
+        // as in the kick-and-drift and displace launches that dominate a
+        // trajectory (the exponential's code decides the tile for double-float)
+        fg_status s = force(FM_DISPLACE, buf_[cur_], nullptr, buf_[(cur_ + 1) % 3], 0, 0, 0.01);
         if (s != FG_OK) {
           cudaEventDestroy(a);
           cudaEventDestroy(b);
