@@ -597,8 +597,34 @@ class Backend final : public IBackend {
     }
     return gauge_launch(mode, a);
   }
-  // The fused gauge-force kernel with whatever a.FF holds (no solve).
+  // The fused gauge-force kernel with whatever a.FF holds (no solve).  With
+  // split_exp_ (the default for double-float) the exponential of a
+  // kick-and-drift or a displacement runs in a launch of its own after the
+  // force (the same arithmetic, the same bits): the staple products and the
+  // double-float exponential together overflow the instruction cache, and
+  // the split takes 16-21% off a double-float trajectory, while FP32 runs 9%
+  // faster fused.  FG_SPLIT_EXP=0 / =1 in the environment turns the split
+  // off / on for any precision.
+  const bool split_exp_ = [] {
+    const char* e = std::getenv("FG_SPLIT_EXP");
+    return e ? e[0] == '1' : std::is_same<R, DF>::value;
+  }();
   fg_status gauge_launch(int mode, const ForceArgs& a) {
+    if (split_exp_ && (mode == FM_KICK_DRIFT || mode == FM_DISPLACE)) {
+      ForceArgs f = a;
+      fg_status s;
+      if (mode == FM_KICK_DRIFT) {
+        if ((s = run(KC_GAUGE_FORCE, [&] { return launch_gauge_force<R, NC>(g_, FM_KICK, f, st_); })) != FG_OK)
+          return s;
+        return run(KC_DRIFT, [&] {
+          return launch_drift<R, NC>(g_, a.Ubase, P_, a.Uout, a.cdrift, a.reunit, st_);
+        });
+      }
+      f.F = F_;
+      if ((s = run(KC_GAUGE_FORCE, [&] { return launch_gauge_force<R, NC>(g_, FM_STORE, f, st_); })) != FG_OK)
+        return s;
+      return run(KC_DRIFT, [&] { return launch_drift<R, NC>(g_, a.U, F_, a.Uout, -a.cdisp, 0, st_); });
+    }
     return run(KC_GAUGE_FORCE, [&] { return launch_gauge_force<R, NC>(g_, mode, a, st_); });
   }
 

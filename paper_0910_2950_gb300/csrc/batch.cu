@@ -658,7 +658,29 @@ class Batch final : public IBatch {
       return cudaGetLastError();
     });
   }
+  // Double-float: the exponential of a kick-and-drift or a displacement runs
+  // in a launch of its own after the force (the same arithmetic, the same
+  // bits); the two long code paths in one launch overflow the instruction
+  // cache.  FG_SPLIT_EXP=0 / =1 in the environment turns the split off / on
+  // for any precision.
+  const bool split_exp_ = [] {
+    const char* e = std::getenv("FG_SPLIT_EXP");
+    return e ? e[0] == '1' : std::is_same<R, DF>::value;
+  }();
   fg_status force(int mode, void* U, void* Ubase, void* Uout, double ckick, double cdrift, double cdisp) {
+    if (split_exp_ && mode == FM_KICK_DRIFT) {
+      fg_status s = force_tiles(FM_KICK, U, nullptr, nullptr, ckick, 0, 0);
+      if (s != FG_OK) return s;
+      return drift(Ubase, Uout, cdrift);
+    }
+    if (split_exp_ && mode == FM_DISPLACE) {
+      fg_status s = force_tiles(FM_STORE, U, nullptr, nullptr, 0, 0, 0);
+      if (s != FG_OK) return s;
+      return drift(U, Uout, -cdisp, F_, 0);
+    }
+    return force_tiles(mode, U, Ubase, Uout, ckick, cdrift, cdisp);
+  }
+  fg_status force_tiles(int mode, void* U, void* Ubase, void* Uout, double ckick, double cdrift, double cdisp) {
     switch (hsel_) {
       case 0: return force_h<16>(0, mode, U, Ubase, Uout, F_, ckick, cdrift, cdisp);
       case 2:
@@ -667,24 +689,27 @@ class Batch final : public IBatch {
       default: return force_h<32>(1, mode, U, Ubase, Uout, F_, ckick, cdrift, cdisp);
     }
   }
+  // Uout = exp(i c G) Uin for the generator G (the momenta, or the force
+  // buffer for a displacement); reunit < 0: the handle's setting.
   template <int H>
-  fg_status drift_h(int hi, void* Uin, void* Uout, double c) {
+  fg_status drift_h(int hi, void* Uin, void* Uout, double c, void* G, int reunit) {
     const int nt = ntiles_[hi];
-    const int reunit = b_->prm.reunitarize;
     return lrun([&] {
       batch_drift_kernel<R, NC, H><<<grid(nt, 2), dim3(2 * H, 4), 0, st_>>>(d_tiles_[hi], nt, d_chains_h_[hi],
-                                                                            (char*)Uin, (char*)P_, (char*)Uout, c,
+                                                                            (char*)Uin, (char*)G, (char*)Uout, c,
                                                                             reunit);
       return cudaGetLastError();
     });
   }
-  fg_status drift(void* Uin, void* Uout, double c) {
+  fg_status drift(void* Uin, void* Uout, double c, void* G = nullptr, int reunit = -1) {
+    if (G == nullptr) G = P_;
+    if (reunit < 0) reunit = b_->prm.reunitarize;
     switch (hsel_) {
-      case 0: return drift_h<16>(0, Uin, Uout, c);
+      case 0: return drift_h<16>(0, Uin, Uout, c, G, reunit);
       case 2:
-        if constexpr (kTileSizes > 2) return drift_h<64>(2, Uin, Uout, c);
+        if constexpr (kTileSizes > 2) return drift_h<64>(2, Uin, Uout, c, G, reunit);
         [[fallthrough]];
-      default: return drift_h<32>(1, Uin, Uout, c);
+      default: return drift_h<32>(1, Uin, Uout, c, G, reunit);
     }
   }
   template <int H>
