@@ -67,7 +67,8 @@ template <> struct TileBounds<64> { static constexpr int min_blocks = 1; };
 // Register cap of the force kernel: 128 per thread for FP32 and FP64 links;
 // double-float links get up to 255 (as in the single-lattice kernel).
 template <typename R, int H>
-constexpr int kBatchMinBlocks = std::is_same<R, DF>::value ? (H == 16 ? 2 : 1) : TileBounds<H>::min_blocks;
+constexpr int kBatchMinBlocks =
+    std::is_same<R, DF>::value ? (H == 16 ? 2 * FG_FORCE_DF_MIN_BLOCKS : FG_FORCE_DF_MIN_BLOCKS) : TileBounds<H>::min_blocks;
 
 // Double-float links: a block barrier after each tile keeps the warps of an
 // SM on the same tile.  Left to drift apart, some warps run the staple

@@ -229,10 +229,13 @@ __device__ __forceinline__ void force_link(const Gauge<R, NC>& U, const Mom<R>& 
 template <typename R, int NC>
 constexpr bool kForceSharedT = FG_FORCE_SHARED_T && std::is_same<R, float>::value && NC == 6;
 #ifndef FG_FORCE_DF_MIN_BLOCKS
-#define FG_FORCE_DF_MIN_BLOCKS 1
+#define FG_FORCE_DF_MIN_BLOCKS 2
 #endif
-// Double-float links need about twice the registers of FP32 ones: one block
-// of 256 threads per SM, up to 255 registers a thread.
+// Double-float links need about twice the registers of FP32 ones.  With the
+// exponential in a launch of its own the force launch fits two blocks of
+// 256 threads per SM (128 registers a thread): 2-3% faster than one block
+// with up to 255 registers (32^4 trajectory 34.7 against 35.5 ms, 64-chain
+// batch 39.7 against 40.5 ms).
 template <typename R, int NC>
 constexpr int kForceMinBlocks = std::is_same<R, DF>::value
                                     ? FG_FORCE_DF_MIN_BLOCKS
