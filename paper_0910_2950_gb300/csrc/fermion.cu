@@ -192,9 +192,25 @@ __global__ void __launch_bounds__(kDslashThreads, DslashMinBlocks<R>::value) cg_
     const typename Vec2<R>::T* __restrict__ p, typename Vec2<R>::T* __restrict__ r2,
     typename Vec2<R>::T* __restrict__ p2, Gauge<R, NC> U, Geom g, double* __restrict__ partial,
     CgDev* __restrict__ cgd, double* __restrict__ hist, int* __restrict__ iter_out, int maxiter) {
-  if (cgd->done) return;
-  const FoldSrc<R> src{r, ap, p, R(cgd->alpha), R(cgd->beta)};
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cgd->done) {
+    // no iteration after convergence, but the host has already taken r2, p2
+    // as the current buffers (a certification that finds the FP64 residual
+    // still too large continues from them): move r and p there
+    if (i < g.Vh) {
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        const size_t j = (size_t)q * g.Vh + i;
+        Cx<R> a0, a1;
+        Quad<R>::load(r, j, a0, a1);
+        Quad<R>::store(r2, j, a0, a1);
+        Quad<R>::load(p, j, a0, a1);
+        Quad<R>::store(p2, j, a0, a1);
+      }
+    }
+    return;
+  }
+  const FoldSrc<R> src{r, ap, p, R(cgd->alpha), R(cgd->beta)};
   R acc = R(0);
   if (i < g.Vh) {
     // the even site i: x, r', p'
