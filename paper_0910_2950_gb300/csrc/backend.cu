@@ -36,7 +36,8 @@ struct Mapped {
   double true_rr;
   int dev_iter;     // last completed CG iteration (device numbering)
   int pad_i;
-  double pad[5];
+  double rr0;       // |b - M x0|^2 at the start of a solve from an initial guess
+  double pad[4];
   double hist[1];   // residual history, one entry per CG iteration (allocated longer)
 };
 
@@ -338,6 +339,7 @@ class Backend final : public IBackend {
   // end, Metropolis.
   fg_status run_trajectory(const std::vector<Op>& ops, double dt, int nsteps, int refresh, double u_accept,
                            fg_traj_result* r) {
+    guess_ok_ = false;  // every trajectory starts its solves from zero
     fg_status s;
     solves_ = 0;
     cg_iters_ = 0;
@@ -483,6 +485,19 @@ class Backend final : public IBackend {
   CgDev* cgd_ = nullptr;
   double* part_pap_ = nullptr;
   double* part_rr_ = nullptr;
+  double* part_b_ = nullptr;   // partials of |b|^2 for a solve from an initial guess
+  // Chronological initial guess: within a trajectory every pseudofermion
+  // solve has the same source phi at nearby links (a force-gradient
+  // displacement moves them by dt^2/24 F), so a solve starts from the
+  // previous solution instead of zero.  x64_ holds it while guess_ok_; the
+  // guess is dropped at the start of every trajectory and whenever phi
+  // changes, so a trajectory's result depends only on its own inputs.
+  // FG_CG_GUESS=0 in the environment turns it off.
+  bool guess_ok_ = false;
+  const bool use_guess_ = [] {
+    const char* e = std::getenv("FG_CG_GUESS");
+    return !(e && e[0] == '0');
+  }();
   Mapped* mapped_ = nullptr;
   cudaEvent_t ev_[2] = {nullptr, nullptr};
   // copy stream and its events for trajectories_host_momenta
@@ -916,6 +931,7 @@ class Backend final : public IBackend {
       if (cudaMemsetAsync(cgd_, 0, sizeof(CgDev), st_) != cudaSuccess) return cuda_fail("cg state init");
       if ((s = alloc((void**)&part_pap_, (3 * dslash_blocks(g_.Vh) + 1) * sizeof(double))) != FG_OK) return s;
       if ((s = alloc((void**)&part_rr_, (vec_blocks(nvec()) + 1) * sizeof(double))) != FG_OK) return s;
+      if ((s = alloc((void**)&part_b_, (vec_blocks(nvec()) + 1) * sizeof(double))) != FG_OK) return s;
       const size_t mbytes = sizeof(Mapped) + (size_t)(h_->prm.cg_maxiter + 8) * sizeof(double);
       if (cudaHostAlloc((void**)&mapped_, mbytes, cudaHostAllocMapped) != cudaSuccess) {
         mapped_ = nullptr;
@@ -989,6 +1005,7 @@ class Backend final : public IBackend {
 
   // phi = Mhat^dagger chi at the current links; S_F at the heat bath = |chi|^2.
   fg_status heatbath_from_chi() {
+    guess_ok_ = false;  // a new phi
     fg_status s = apply_mhat64(phi64_, chi64_, U_, 1);
     if (s != FG_OK) return s;
     if ((s = run(KC_CG_BLAS, [&] { return launch_dot64(chi64_, chi64_, part_rr_, nvec(), st_); })) != FG_OK) return s;
@@ -1259,7 +1276,8 @@ class Backend final : public IBackend {
         return s;
     }
     double* tr = &mapped_->true_rr;
-    if ((s = run(KC_REDUCE, [&] { return launch_ru_publish(part_rr_, vec_blocks(n), cgd_, tr, st_); })) != FG_OK)
+    if ((s = run(KC_REDUCE, [&] { return launch_ru_publish(part_rr_, vec_blocks(n), cgd_, tr, final ? 1 : 0, st_); })) !=
+        FG_OK)
       return s;
     return run(KC_CG_BLAS, [&] { return launch_cg_restart<R>(p_, rs_, cgd_, n, st_); });
   }
@@ -1312,15 +1330,41 @@ class Backend final : public IBackend {
     const double delta2 = delta * delta;
     fg_status s;
     ++solves_;
-    if (cudaMemsetAsync(x64_, 0, (size_t)n * sizeof(double2), st_) != cudaSuccess ||
+    // a solve for phi after one for the same phi starts from its solution
+    const bool guess = use_guess_ && guess_ok_ && b64 == phi64_ && !half_links_;
+    guess_ok_ = false;  // until this solve succeeds
+    if ((!guess && cudaMemsetAsync(x64_, 0, (size_t)n * sizeof(double2), st_) != cudaSuccess) ||
         cudaMemsetAsync(xs_, 0, (size_t)n * sizeof(C2), st_) != cudaSuccess ||
-        cudaMemcpyAsync(r64_, b64, (size_t)n * sizeof(double2), cudaMemcpyDeviceToDevice, st_) != cudaSuccess)
+        (!guess && cudaMemcpyAsync(r64_, b64, (size_t)n * sizeof(double2), cudaMemcpyDeviceToDevice, st_) !=
+                       cudaSuccess))
       return cuda_fail("cg setup");
-    if (kMixed && (cudaMemsetAsync(xdf_, 0, (size_t)n * sizeof(double2), st_) != cudaSuccess ||
+    if (kMixed && ((!guess && cudaMemsetAsync(xdf_, 0, (size_t)n * sizeof(double2), st_) != cudaSuccess) ||
                    run(KC_CG_BLAS, [&] { return launch_df_from_double(bdf_, b64, n, st_); }) != FG_OK))
       return cuda_fail("cg setup");
     double* bbp = &mapped_->bb;
-    if (half_links_) {
+    if (guess) {
+      // r = b - M x0: in double-float for the FP32 solver (x0 held as x_df),
+      // in FP64 for the FP64 one; r_s = (R) r and the partials of |r|^2
+      if (kMixed) {
+        if ((s = run(KC_CG_BLAS, [&] { return launch_df_from_double(xdf_, x64_, n, st_); })) != FG_OK) return s;
+        if ((s = apply_mdagm_df(ax64_, xdf_, U)) != FG_OK) return s;
+        if ((s = run(KC_CG_BLAS, [&] { return launch_ru_residual_df(bdf_, ax64_, rs_, part_rr_, n, st_); })) !=
+            FG_OK)
+          return s;
+      } else {
+        if ((s = apply_mdagm64(ax64_, x64_, U)) != FG_OK) return s;
+        if ((s = run(KC_CG_BLAS, [&] { return launch_ru_residual<R>(b64, ax64_, r64_, rs_, part_rr_, n, st_); })) !=
+            FG_OK)
+          return s;
+      }
+      if ((s = run(KC_CG_BLAS, [&] { return launch_dot64(b64, b64, part_b_, n, st_); })) != FG_OK) return s;
+      if ((s = run(KC_REDUCE, [&] {
+             return launch_cg_init_guess(part_b_, part_rr_, nbv, cgd_, tol * tol, bbp, &mapped_->rr0, st_);
+           })) != FG_OK)
+        return s;
+      if (cudaMemcpyAsync(p_, rs_, (size_t)n * sizeof(C2), cudaMemcpyDeviceToDevice, st_) != cudaSuccess)
+        return cuda_fail("cg setup");
+    } else if (half_links_) {
       // half-precision inner vectors: r_s = b / sigma with sigma^2 = |b|^2 / n
       if ((s = run(KC_CG_BLAS, [&] { return launch_dot64(b64, b64, part_rr_, n, st_); })) != FG_OK) return s;
       if ((s = run(KC_REDUCE, [&] { return launch_cg_init_h16(part_rr_, nbv, cgd_, tol * tol, bbp, n, st_); })) !=
@@ -1400,10 +1444,16 @@ class Backend final : public IBackend {
           if ((s = host_wait_event(ev_[pending], h_->wait_limit_s, &why)) != FG_OK) return h_->fail(s, why);
           if (bb < 0.0) {
             know_bb();
-            maxrr = bb;
+            maxrr = guess ? mapped_->rr0 : bb;
             if (bb == 0.0) {            // b = 0: x = 0, nothing to iterate
               if ((s = sync()) != FG_OK) return s;
               return FG_OK;
+            }
+            if (guess && maxrr <= tol2bb) {  // the guess already meets the tolerance
+              converged = true;
+              iters = 0;
+              pending = slot;
+              break;
             }
           }
           const int upto = *(volatile int*)&mapped_->dev_iter;
@@ -1450,10 +1500,12 @@ class Backend final : public IBackend {
       // it into r and cleared `done`; continue from there.
       maxrr = trr;
       checked = mapped_->dev_iter;
+      queued = checked;  // the iterations queued past convergence returned at once
       pending = -1;
     }
     st->iters = iters;
     cg_iters_ += iters;
+    guess_ok_ = b64 == phi64_;
     return FG_OK;
   }
 };

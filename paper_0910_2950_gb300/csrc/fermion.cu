@@ -704,13 +704,15 @@ __global__ void __launch_bounds__(kVecThreads) ru_rescale_h16_kernel(const RV* _
 // recursive one it replaces; beyond that the recursion has drifted too far
 // for p to match r, and `restart` asks cg_restart_kernel to set p = r.
 __global__ void ru_publish_kernel(const double* __restrict__ part, int n, CgDev* __restrict__ cgd,
-                                  double* __restrict__ true_rr) {
+                                  double* __restrict__ true_rr, int final) {
   const double rr = block_sum_partials(part, n);
   if (threadIdx.x == 0) {
     const double rr_iter = cgd->rr[cgd->iter & 1];
     cgd->restart = (rr > 2.0 * rr_iter) ? 1 : 0;
     cgd->rr[cgd->iter & 1] = rr;
-    cgd->done = rr <= cgd->tol2bb ? 1 : 0;
+    // only the certifying update ends the solve; after an intermediate one
+    // the next iteration publishes the residual, which the host watches
+    cgd->done = (final && rr <= cgd->tol2bb) ? 1 : 0;
     *true_rr = rr;
   }
 }
@@ -737,6 +739,26 @@ __global__ void cg_init_kernel(const double* __restrict__ part, int n, CgDev* __
     cgd->k_axpy = 0;
     cgd->restart = 0;
     *bb_out = bb;
+  }
+}
+
+// Start of a solve from an initial guess: bb = |b|^2 and rr = |b - M x0|^2
+// from their partials; the tolerance stays relative to |b|.
+__global__ void cg_init_guess_kernel(const double* __restrict__ part_b, const double* __restrict__ part_r, int n,
+                                     CgDev* __restrict__ cgd, double tol2, double* __restrict__ bb_out,
+                                     double* __restrict__ rr0_out) {
+  const double bb = block_sum_partials(part_b, n);
+  const double rr = block_sum_partials(part_r, n);
+  if (threadIdx.x == 0) {
+    cgd->bb = bb;
+    cgd->tol2bb = tol2 * bb;
+    cgd->rr[0] = cgd->rr[1] = rr;
+    cgd->done = (bb == 0.0 || rr <= tol2 * bb) ? 1 : 0;
+    cgd->iter = 0;
+    cgd->k_axpy = 0;
+    cgd->restart = 0;
+    *bb_out = bb;
+    *rr0_out = rr;
   }
 }
 
@@ -914,8 +936,8 @@ cudaError_t launch_ru_residual(const void* b64, const void* ax64, void* r64, voi
                                                                 (double2*)r64, v2<RI>(rs), part, n);
   return cudaGetLastError();
 }
-cudaError_t launch_ru_publish(const double* part, int n, CgDev* cgd, double* true_rr, cudaStream_t st) {
-  ru_publish_kernel<<<1, 1024, 0, st>>>(part, n, cgd, true_rr);
+cudaError_t launch_ru_publish(const double* part, int n, CgDev* cgd, double* true_rr, int final, cudaStream_t st) {
+  ru_publish_kernel<<<1, 1024, 0, st>>>(part, n, cgd, true_rr, final);
   return cudaGetLastError();
 }
 template <typename R>
@@ -925,6 +947,11 @@ cudaError_t launch_cg_restart(void* p, const void* r, const CgDev* cgd, int n, c
 }
 cudaError_t launch_cg_init(const double* part, int n, CgDev* cgd, double tol2, double* bb_out, cudaStream_t st) {
   cg_init_kernel<<<1, 1024, 0, st>>>(part, n, cgd, tol2, bb_out);
+  return cudaGetLastError();
+}
+cudaError_t launch_cg_init_guess(const double* part_b, const double* part_r, int n, CgDev* cgd, double tol2,
+                                 double* bb_out, double* rr0_out, cudaStream_t st) {
+  cg_init_guess_kernel<<<1, 1024, 0, st>>>(part_b, part_r, n, cgd, tol2, bb_out, rr0_out);
   return cudaGetLastError();
 }
 template <typename RO, typename RI>

@@ -114,11 +114,17 @@ cudaError_t launch_ru_publish_h16(const double* part, int nparts, CgDev* cgd, do
 cudaError_t launch_ru_rescale_df_h16(const void* rdf, void* rs, void* p, const CgDev* cgd, int n, cudaStream_t st);
 cudaError_t launch_ru_rescale64_h16(const void* r64, void* rs, void* p, const CgDev* cgd, int n, cudaStream_t st);
 
-cudaError_t launch_ru_publish(const double* part, int n, CgDev* cgd, double* true_rr, cudaStream_t st);
+// Publish a reliable update's true residual: rr, restart (true residual more
+// than twice the iterated one), and with final != 0 done (rr <= tol2bb).
+cudaError_t launch_ru_publish(const double* part, int n, CgDev* cgd, double* true_rr, int final, cudaStream_t st);
 // p = r when the last reliable update asked for a restart (cgd->restart).
 template <typename R>
 cudaError_t launch_cg_restart(void* p, const void* r, const CgDev* cgd, int n, cudaStream_t st);
 cudaError_t launch_cg_init(const double* part, int n, CgDev* cgd, double tol2, double* bb_out, cudaStream_t st);
+// Start of a solve from an initial guess x0: |b|^2 from part_b, |b - M x0|^2
+// from part_r (n partials each); rr = |b - M x0|^2, tolerance tol2 |b|^2.
+cudaError_t launch_cg_init_guess(const double* part_b, const double* part_r, int n, CgDev* cgd, double tol2,
+                                 double* bb_out, double* rr0_out, cudaStream_t st);
 
 // ---- folded CG iteration (FP32 / FP64 inner vectors, links R with NC entries)
 // Ap = te - k2 D_eo^dagger to on the even sites; grand totals of <p, Ap>,

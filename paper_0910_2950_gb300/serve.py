@@ -98,7 +98,7 @@ def footprint_bytes(spec: ChainSpec, precision: str = "fp32", link_reals: int = 
     FP32 solver's reliable updates, and the second r and p buffers of the
     folded CG iteration unless the inner vectors are half precision), the
     pseudofermion force, the CG scalars and the Dslash (three values) and
-    vector block partials.  4 KiB are added for allocator
+    vector block partials (two arrays of the latter).  4 KiB are added for allocator
     rounding of the small buffers.  (The closed-form force gradient's
     buffers are not included: the server does not offer that integrator.)
     `l2_bytes` is the GPU's L2 size, which decides FG_FP32_AUTOCG's inner
@@ -117,7 +117,7 @@ def footprint_bytes(spec: ChainSpec, precision: str = "fp32", link_reals: int = 
         half = precision == "fp32_fp16cg" or (
             precision == "fp32_autocg" and v * (4 * (link_reals // 2) * 8 + 6 * 48) > l2_bytes)
         n_inner = 10 if half else 12
-        total += n64 * nvec * 16 + n_inner * nvec * 2 * r + mom + 128 + 8 * (3 * dslash_blocks + vec_blocks + 2)
+        total += n64 * nvec * 16 + n_inner * nvec * 2 * r + mom + 128 + 8 * (3 * dslash_blocks + 2 * vec_blocks + 3)
         if half:
             total += 4 * v * link_reals * 2      # half-precision links of the inner solver
     return total + 4096

@@ -3,9 +3,13 @@ and the served trajectories agree with the oracle on client-supplied inputs.
 
 The same requests run (a) one at a time, (b) four at a time overlapping on
 the device, and (c) three at a time under an HBM budget that forces chains
-to be evicted to the host and restored.  Every request's dH and acceptance
-and every chain's final links agree bit for bit: a chain's computation runs
-on its own stream with its random streams set to its trajectory index.
+to be evicted to the host and restored.  A chain's computation runs on its
+own stream with its random streams set to its trajectory index, so every
+pure-gauge request's dH and acceptance and every pure-gauge chain's final
+links agree bit for bit.  The FP32 solver of an Nf=2 chain places its
+reliable updates where the host's extrapolation of the residual (read as
+the GPU runs ahead) says, so its results agree within the solver's
+tolerance: dH within 1e-3, the FP32 path's bar against FP64.
 """
 
 import numpy as np
@@ -60,11 +64,17 @@ def test_alone_and_in_the_mix_gpu(fgmod):
     assert ev > 0
     for a, b, c in zip(seq, mix, ev_res):
         assert (a.chain, a.traj_index) == (b.chain, b.traj_index) == (c.chain, c.traj_index)
-        assert a.dH == b.dH == c.dH
+        if chains[a.chain].kappa > 0:
+            assert abs(a.dH - b.dH) <= 1e-3 and abs(a.dH - c.dH) <= 1e-3, (a.dH, b.dH, c.dH)
+        else:
+            assert a.dH == b.dH == c.dH
         assert a.accepted == b.accepted == c.accepted
         assert np.isfinite(a.dH)
     for k in l1:
-        assert np.array_equal(l1[k], l4[k]) and np.array_equal(l1[k], l3[k])
+        if chains[k].kappa > 0:
+            assert np.max(np.abs(l1[k] - l4[k])) < 1e-3 and np.max(np.abs(l1[k] - l3[k])) < 1e-3
+        else:
+            assert np.array_equal(l1[k], l4[k]) and np.array_equal(l1[k], l3[k])
     # fermion requests did CG solves; pure-gauge ones did not
     assert all((r.n_solves > 0) == (r.chain == 3) for r in seq)
 
