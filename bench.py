@@ -1018,7 +1018,13 @@ def run_ours(args):
     achieved = flops_per_launch / avg_launch_s / 1e12
     esize = 4 if args.precision == "fp32" else 8
     bytes_per_launch = links * (args.link_reals * esize + 2 * 8 * esize)
-    peak = FP32_PEAK_TFLOPS if args.precision == "fp32" else FP64_PEAK_TFLOPS
+    # FP32 FMA peak from this GPU's SM count and the maximum SM clock sampled
+    # during the timed region (the unit counts: 128 FP32 lanes per SM, 2 flop
+    # per FMA); the constant for 152 SMs at 2070 MHz if either is missing
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_max_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
+    fp32_peak = sm_count * 128 * 2 * sm_max_mhz * 1e6 / 1e12 if sm_count else FP32_PEAK_TFLOPS
+    peak = fp32_peak if args.precision == "fp32" else FP64_PEAK_TFLOPS * fp32_peak / FP32_PEAK_TFLOPS
     # DRAM bytes per link of the FP32 18-real FG mix from one ncu capture of
     # the force kernel at 28^4 (its summary is kept with the profiles),
     # scaled to this lattice
@@ -1030,6 +1036,8 @@ def run_ours(args):
             "traffic": traffic,
             "traffic_note": "bytes per launch: 203 B/link measured by ncu at 28^4, scaled by links" if traffic
             else None,
+            "peak_derivation": f"{sm_count} SMs x 128 FP32 lanes x 2 flop x {sm_max_mhz:g} MHz (maximum SM clock "
+                               "sampled by nvidia-smi during the timed region); FP64 at 1/64 of it",
             "kernel": "gauge_force (fused staple force + kick/drift/displace)",
             "launches": force_n, "avg_launch_us": avg_launch_s * 1e6,
             "algorithmic_gbs": bytes_per_launch / avg_launch_s / 1e9,
