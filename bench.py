@@ -1076,11 +1076,15 @@ def run_ours(args):
         ncanon_u = lat.V * 4 * 18
         ncanon_p = lat.V * 4 * 8
         hu = torch.empty(ncanon_u, dtype=torch.float64, pin_memory=True).numpy()
-        hp = torch.empty(ncanon_p, dtype=torch.float64, pin_memory=True).numpy()
+        # an FP32 chain takes its momenta as FP32 (the precision it holds them
+        # in): half the bytes of the FP64 canonical arrays
+        pdt = torch.float32 if args.precision == "fp32" else torch.float64
+        p_bytes = 4 if args.precision == "fp32" else 8
+        hp = torch.empty(ncanon_p, dtype=pdt, pin_memory=True).numpy()
         hu[:] = lat.get_gauge().view(np.float64).ravel()
         rng = inputs.make_rng(seeds["e2e_momenta"])
         hp[:] = rng.standard_normal(ncanon_p)
-        hp2 = torch.empty(ncanon_p, dtype=torch.float64, pin_memory=True).numpy()
+        hp2 = torch.empty(ncanon_p, dtype=pdt, pin_memory=True).numpy()
         hp2[:] = rng.standard_normal(ncanon_p)
         moms = [hp if k % 2 == 0 else hp2 for k in range(args.steps)]
         lat.set_gauge(hu)
@@ -1118,12 +1122,12 @@ def run_ours(args):
         torch.cuda.synchronize()
         e2e_sl = reduce_max(time.perf_counter() - t0, world, "cuda")
         e2e = {"value": whole_job_rate(args.steps, world, e2e_s), "unit": UNIT,
-               "h2d_bytes_per_step": ncanon_p * 8,
+               "h2d_bytes_per_step": ncanon_p * p_bytes,
                "d2h_bytes_per_step": 6 * 8,
-               "note": "per trajectory through fg_trajectories_host_momenta: momenta uploaded from pinned "
-                       "host memory (canonical FP64) on a copy stream while the previous trajectory runs, "
-                       "trajectory run on the device-resident chain, result (dH, H0, H1 sums, accept) read "
-                       "back after each trajectory",
+               "note": "per trajectory through fg_trajectories_host_momenta(_f32): momenta uploaded from pinned "
+                       "host memory (canonical, in the chain's precision: FP32 for an FP32 chain) on a copy "
+                       "stream while the previous trajectory runs, trajectory run on the device-resident chain, "
+                       "result (dH, H0, H1 sums, accept) read back after each trajectory",
                "sequential": {"value": whole_job_rate(args.steps, world, e2e_seq), "unit": UNIT,
                               "h2d_bytes_per_step": ncanon_p * 8, "d2h_bytes_per_step": 6 * 8,
                               "note": "fg_set_momenta then fg_trajectory per trajectory: upload, conversion "

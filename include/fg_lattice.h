@@ -263,6 +263,13 @@ fg_status fg_trajectory_nested(fg_lattice *h, fg_integrator outer, fg_integrator
 fg_status fg_trajectories_host_momenta(fg_lattice *h, fg_integrator integ, double dt, double tau, int n,
                                        const double *const *host_p8, const double *u_accept,
                                        fg_traj_result *out);
+/* The same with FP32 host momenta (canonical layout, 4 V 8 floats each):
+ * half the bytes to upload.  An FP32 handle holds its momenta in FP32, so
+ * its trajectories are the same bits as from the FP64 arrays rounded to
+ * FP32; FP64 and double-float handles widen the FP32 values exactly. */
+fg_status fg_trajectories_host_momenta_f32(fg_lattice *h, fg_integrator integ, double dt, double tau, int n,
+                                           const float *const *host_p8, const double *u_accept,
+                                           fg_traj_result *out);
 
 /* Building blocks for callers and tests (even-site spinors, host layout above). */
 /* out = Mhat in (dagger = 0) or Mhat^dagger in (dagger = 1). */

@@ -126,7 +126,7 @@ class Backend final : public IBackend {
   // (into the other half of the canonical staging buffer, on a copy stream)
   // overlaps trajectory k on st_.  Each half is rewritten only after the
   // conversion that read it two trajectories earlier has run.
-  fg_status trajectories_host_momenta(int integ, double dt, int nsteps, int n, const double* const* hp,
+  fg_status trajectories_host_momenta(int integ, double dt, int nsteps, int n, const void* const* hp, int f32,
                                       const double* u, fg_traj_result* out) override {
     if (n <= 0) return FG_OK;
     const size_t nd = (size_t)4 * g_.V * 8;
@@ -134,10 +134,11 @@ class Backend final : public IBackend {
     if (s != FG_OK) return s;
     if ((s = ensure_copy_stream()) != FG_OK) return s;
     double* const stage[2] = {canon_, canon_ + nd};
+    const size_t bytes = nd * (f32 ? sizeof(float) : sizeof(double));
     auto upload = [&](int j) -> fg_status {
       const int b = j & 1;
       if (j >= 2 && cudaStreamWaitEvent(cs_, ev_read_[b], 0) != cudaSuccess) return cuda_fail("stream wait");
-      if (cudaMemcpyAsync(stage[b], hp[j], nd * sizeof(double), cudaMemcpyHostToDevice, cs_) != cudaSuccess)
+      if (cudaMemcpyAsync(stage[b], hp[j], bytes, cudaMemcpyHostToDevice, cs_) != cudaSuccess)
         return cuda_fail("momenta upload");
       if (cudaEventRecord(ev_copied_[b], cs_) != cudaSuccess) return cuda_fail("event record");
       return FG_OK;
@@ -150,7 +151,10 @@ class Backend final : public IBackend {
         s = cuda_fail("stream wait");
         break;
       }
-      s = run(KC_CONVERT, [&] { return launch_mom_to_device<R>(g_, stage[b], P_, st_); });
+      s = run(KC_CONVERT, [&] {
+        return f32 ? launch_mom_to_device_f32<R>(g_, reinterpret_cast<const float*>(stage[b]), P_, st_)
+                   : launch_mom_to_device<R>(g_, stage[b], P_, st_);
+      });
       if (s != FG_OK) break;
       if (cudaEventRecord(ev_read_[b], st_) != cudaSuccess) {
         s = cuda_fail("event record");

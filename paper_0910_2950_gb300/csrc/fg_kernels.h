@@ -96,6 +96,9 @@ template <typename R, int NC>
 cudaError_t launch_gauge_to_canon(const GeomH& g, const void* U, double* canon, cudaStream_t st);
 template <typename R>
 cudaError_t launch_mom_to_device(const GeomH& g, const double* canon, void* P, cudaStream_t st);
+// The same from canonical FP32 momenta.
+template <typename R>
+cudaError_t launch_mom_to_device_f32(const GeomH& g, const float* canon, void* P, cudaStream_t st);
 template <typename R>
 cudaError_t launch_mom_to_canon(const GeomH& g, const void* P, double* canon, cudaStream_t st);
 

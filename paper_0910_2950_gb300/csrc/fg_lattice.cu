@@ -386,10 +386,9 @@ fg_status fg_trajectory_nested(fg_lattice* h, fg_integrator outer, fg_integrator
   if (out) *out = r;
   return s;
 }
-fg_status fg_trajectories_host_momenta(fg_lattice* h, fg_integrator integ, double dt, double tau, int n,
-                                       const double* const* host_p8, const double* u_accept,
-                                       fg_traj_result* out) {
-  FG_CHECK_HANDLE(h);
+static fg_status host_momenta_trajectories(fg_lattice* h, fg_integrator integ, double dt, double tau, int n,
+                                           const void* const* host_p8, int f32, const double* u_accept,
+                                           fg_traj_result* out) {
   if ((int)integ < 0 || (int)integ > 5) return h->fail(FG_EINVAL, "bad integrator");
   if (!(dt > 0.0) || !(tau > 0.0)) return h->fail(FG_EINVAL, "dt and tau must be positive");
   const int ns = (int)std::llround(tau / dt);
@@ -400,7 +399,21 @@ fg_status fg_trajectories_host_momenta(fg_lattice* h, fg_integrator integ, doubl
     if (!host_p8[k]) return h->fail(FG_EINVAL, "null momenta pointer");
     if (u_accept && !(u_accept[k] < 1.0)) return h->fail(FG_EINVAL, "u_accept must be < 1");
   }
-  return h->be->trajectories_host_momenta((int)integ, dt, ns, n, host_p8, u_accept, out);
+  return h->be->trajectories_host_momenta((int)integ, dt, ns, n, host_p8, f32, u_accept, out);
+}
+fg_status fg_trajectories_host_momenta(fg_lattice* h, fg_integrator integ, double dt, double tau, int n,
+                                       const double* const* host_p8, const double* u_accept,
+                                       fg_traj_result* out) {
+  FG_CHECK_HANDLE(h);
+  return host_momenta_trajectories(h, integ, dt, tau, n, reinterpret_cast<const void* const*>(host_p8), 0,
+                                   u_accept, out);
+}
+fg_status fg_trajectories_host_momenta_f32(fg_lattice* h, fg_integrator integ, double dt, double tau, int n,
+                                           const float* const* host_p8, const double* u_accept,
+                                           fg_traj_result* out) {
+  FG_CHECK_HANDLE(h);
+  return host_momenta_trajectories(h, integ, dt, tau, n, reinterpret_cast<const void* const*>(host_p8), 1,
+                                   u_accept, out);
 }
 fg_status fg_apply_mhat(fg_lattice* h, const double* in, double* out, int dagger) {
   FG_CHECK_HANDLE(h);

@@ -83,8 +83,9 @@ struct IBackend {
                                fg_traj_result* r) = 0;
   virtual fg_status trajectory_nested(int outer, int inner, int n_inner, double dt, int nsteps, int refresh,
                                       double u_accept, fg_traj_result* r) = 0;
-  virtual fg_status trajectories_host_momenta(int integ, double dt, int nsteps, int n, const double* const* host_p8,
-                                              const double* u_accept, fg_traj_result* out) = 0;
+  // host_p8[k]: n canonical momentum arrays, FP64 (f32 = 0) or FP32 (f32 = 1)
+  virtual fg_status trajectories_host_momenta(int integ, double dt, int nsteps, int n, const void* const* host_p8,
+                                              int f32, const double* u_accept, fg_traj_result* out) = 0;
   virtual fg_status apply_mhat(const double* in, double* out, int dagger) = 0;
   virtual fg_status apply_mhat_inner(const double* in, double* out, int dagger) = 0;
   virtual fg_status cg_solve(const double* b, double* x, fg_cg_result* r) = 0;

@@ -207,8 +207,8 @@ __global__ void gauge_to_canon_kernel(Gauge<R, NC> U, double* __restrict__ canon
   }
 }
 
-template <typename R>
-__global__ void mom_to_device_kernel(const double* __restrict__ canon, Mom<R> P, Geom g) {
+template <typename R, typename T>
+__global__ void mom_to_device_kernel(const T* __restrict__ canon, Mom<R> P, Geom g) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 4 * g.V) return;
   const int lex = i >> 2, mu = i & 3;
@@ -381,7 +381,7 @@ cudaError_t launch_gauge_to_canon(const GeomH& gh, const void* U, double* canon,
 }
 template <typename R>
 cudaError_t launch_mom_to_device(const GeomH& gh, const double* canon, void* P, cudaStream_t st) {
-  mom_to_device_kernel<R><<<(4 * gh.V + 255) / 256, 256, 0, st>>>(canon, mom_of<R>(P, gh.V), to_dev(gh));
+  mom_to_device_kernel<R, double><<<(4 * gh.V + 255) / 256, 256, 0, st>>>(canon, mom_of<R>(P, gh.V), to_dev(gh));
   return cudaGetLastError();
 }
 template <typename R>
@@ -441,6 +441,14 @@ template cudaError_t launch_refresh_momenta<DF>(const GeomH&, void*, uint64_t, u
 template cudaError_t launch_mom_to_device<double>(const GeomH&, const double*, void*, cudaStream_t);
 template cudaError_t launch_mom_to_device<float>(const GeomH&, const double*, void*, cudaStream_t);
 template cudaError_t launch_mom_to_device<DF>(const GeomH&, const double*, void*, cudaStream_t);
+template <typename R>
+cudaError_t launch_mom_to_device_f32(const GeomH& gh, const float* canon, void* P, cudaStream_t st) {
+  mom_to_device_kernel<R, float><<<(4 * gh.V + 255) / 256, 256, 0, st>>>(canon, mom_of<R>(P, gh.V), to_dev(gh));
+  return cudaGetLastError();
+}
+template cudaError_t launch_mom_to_device_f32<double>(const GeomH&, const float*, void*, cudaStream_t);
+template cudaError_t launch_mom_to_device_f32<float>(const GeomH&, const float*, void*, cudaStream_t);
+template cudaError_t launch_mom_to_device_f32<DF>(const GeomH&, const float*, void*, cudaStream_t);
 template cudaError_t launch_mom_to_canon<double>(const GeomH&, const void*, double*, cudaStream_t);
 template cudaError_t launch_mom_to_canon<float>(const GeomH&, const void*, double*, cudaStream_t);
 template cudaError_t launch_mom_to_canon<DF>(const GeomH&, const void*, double*, cudaStream_t);

@@ -87,6 +87,8 @@ SIGNATURES = {
     "fg_timing_reset": (_i, [_vp]),
     "fg_kernel_time": (_i, [_vp, C.c_char_p, _dp, C.POINTER(C.c_longlong)]),
     "fg_trajectory_nested": (_i, [_vp, _i, _i, _i, _d, _d, _i, _d, C.POINTER(FgTrajResult)]),
+    "fg_trajectories_host_momenta_f32": (_i, [_vp, _i, _d, _d, _i, C.POINTER(C.POINTER(C.c_float)), _dp,
+                                              C.POINTER(FgTrajResult)]),
     "fg_trajectories_host_momenta": (_i, [_vp, _i, _d, _d, _i, C.POINTER(_dp), _dp,
                                          C.POINTER(FgTrajResult)]),
     "fg_launch_count": (C.c_longlong, [_vp]),
@@ -275,14 +277,27 @@ class Lattice:
     def trajectories_host_momenta(self, integrator, dt, tau, momenta, u_accept=None):
         """len(momenta) trajectories (refresh off), trajectory k from the host
         momenta ``momenta[k]``; uploads overlap the previous trajectory (use
-        page-locked arrays for the overlap).  Returns one result dict each."""
-        arrs = [_f64(p, (self.V, 4, 8)) for p in momenta]
-        n = len(arrs)
-        ptrs = (_dp * max(n, 1))(*[_ptr(a) for a in arrs])
+        page-locked arrays for the overlap).  float32 arrays (all of them)
+        are uploaded as FP32, anything else as FP64.  Returns one result dict
+        each."""
+        n = len(momenta)
         u = None if u_accept is None else _f64(u_accept, (n,))
         res = (FgTrajResult * max(n, 1))()
-        self._call("fg_trajectories_host_momenta", INTEGRATORS[integrator], float(dt), float(tau), n, ptrs,
-                   _ptr(u) if u is not None else None, res)
+        if n > 0 and all(np.asarray(p).dtype == np.float32 for p in momenta):
+            # FP32 arrays go up as they are (half the bytes)
+            arrs = [np.ascontiguousarray(p, dtype=np.float32).reshape(-1) for p in momenta]
+            for a in arrs:
+                if a.size != self.V * 32:
+                    raise ValueError(f"momenta: expected {self.V * 32} floats, got {a.size}")
+            fp = C.POINTER(C.c_float)
+            ptrs = (fp * n)(*[a.ctypes.data_as(fp) for a in arrs])
+            self._call("fg_trajectories_host_momenta_f32", INTEGRATORS[integrator], float(dt), float(tau), n,
+                       ptrs, _ptr(u) if u is not None else None, res)
+        else:
+            arrs = [_f64(p, (self.V, 4, 8)) for p in momenta]
+            ptrs = (_dp * max(n, 1))(*[_ptr(a) for a in arrs])
+            self._call("fg_trajectories_host_momenta", INTEGRATORS[integrator], float(dt), float(tau), n, ptrs,
+                       _ptr(u) if u is not None else None, res)
         return [{k: getattr(r, k) for k, _ in FgTrajResult._fields_} for r in res[:n]]
 
     # -- fermion building blocks

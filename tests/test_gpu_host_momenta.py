@@ -94,6 +94,32 @@ def test_nf2_matches_sequential(fgmod):
         assert np.array_equal(a.get_gauge(), b.get_gauge())
 
 
+@pytest.mark.parametrize("precision", ["fp32", "df64", "fp64"])
+def test_fp32_host_momenta(fgmod, precision):
+    """FP32 host momenta (half the upload): the trajectories are those of the
+    FP64 host momenta rounded to FP32, bit for bit (every handle widens or
+    keeps the FP32 values exactly)."""
+    import torch
+    dims = (8, 8, 8, 8)
+    u0 = inputs.hot_start(dims, 41)
+    m64 = [p.astype(np.float32).astype(np.float64) for p in _momenta(dims, 4, 42, False)]
+    m32 = []
+    for p in m64:
+        buf = torch.empty(p.size, dtype=torch.float32, pin_memory=True).numpy()
+        buf[:] = p
+        m32.append(buf)
+    us = [0.0, 0.5, -1.0, -1.0]
+    kw = dict(precision=precision, seed=9)
+    with fgmod.Lattice(dims, BETA, **kw) as a, fgmod.Lattice(dims, BETA, **kw) as b:
+        a.set_gauge(u0)
+        b.set_gauge(u0)
+        ra = a.trajectories_host_momenta("fg", 0.25, 1.0, m32, u_accept=us)
+        rb = b.trajectories_host_momenta("fg", 0.25, 1.0, m64, u_accept=us)
+        assert ra == rb
+        assert np.array_equal(a.get_gauge(), b.get_gauge())
+        assert np.array_equal(a.get_momenta(), b.get_momenta())
+
+
 def test_arguments(fgmod):
     dims = (4, 4, 4, 4)
     with fgmod.Lattice(dims, BETA, precision="fp32") as lat:
