@@ -1087,6 +1087,17 @@ def run_ours(args):
         hp2 = torch.empty(ncanon_p, dtype=pdt, pin_memory=True).numpy()
         hp2[:] = rng.standard_normal(ncanon_p)
         moms = [hp if k % 2 == 0 else hp2 for k in range(args.steps)]
+        # fg_set_momenta takes canonical FP64: the sequential and stateless
+        # forms get pinned FP64 copies of the same momenta (no per-step host
+        # conversion inside their timed regions)
+        if pdt == torch.float64:
+            moms64 = moms
+        else:
+            hp64 = torch.empty(ncanon_p, dtype=torch.float64, pin_memory=True).numpy()
+            hp64b = torch.empty(ncanon_p, dtype=torch.float64, pin_memory=True).numpy()
+            hp64[:] = hp
+            hp64b[:] = hp2
+            moms64 = [hp64 if k % 2 == 0 else hp64b for k in range(args.steps)]
         lat.set_gauge(hu)
         torch.cuda.synchronize()
         if world > 1:
@@ -1106,7 +1117,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for k in range(args.steps):
-            lat.set_momenta(moms[k])
+            lat.set_momenta(moms64[k])
             r = lat.trajectory(args.integrator, args.dt, TAU, refresh=False, u_accept=-1.0)
         torch.cuda.synchronize()
         e2e_seq = reduce_max(time.perf_counter() - t0, world, "cuda")
@@ -1116,7 +1127,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         for _ in range(args.steps):
             lat.set_gauge(hu)
-            lat.set_momenta(hp)
+            lat.set_momenta(moms64[0])
             r = lat.trajectory(args.integrator, args.dt, TAU, refresh=False, u_accept=-1.0)
             lat.get_gauge(out=hu)
         torch.cuda.synchronize()
@@ -1130,8 +1141,8 @@ def run_ours(args):
                        "result (dH, H0, H1 sums, accept) read back after each trajectory",
                "sequential": {"value": whole_job_rate(args.steps, world, e2e_seq), "unit": UNIT,
                               "h2d_bytes_per_step": ncanon_p * 8, "d2h_bytes_per_step": 6 * 8,
-                              "note": "fg_set_momenta then fg_trajectory per trajectory: upload, conversion "
-                                      "and MD in sequence"},
+                              "note": "fg_set_momenta (canonical FP64 from pinned memory) then fg_trajectory "
+                                      "per trajectory: upload, conversion and MD in sequence"},
                "stateless": {"value": whole_job_rate(args.steps, world, e2e_sl), "unit": UNIT,
                              "h2d_bytes_per_step": (ncanon_u + ncanon_p) * 8,
                              "d2h_bytes_per_step": ncanon_u * 8 + 6 * 8,
