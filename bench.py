@@ -592,6 +592,7 @@ def fermion_measurement(fg, stream, rank, hbm_peak, dims=(16, 16, 16, 32)):
                                "cg_iterations": r64["cg_iters"]}
     trajs["dH_error_fp32_vs_fp64_dt_0.1"] = abs(trajs["fg_dt_0.1"]["dH"] - r64["dH"])
     lat.close()
+    inner16 = inner_precision_measurement(fg, stream, rank, u, dims)
     ds_ms, ds_n = cls["dslash"]
     avg = ds_ms / 1000.0 / max(ds_n, 1)
     achieved = DSLASH_BYTES_CG_AVG * vh / avg / 1e9
@@ -615,9 +616,59 @@ def fermion_measurement(fg, stream, rank, hbm_peak, dims=(16, 16, 16, 32)):
         "fermion_force_roofline": ff_roof,
         "trajectories": trajs,
         "half_precision_cg": half,
+        "inner_precision_16bit": inner16,
         "trajectories_note": "one FG trajectory per entry from the same links, momenta and chi; FP32 "
                              "links/forces with the mixed solver vs the FP64 path; ms is wall clock",
     }
+
+
+def inner_precision_measurement(fg, stream, rank, u_small, dims_small, solves=3):
+    """The inner solver's storage format at the two Nf=2 sizes (16^3 x 32,
+    whose fields fit in L2, with the thermalised links of the Nf=2
+    measurement; 24^3 x 48, which does not, from a device hot start and 20
+    FG trajectories): FP32, IEEE half and bfloat16 links and vectors (the
+    16-bit ones with reliable updates at least every factor 0.1 of residual,
+    bfloat16 also every 0.3), solves to 1e-10 at kappa 0.158.  Device time
+    is the sum of the solver's kernels over one timed solve (single
+    launches); wall time includes the pageable copies of b and x."""
+    big = (24, 24, 24, 48)
+    th = fg.Lattice(big, 5.6, precision="fp32", seed=480 + rank, stream=stream)
+    th.random_gauge()
+    for _ in range(10):
+        th.trajectory("fg", 0.125, TAU, refresh=True, u_accept=0.0)
+    for _ in range(10):
+        th.trajectory("fg", 0.25, TAU, refresh=True, u_accept=-1.0)
+    u_big = th.get_gauge()
+    th.close()
+    out = {}
+    for dims, u in ((tuple(dims_small), u_small), (big, u_big)):
+        bs = [inputs.gaussian_spinor_even(dims, 70 + k + rank) for k in range(solves + 2)]
+        res = {}
+        for prec, delta in (("fp32", 0.01), ("fp32_fp16cg", 0.1), ("fp32_bf16cg", 0.1), ("fp32_bf16cg", 0.3)):
+            with fg.Lattice(dims, 5.6, kappa=0.158, precision=prec, cg_tol=1e-10, cg_delta=delta, seed=490 + rank,
+                            stream=stream) as l:
+                l.set_gauge(u)
+                l.cg_solve(bs[0])
+                it = ru = 0
+                rmax = 0.0
+                t0 = time.perf_counter()
+                for k in range(solves):
+                    _, info = l.cg_solve(bs[1 + k])
+                    it += info["iterations"]
+                    ru += info["reliable_updates"]
+                    rmax = max(rmax, info["true_residual"])
+                wall_ms = 1000 * (time.perf_counter() - t0) / solves
+                l.timing(True)
+                l.timing_reset()
+                l.cg_solve(bs[-1])
+                dev_ms = sum(l.kernel_time(c)[0] for c in ("dslash", "dslash_df", "dslash_fp64", "cg_blas",
+                                                           "reduce", "convert"))
+                l.timing(False)
+            res[f"{prec}_delta_{delta}"] = {"device_ms_per_solve": dev_ms, "wall_ms_per_solve": wall_ms,
+                                            "cg_iterations_per_solve": it / solves,
+                                            "reliable_updates_per_solve": ru / solves, "true_residual_max": rmax}
+        out["x".join(map(str, dims))] = res
+    return out
 
 
 def precision_measurement(fg, stream, rank, L=16, n_time=5):

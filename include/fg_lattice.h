@@ -118,13 +118,19 @@ typedef enum {
  * (links and six half-lattice spinors, (4 NC 8 + 6 48) V bytes for NC
  * complex entries per link) exceeds the GPU's L2 cache, and FG_FP32
  * otherwise: below that size the fields stay in L2, half precision saves no
- * memory traffic and its extra reliable updates cost time. */
+ * memory traffic and its extra reliable updates cost time.
+ * FG_FP32_BF16CG is FG_FP32_FP16CG with bfloat16 in place of IEEE half for
+ * the inner links and vectors: the same bytes, the exponent range of FP32,
+ * 8 instead of 11 significant bits (unit roundoff 2^-8, ~4e-3 relative
+ * error of the inner operator), so the reliable updates have more to
+ * correct. */
 typedef enum {
   FG_FP64 = 0,
   FG_FP32 = 1,
   FG_FP32_FP16CG = 2,
   FG_DF64 = 3,
-  FG_FP32_AUTOCG = 4
+  FG_FP32_AUTOCG = 4,
+  FG_FP32_BF16CG = 5
 } fg_precision;
 
 typedef struct {
@@ -280,7 +286,8 @@ fg_status fg_apply_mhat(fg_lattice *h, const double *host_in_even, double *host_
  * precision, the two Dslash launches of Mhat in that precision, the output
  * widened to FP64.  Inner precision: FP32 links and spinors for FG_FP32;
  * half-precision links (a copy made for the call) and half-precision spinors
- * scaled by sigma, sigma^2 = |in|^2 / n, for FG_FP32_FP16CG; FP64 for FG_FP64
+ * scaled by sigma, sigma^2 = |in|^2 / n, for FG_FP32_FP16CG; the same in
+ * bfloat16 for FG_FP32_BF16CG; FP64 for FG_FP64
  * (then equal to fg_apply_mhat).  FG_ESTATE for pure-gauge handles. */
 fg_status fg_apply_mhat_inner(fg_lattice *h, const double *host_in_even, double *host_out_even,
                               int dagger);

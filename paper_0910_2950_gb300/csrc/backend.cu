@@ -228,8 +228,8 @@ class Backend final : public IBackend {
         if ((s = run(KC_CG_BLAS, [&] { return launch_dot64(b64_, b64_, part_rr_, n, st_); })) != FG_OK) return s;
         if ((s = run(KC_REDUCE, [&] { return launch_cg_init_h16(part_rr_, nbv, cgd_, 0.0, bbp, n, st_); })) != FG_OK)
           return s;
-        if ((s = run(KC_CG_BLAS, [&] { return launch_scale_to_h16(rs_, b64_, cgd_, n, st_); })) != FG_OK) return s;
-        if ((s = run(KC_CONVERT, [&] { return launch_links_to_half<NC>(g_, U_, U16_, st_); })) != FG_OK) return s;
+        if ((s = run(KC_CG_BLAS, [&] { return launch_scale_to_h16(s16_, rs_, b64_, cgd_, n, st_); })) != FG_OK) return s;
+        if ((s = run(KC_CONVERT, [&] { return launch_links_to_half<NC>(s16_, g_, U_, U16_, st_); })) != FG_OK) return s;
         Uin = U16_;
       } else {
         if ((s = run(KC_CG_BLAS, [&] { return launch_convert<R, double>(rs_, b64_, nullptr, n, st_); })) != FG_OK)
@@ -242,7 +242,7 @@ class Backend final : public IBackend {
       if ((s = run(KC_DSLASH, [&] { return inner_dslash(te_, to_, rs_, nullptr, Uin, 0, dagger, 1, -k2, nullptr, false); })) !=
           FG_OK)
         return s;
-      if (half_links_) s = run(KC_CONVERT, [&] { return launch_h16_to_double_scaled(ax64_, te_, cgd_, n, st_); });
+      if (half_links_) s = run(KC_CONVERT, [&] { return launch_h16_to_double_scaled(s16_, ax64_, te_, cgd_, n, st_); });
       else s = run(KC_CONVERT, [&] { return launch_convert<double, R>(ax64_, te_, nullptr, n, st_); });
       if (s != FG_OK) return s;
       return download_spinor(ax64_, out);
@@ -456,12 +456,16 @@ class Backend final : public IBackend {
   // Double-float handles are pure gauge (fg_lattice_create rejects kappa > 0):
   // their fermion entry points are not compiled.
   static constexpr bool kFerm = !std::is_same<R, DF>::value;
-  fg_status no_fermions() { return h_->fail(FG_ESTATE, "fermions need FG_FP64, FG_FP32, FG_FP32_FP16CG or FG_FP32_AUTOCG"); }
-  // inner CG Dslash on a half-precision copy of the links (FG_FP32_FP16CG,
-  // and FG_FP32_AUTOCG above the L2 size)
+  fg_status no_fermions() {
+    return h_->fail(FG_ESTATE, "fermions need FG_FP64, FG_FP32, FG_FP32_FP16CG, FG_FP32_AUTOCG or FG_FP32_BF16CG");
+  }
+  // inner CG Dslash on a 16-bit copy of the links: IEEE half for
+  // FG_FP32_FP16CG (and FG_FP32_AUTOCG above the L2 size), bfloat16 for
+  // FG_FP32_BF16CG
   void* U16_ = nullptr;
-  const bool half_links_ = kMixed && (h_->prm.precision == FG_FP32_FP16CG ||
+  const bool half_links_ = kMixed && (h_->prm.precision == FG_FP32_FP16CG || h_->prm.precision == FG_FP32_BF16CG ||
                                       (h_->prm.precision == FG_FP32_AUTOCG && inner_exceeds_l2()));
+  const int s16_ = h_->prm.precision == FG_FP32_BF16CG ? S16_BF16 : S16_HALF;
   // The FP32 inner solver's working set (links and six half-lattice spinor
   // vectors) against the GPU's L2 cache.
   bool inner_exceeds_l2() const {
@@ -1069,9 +1073,9 @@ class Backend final : public IBackend {
     }
   }
 
-  // Dslash of the inner iterations: on the FP32 links, or with
-  // FG_FP32_FP16CG on their half-precision copy (then U is that copy) and
-  // half-precision spinors.
+  // Dslash of the inner iterations: on the FP32 links, or with a 16-bit
+  // inner solver on the links' 16-bit copy (then U is that copy) and 16-bit
+  // spinors.
   // `solver` = false: outside a solve (no early return on the solver's
   // converged flag).
   cudaError_t inner_dslash(void* out, const void* in, const void* x, const void* pdot, const void* U, int out_par,
@@ -1079,7 +1083,7 @@ class Backend final : public IBackend {
     CgDev* const cgd = solver ? cgd_ : nullptr;
     if constexpr (kMixed) {
       if (half_links_)
-        return launch_dslash_h16<Half16, NC>(g_, out, in, x, pdot, U, out_par, dag, mode, b, partial, cgd, st_);
+        return launch_dslash_h16<NC>(s16_, g_, out, in, x, pdot, U, out_par, dag, mode, b, partial, cgd, st_);
     }
     return launch_dslash<R, NC, R>(g_, out, in, x, pdot, U, out_par, dag, mode, b, partial, cgd, st_);
   }
@@ -1129,8 +1133,8 @@ class Backend final : public IBackend {
     if ((e = inner_dslash(to_, te_, nullptr, nullptr, U, 1, 1, 0, 1.0, nullptr)) != cudaSuccess) return e;
     if ((e = inner_dslash(ap_, to_, te_, p_, U, 0, 1, 2, -k2, part_pap_)) != cudaSuccess) return e;
     if (half_links_) {
-      if ((e = launch_cg_axpy_h16(xs_, rs_, p_, ap_, cgd_, part_rr_, n, st_)) != cudaSuccess) return e;
-      return launch_cg_xpay_h16(p_, rs_, cgd_, mapped_->hist, &mapped_->dev_iter, h_->prm.cg_maxiter, n, st_);
+      if ((e = launch_cg_axpy_h16(s16_, xs_, rs_, p_, ap_, cgd_, part_rr_, n, st_)) != cudaSuccess) return e;
+      return launch_cg_xpay_h16(s16_, p_, rs_, cgd_, mapped_->hist, &mapped_->dev_iter, h_->prm.cg_maxiter, n, st_);
     }
     if ((e = launch_cg_axpy<R>(xs_, rs_, p_, ap_, cgd_, part_rr_, n, st_)) !=
         cudaSuccess)
@@ -1166,11 +1170,11 @@ class Backend final : public IBackend {
     if ((s = run(KC_DSLASH, [&] { return inner_dslash(ap_, to_, te_, p_, U, 0, 1, 2, -k2, part_pap_); })) != FG_OK)
       return s;
     if (half_links_) {
-      if ((s = run(KC_CG_BLAS, [&] { return launch_cg_axpy_h16(xs_, rs_, p_, ap_, cgd_, part_rr_, n, st_); })) !=
+      if ((s = run(KC_CG_BLAS, [&] { return launch_cg_axpy_h16(s16_, xs_, rs_, p_, ap_, cgd_, part_rr_, n, st_); })) !=
           FG_OK)
         return s;
       return run(KC_CG_BLAS, [&] {
-        return launch_cg_xpay_h16(p_, rs_, cgd_, mapped_->hist, &mapped_->dev_iter, h_->prm.cg_maxiter, n, st_);
+        return launch_cg_xpay_h16(s16_, p_, rs_, cgd_, mapped_->hist, &mapped_->dev_iter, h_->prm.cg_maxiter, n, st_);
       });
     }
     if ((s = run(KC_CG_BLAS, [&] {
@@ -1302,7 +1306,7 @@ class Backend final : public IBackend {
         return s;
       if ((s = run(KC_REDUCE, [&] { return launch_ru_publish_h16(part_rr_, nbv, cgd_, tr, n, st_); })) != FG_OK)
         return s;
-      return run(KC_CG_BLAS, [&] { return launch_ru_rescale_df_h16(ax64_, rs_, p_, cgd_, n, st_); });
+      return run(KC_CG_BLAS, [&] { return launch_ru_rescale_df_h16(s16_, ax64_, rs_, p_, cgd_, n, st_); });
     }
     if ((s = run(KC_CG_BLAS, [&] { return launch_df_to_double(x64_, xdf_, n, st_); })) != FG_OK) return s;
     if ((s = apply_mdagm64(ax64_, x64_, U)) != FG_OK) return s;
@@ -1310,7 +1314,7 @@ class Backend final : public IBackend {
       return s;
     if ((s = run(KC_REDUCE, [&] { return launch_ru_publish_h16(part_rr_, nbv, cgd_, tr, n, st_); })) != FG_OK)
       return s;
-    return run(KC_CG_BLAS, [&] { return launch_ru_rescale64_h16(r64_, rs_, p_, cgd_, n, st_); });
+    return run(KC_CG_BLAS, [&] { return launch_ru_rescale64_h16(s16_, r64_, rs_, p_, cgd_, n, st_); });
   }
 
   // Conjugate gradient on Mhat^dagger Mhat x = b (b FP64 on the device), x0 = 0,
@@ -1374,7 +1378,7 @@ class Backend final : public IBackend {
       if ((s = run(KC_REDUCE, [&] { return launch_cg_init_h16(part_rr_, nbv, cgd_, tol * tol, bbp, n, st_); })) !=
           FG_OK)
         return s;
-      if ((s = run(KC_CG_BLAS, [&] { return launch_scale_to_h16(rs_, b64, cgd_, n, st_); })) != FG_OK) return s;
+      if ((s = run(KC_CG_BLAS, [&] { return launch_scale_to_h16(s16_, rs_, b64, cgd_, n, st_); })) != FG_OK) return s;
       if (cudaMemcpyAsync(p_, rs_, (size_t)n * sizeof(__half2), cudaMemcpyDeviceToDevice, st_) != cudaSuccess)
         return cuda_fail("cg setup");
     } else {
@@ -1388,7 +1392,7 @@ class Backend final : public IBackend {
     // the inner iterations' links: the FP32 field, or its half-precision copy
     const void* Uin = U;
     if (half_links_) {
-      if ((s = run(KC_CONVERT, [&] { return launch_links_to_half<NC>(g_, U, U16_, st_); })) != FG_OK) return s;
+      if ((s = run(KC_CONVERT, [&] { return launch_links_to_half<NC>(s16_, g_, U, U16_, st_); })) != FG_OK) return s;
       Uin = U16_;
     }
     if (fold_ && (s = fold_prime(Uin)) != FG_OK) return s;

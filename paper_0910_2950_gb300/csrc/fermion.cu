@@ -507,14 +507,16 @@ __global__ void __launch_bounds__(kVecThreads) df_to_double_kernel(double2* __re
 }
 
 // ---------------------------------------------------------------------------
-// Half-precision inner vectors.  The solver iterates on r / sigma: CG is
-// invariant under a common scale of r and p, and keeping |r / sigma|^2 = n
-// after every reliable update keeps the entries O(1), far from the ends of
-// the half range.  Scalars (rr, pAp, alpha, beta) are in the scaled units;
+// 16-bit inner vectors (S = Half16 or BF16).  The solver iterates on
+// r / sigma: CG is invariant under a common scale of r and p, and keeping
+// |r / sigma|^2 = n after every reliable update keeps the entries O(1), far
+// from the ends of the half range.  Scalars (rr, pAp, alpha, beta) are in the scaled units;
 // the history and the convergence test use rr sigma^2.
-__global__ void __launch_bounds__(kVecThreads) cg_axpy_h16_kernel(float2* __restrict__ x, __half2* __restrict__ r,
-                                                                  const __half2* __restrict__ p,
-                                                                  const __half2* __restrict__ ap,
+template <typename S>
+__global__ void __launch_bounds__(kVecThreads) cg_axpy_h16_kernel(float2* __restrict__ x,
+                                                                  typename Conv16<S>::T2* __restrict__ r,
+                                                                  const typename Conv16<S>::T2* __restrict__ p,
+                                                                  const typename Conv16<S>::T2* __restrict__ ap,
                                                                   CgDev* __restrict__ cgd, double* __restrict__ rr_part,
                                                                   int n) {
   if (cgd->done) return;
@@ -526,14 +528,14 @@ __global__ void __launch_bounds__(kVecThreads) cg_axpy_h16_kernel(float2* __rest
   float acc = 0.0f;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     float2 xv = x[i];
-    float2 rv = __half22float2(r[i]);
-    const float2 pv = __half22float2(p[i]), av = __half22float2(ap[i]);
+    float2 rv = Conv16<S>::f2(r[i]);
+    const float2 pv = Conv16<S>::f2(p[i]), av = Conv16<S>::f2(ap[i]);
     xv.x = fmaf(a, pv.x, xv.x); xv.y = fmaf(a, pv.y, xv.y);
     rv.x = fmaf(-a, av.x, rv.x); rv.y = fmaf(-a, av.y, rv.y);
     x[i] = xv;
-    const __half2 rh = __float22half2_rn(rv);
+    const typename Conv16<S>::T2 rh = Conv16<S>::of(rv);
     r[i] = rh;
-    const float2 rq = __half22float2(rh);   // |r|^2 of the stored residual
+    const float2 rq = Conv16<S>::f2(rh);   // |r|^2 of the stored residual
     acc = fmaf(rq.x, rq.x, acc);
     acc = fmaf(rq.y, rq.y, acc);
   }
@@ -544,8 +546,9 @@ __global__ void __launch_bounds__(kVecThreads) cg_axpy_h16_kernel(float2* __rest
   block_reduce_total(double(acc), rr_part, &cgd->ticket[1], &cgd->rr_next);
 }
 
-__global__ void __launch_bounds__(kVecThreads) cg_xpay_h16_kernel(__half2* __restrict__ p,
-                                                                  const __half2* __restrict__ r,
+template <typename S>
+__global__ void __launch_bounds__(kVecThreads) cg_xpay_h16_kernel(typename Conv16<S>::T2* __restrict__ p,
+                                                                  const typename Conv16<S>::T2* __restrict__ r,
                                                                   CgDev* __restrict__ cgd, double* __restrict__ hist,
                                                                   int* __restrict__ iter_out, int maxiter, int n) {
   if (cgd->done) return;
@@ -563,11 +566,11 @@ __global__ void __launch_bounds__(kVecThreads) cg_xpay_h16_kernel(__half2* __res
   }
   const float beta = float(rr_old > 0.0 ? rr_new / rr_old : 0.0);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    float2 pv = __half22float2(p[i]);
-    const float2 rv = __half22float2(r[i]);
+    float2 pv = Conv16<S>::f2(p[i]);
+    const float2 rv = Conv16<S>::f2(r[i]);
     pv.x = fmaf(beta, pv.x, rv.x);
     pv.y = fmaf(beta, pv.y, rv.y);
-    p[i] = __float22half2_rn(pv);
+    p[i] = Conv16<S>::of(pv);
   }
 }
 
@@ -589,23 +592,25 @@ __global__ void cg_init_h16_kernel(const double* __restrict__ part, int nparts, 
   }
 }
 
-__global__ void __launch_bounds__(kVecThreads) scale_to_h16_kernel(__half2* __restrict__ rs,
+template <typename S>
+__global__ void __launch_bounds__(kVecThreads) scale_to_h16_kernel(typename Conv16<S>::T2* __restrict__ rs,
                                                                    const double2* __restrict__ b,
                                                                    const CgDev* __restrict__ cgd, int n) {
   const double inv = 1.0 / sqrt(cgd->sigma2);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const double2 v = b[i];
-    rs[i] = __floats2half2_rn(float(v.x * inv), float(v.y * inv));
+    rs[i] = Conv16<S>::of(make_float2(float(v.x * inv), float(v.y * inv)));
   }
 }
 
-// dst (FP64) = sigma src (half-precision inner vector in scaled units).
+// dst (FP64) = sigma src (16-bit inner vector in scaled units).
+template <typename S>
 __global__ void __launch_bounds__(kVecThreads) h16_to_double_scaled_kernel(double2* __restrict__ dst,
-                                                                          const __half2* __restrict__ src,
+                                                                          const typename Conv16<S>::T2* __restrict__ src,
                                                                           const CgDev* __restrict__ cgd, int n) {
   const double sg = sqrt(cgd->sigma2);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const float2 v = __half22float2(src[i]);
+    const float2 v = Conv16<S>::f2(src[i]);
     dst[i] = make_double2(sg * (double)v.x, sg * (double)v.y);
   }
 }
@@ -669,9 +674,10 @@ __global__ void ru_publish_h16_kernel(const double* __restrict__ part, int npart
   }
 }
 
-template <typename RV>
-__global__ void __launch_bounds__(kVecThreads) ru_rescale_h16_kernel(const RV* __restrict__ r, __half2* __restrict__ rs,
-                                                                     __half2* __restrict__ p,
+template <typename S, typename RV>
+__global__ void __launch_bounds__(kVecThreads) ru_rescale_h16_kernel(const RV* __restrict__ r,
+                                                                     typename Conv16<S>::T2* __restrict__ rs,
+                                                                     typename Conv16<S>::T2* __restrict__ p,
                                                                      const CgDev* __restrict__ cgd, int n) {
   const double inv = 1.0 / sqrt(cgd->sigma2);
   const float rho = float(cgd->rho);
@@ -687,13 +693,13 @@ __global__ void __launch_bounds__(kVecThreads) ru_rescale_h16_kernel(const RV* _
       re = v.x;
       im = v.y;
     }
-    const __half2 h = __floats2half2_rn(float(re * inv), float(im * inv));
+    const typename Conv16<S>::T2 h = Conv16<S>::of(make_float2(float(re * inv), float(im * inv)));
     rs[i] = h;
     if (restart) {
       p[i] = h;
     } else {
-      const float2 pv = __half22float2(p[i]);
-      p[i] = __floats2half2_rn(rho * pv.x, rho * pv.y);
+      const float2 pv = Conv16<S>::f2(p[i]);
+      p[i] = Conv16<S>::of(make_float2(rho * pv.x, rho * pv.y));
     }
   }
 }
@@ -977,19 +983,19 @@ cudaError_t launch_df_to_double(void* dst, const void* src, int n, cudaStream_t 
   df_to_double_kernel<<<vec_blocks(n), kVecThreads, 0, st>>>((double2*)dst, (const float4*)src, n);
   return cudaGetLastError();
 }
-template <typename RL, int NC>
-cudaError_t launch_dslash_h16(const GeomH& gh, void* out, const void* in, const void* x, const void* pdot,
-                              const void* U, int out_par, int dag, int mode, double b, double* partial,
-                              CgDev* cgd, cudaStream_t st) {
-  Gauge<RL, NC> u;
+template <typename S, int NC>
+static cudaError_t dslash16(const GeomH& gh, void* out, const void* in, const void* x, const void* pdot,
+                            const void* U, int out_par, int dag, int mode, double b, double* partial, CgDev* cgd,
+                            cudaStream_t st) {
+  typedef typename Conv16<S>::T2 T2;
+  Gauge<S, NC> u;
   u.p = const_cast<void*>(U);
   u.V = gh.V;
   const Geom g = to_devg(gh);
   const int nb = dslash_blocks(gh.Vh);
 #define FG_DH(D, M)                                                                                            \
-  dslash_kernel<RL, NC, float, D, M, Half16><<<nb, kDslashThreads, 0, st>>>(                                  \
-      (__half2*)out, (const __half2*)in, (const __half2*)x, (const __half2*)pdot, u, g, out_par, float(b),     \
-      partial, cgd)
+  dslash_kernel<S, NC, float, D, M, S><<<nb, kDslashThreads, 0, st>>>(                                        \
+      (T2*)out, (const T2*)in, (const T2*)x, (const T2*)pdot, u, g, out_par, float(b), partial, cgd)
   if (dag) {
     if (mode == 0) FG_DH(1, 0); else if (mode == 1) FG_DH(1, 1); else FG_DH(1, 2);
   } else {
@@ -998,20 +1004,37 @@ cudaError_t launch_dslash_h16(const GeomH& gh, void* out, const void* in, const 
 #undef FG_DH
   return cudaGetLastError();
 }
-template cudaError_t launch_dslash_h16<Half16, 9>(const GeomH&, void*, const void*, const void*, const void*,
-                                                  const void*, int, int, int, double, double*, CgDev*, cudaStream_t);
-template cudaError_t launch_dslash_h16<Half16, 6>(const GeomH&, void*, const void*, const void*, const void*,
-                                                  const void*, int, int, int, double, double*, CgDev*, cudaStream_t);
-cudaError_t launch_cg_axpy_h16(void* xs, void* r, const void* p, const void* ap, CgDev* cgd, double* rr_part, int n,
-                               cudaStream_t st) {
-  cg_axpy_h16_kernel<<<vec_blocks(n), kVecThreads, 0, st>>>((float2*)xs, (__half2*)r, (const __half2*)p,
-                                                            (const __half2*)ap, cgd, rr_part, n);
+template <int NC>
+cudaError_t launch_dslash_h16(int s16, const GeomH& gh, void* out, const void* in, const void* x, const void* pdot,
+                              const void* U, int out_par, int dag, int mode, double b, double* partial,
+                              CgDev* cgd, cudaStream_t st) {
+  return s16 == S16_BF16
+             ? dslash16<BF16, NC>(gh, out, in, x, pdot, U, out_par, dag, mode, b, partial, cgd, st)
+             : dslash16<Half16, NC>(gh, out, in, x, pdot, U, out_par, dag, mode, b, partial, cgd, st);
+}
+template cudaError_t launch_dslash_h16<9>(int, const GeomH&, void*, const void*, const void*, const void*,
+                                          const void*, int, int, int, double, double*, CgDev*, cudaStream_t);
+template cudaError_t launch_dslash_h16<6>(int, const GeomH&, void*, const void*, const void*, const void*,
+                                          const void*, int, int, int, double, double*, CgDev*, cudaStream_t);
+// Runs KERNEL<S> with the arguments that follow for the 16-bit format s16.
+#define FG_S16(KERNEL, GRID, ...)                                                                              \
+  do {                                                                                                         \
+    if (s16 == S16_BF16) {                                                                                     \
+      typedef Conv16<BF16>::T2 T2;                                                                             \
+      KERNEL<BF16><<<GRID, kVecThreads, 0, st>>>(__VA_ARGS__);                                                 \
+    } else {                                                                                                   \
+      typedef Conv16<Half16>::T2 T2;                                                                           \
+      KERNEL<Half16><<<GRID, kVecThreads, 0, st>>>(__VA_ARGS__);                                               \
+    }                                                                                                          \
+  } while (0)
+cudaError_t launch_cg_axpy_h16(int s16, void* xs, void* r, const void* p, const void* ap, CgDev* cgd,
+                               double* rr_part, int n, cudaStream_t st) {
+  FG_S16(cg_axpy_h16_kernel, vec_blocks(n), (float2*)xs, (T2*)r, (const T2*)p, (const T2*)ap, cgd, rr_part, n);
   return cudaGetLastError();
 }
-cudaError_t launch_cg_xpay_h16(void* p, const void* r, CgDev* cgd, double* hist, int* iter_out, int maxiter, int n,
-                               cudaStream_t st) {
-  cg_xpay_h16_kernel<<<vec_blocks(n), kVecThreads, 0, st>>>((__half2*)p, (const __half2*)r, cgd, hist, iter_out,
-                                                            maxiter, n);
+cudaError_t launch_cg_xpay_h16(int s16, void* p, const void* r, CgDev* cgd, double* hist, int* iter_out,
+                               int maxiter, int n, cudaStream_t st) {
+  FG_S16(cg_xpay_h16_kernel, vec_blocks(n), (T2*)p, (const T2*)r, cgd, hist, iter_out, maxiter, n);
   return cudaGetLastError();
 }
 cudaError_t launch_cg_init_h16(const double* part, int nparts, CgDev* cgd, double tol2, double* bb_out, int n,
@@ -1019,12 +1042,13 @@ cudaError_t launch_cg_init_h16(const double* part, int nparts, CgDev* cgd, doubl
   cg_init_h16_kernel<<<1, 256, 0, st>>>(part, nparts, cgd, tol2, bb_out, n);
   return cudaGetLastError();
 }
-cudaError_t launch_scale_to_h16(void* rs, const void* b64, const CgDev* cgd, int n, cudaStream_t st) {
-  scale_to_h16_kernel<<<vec_blocks(n), kVecThreads, 0, st>>>((__half2*)rs, (const double2*)b64, cgd, n);
+cudaError_t launch_scale_to_h16(int s16, void* rs, const void* b64, const CgDev* cgd, int n, cudaStream_t st) {
+  FG_S16(scale_to_h16_kernel, vec_blocks(n), (T2*)rs, (const double2*)b64, cgd, n);
   return cudaGetLastError();
 }
-cudaError_t launch_h16_to_double_scaled(void* dst64, const void* src16, const CgDev* cgd, int n, cudaStream_t st) {
-  h16_to_double_scaled_kernel<<<vec_blocks(n), kVecThreads, 0, st>>>((double2*)dst64, (const __half2*)src16, cgd, n);
+cudaError_t launch_h16_to_double_scaled(int s16, void* dst64, const void* src16, const CgDev* cgd, int n,
+                                        cudaStream_t st) {
+  FG_S16(h16_to_double_scaled_kernel, vec_blocks(n), (double2*)dst64, (const T2*)src16, cgd, n);
   return cudaGetLastError();
 }
 cudaError_t launch_ru_accumulate_df_scaled(void* xdf, void* xs, const CgDev* cgd, int n, cudaStream_t st) {
@@ -1046,16 +1070,27 @@ cudaError_t launch_ru_publish_h16(const double* part, int nparts, CgDev* cgd, do
   ru_publish_h16_kernel<<<1, 256, 0, st>>>(part, nparts, cgd, true_rr, n);
   return cudaGetLastError();
 }
-cudaError_t launch_ru_rescale_df_h16(const void* rdf, void* rs, void* p, const CgDev* cgd, int n, cudaStream_t st) {
-  ru_rescale_h16_kernel<float4><<<vec_blocks(n), kVecThreads, 0, st>>>((const float4*)rdf, (__half2*)rs,
-                                                                       (__half2*)p, cgd, n);
+cudaError_t launch_ru_rescale_df_h16(int s16, const void* rdf, void* rs, void* p, const CgDev* cgd, int n,
+                                     cudaStream_t st) {
+  if (s16 == S16_BF16)
+    ru_rescale_h16_kernel<BF16, float4><<<vec_blocks(n), kVecThreads, 0, st>>>(
+        (const float4*)rdf, (Conv16<BF16>::T2*)rs, (Conv16<BF16>::T2*)p, cgd, n);
+  else
+    ru_rescale_h16_kernel<Half16, float4><<<vec_blocks(n), kVecThreads, 0, st>>>(
+        (const float4*)rdf, (Conv16<Half16>::T2*)rs, (Conv16<Half16>::T2*)p, cgd, n);
   return cudaGetLastError();
 }
-cudaError_t launch_ru_rescale64_h16(const void* r64, void* rs, void* p, const CgDev* cgd, int n, cudaStream_t st) {
-  ru_rescale_h16_kernel<double2><<<vec_blocks(n), kVecThreads, 0, st>>>((const double2*)r64, (__half2*)rs,
-                                                                        (__half2*)p, cgd, n);
+cudaError_t launch_ru_rescale64_h16(int s16, const void* r64, void* rs, void* p, const CgDev* cgd, int n,
+                                    cudaStream_t st) {
+  if (s16 == S16_BF16)
+    ru_rescale_h16_kernel<BF16, double2><<<vec_blocks(n), kVecThreads, 0, st>>>(
+        (const double2*)r64, (Conv16<BF16>::T2*)rs, (Conv16<BF16>::T2*)p, cgd, n);
+  else
+    ru_rescale_h16_kernel<Half16, double2><<<vec_blocks(n), kVecThreads, 0, st>>>(
+        (const double2*)r64, (Conv16<Half16>::T2*)rs, (Conv16<Half16>::T2*)p, cgd, n);
   return cudaGetLastError();
 }
+#undef FG_S16
 cudaError_t launch_dot64(const void* a, const void* b, double* part, int n, cudaStream_t st) {
   dot64_kernel<<<vec_blocks(n), kVecThreads, 0, st>>>((const double2*)a, (const double2*)b, part, n);
   return cudaGetLastError();
@@ -1097,26 +1132,33 @@ template cudaError_t launch_dslash<Half16, 6, float>(const GeomH&, void*, const 
                                                      const void*, const void*, int, int, int, double, double*,
                                                      CgDev*, cudaStream_t);
 
-template <int NC>
-__global__ void __launch_bounds__(256) links_to_half_kernel(Gauge<float, NC> in, Gauge<Half16, NC> out, int V) {
+template <typename S, int NC>
+__global__ void __launch_bounds__(256) links_to_half_kernel(Gauge<float, NC> in, Gauge<S, NC> out, int V) {
   const int s = blockIdx.x * 64 + threadIdx.x;
   const int mu = threadIdx.y;
   if (s >= V) return;
   out.store(mu, s, in.load(mu, s));
 }
 template <int NC>
-cudaError_t launch_links_to_half(const GeomH& gh, const void* U32, void* U16, cudaStream_t st) {
+cudaError_t launch_links_to_half(int s16, const GeomH& gh, const void* U32, void* U16, cudaStream_t st) {
   Gauge<float, NC> a;
   a.p = const_cast<void*>(U32);
   a.V = gh.V;
-  Gauge<Half16, NC> b;
-  b.p = U16;
-  b.V = gh.V;
-  links_to_half_kernel<NC><<<(gh.V + 63) / 64, dim3(64, 4), 0, st>>>(a, b, gh.V);
+  if (s16 == S16_BF16) {
+    Gauge<BF16, NC> b;
+    b.p = U16;
+    b.V = gh.V;
+    links_to_half_kernel<BF16, NC><<<(gh.V + 63) / 64, dim3(64, 4), 0, st>>>(a, b, gh.V);
+  } else {
+    Gauge<Half16, NC> b;
+    b.p = U16;
+    b.V = gh.V;
+    links_to_half_kernel<Half16, NC><<<(gh.V + 63) / 64, dim3(64, 4), 0, st>>>(a, b, gh.V);
+  }
   return cudaGetLastError();
 }
-template cudaError_t launch_links_to_half<9>(const GeomH&, const void*, void*, cudaStream_t);
-template cudaError_t launch_links_to_half<6>(const GeomH&, const void*, void*, cudaStream_t);
+template cudaError_t launch_links_to_half<9>(int, const GeomH&, const void*, void*, cudaStream_t);
+template cudaError_t launch_links_to_half<6>(int, const GeomH&, const void*, void*, cudaStream_t);
 
 template cudaError_t launch_dslash<float, 9, DF>(const GeomH&, void*, const void*, const void*, const void*,
                                                  const void*, int, int, int, double, double*, CgDev*, cudaStream_t);

@@ -12,6 +12,7 @@
 //   spinor  Pair[6][Vh]         entries spin * 3 + colour, two per pair, one parity
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -472,34 +473,54 @@ template <> struct Quad<double> {
   }
 };
 
-// IEEE half storage (tag Half16) with FP32 arithmetic: links of the inner
-// solver and, with a per-solve-cycle scale, its spinor vectors.  A complex
-// number is one __half2, a pair of entries 8 bytes.
+// 16-bit storage with FP32 arithmetic for the inner solver: links and, with
+// a per-solve-cycle scale, its spinor vectors.  A complex number is one pair
+// of 16-bit reals (32 bits), a pair of entries 8 bytes.  Two formats:
+//  * Half16: IEEE binary16, 11 significant bits (unit roundoff 2^-11);
+//  * BF16: bfloat16, the exponent range of FP32 with 8 significant bits
+//    (unit roundoff 2^-8).
 struct Half16 {};
+struct BF16 {};
 template <> struct Vec2<Half16> { typedef __half2 T; };
-__device__ __forceinline__ Cx<float> h2_to_cx(unsigned int w) {
-  const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w));
+template <> struct Vec2<BF16> { typedef __nv_bfloat162 T; };
+// conversions of one complex number (or any pair of reals) to and from the
+// 32-bit pair, round to nearest even
+template <typename S> struct Conv16;
+template <> struct Conv16<Half16> {
+  typedef __half2 T2;
+  static __device__ __forceinline__ float2 f2(T2 h) { return __half22float2(h); }
+  static __device__ __forceinline__ T2 of(float2 v) { return __float22half2_rn(v); }
+};
+template <> struct Conv16<BF16> {
+  typedef __nv_bfloat162 T2;
+  static __device__ __forceinline__ float2 f2(T2 h) { return __bfloat1622float2(h); }
+  static __device__ __forceinline__ T2 of(float2 v) { return __float22bfloat162_rn(v); }
+};
+template <typename S> __device__ __forceinline__ Cx<float> w16_to_cx(unsigned int w) {
+  const float2 f = Conv16<S>::f2(*reinterpret_cast<const typename Conv16<S>::T2*>(&w));
   return cx<float>(f.x, f.y);
 }
-__device__ __forceinline__ unsigned int cx_to_h2(const Cx<float>& c) {
-  const __half2 h = __floats2half2_rn(c.re, c.im);
+template <typename S> __device__ __forceinline__ unsigned int cx_to_w16(const Cx<float>& c) {
+  const typename Conv16<S>::T2 h = Conv16<S>::of(make_float2(c.re, c.im));
   return *reinterpret_cast<const unsigned int*>(&h);
 }
-template <> struct Quad<Half16> {
+template <typename S> struct Quad16 {
   static __device__ __forceinline__ void load(const void* base, size_t idx, Cx<float>& a, Cx<float>& b) {
     const uint2 v = __ldg((const uint2*)base + idx);
-    a = h2_to_cx(v.x);
-    b = h2_to_cx(v.y);
+    a = w16_to_cx<S>(v.x);
+    b = w16_to_cx<S>(v.y);
   }
   static __device__ __forceinline__ void load_cg(const void* base, size_t idx, Cx<float>& a, Cx<float>& b) {
     const uint2 v = ((const uint2*)base)[idx];
-    a = h2_to_cx(v.x);
-    b = h2_to_cx(v.y);
+    a = w16_to_cx<S>(v.x);
+    b = w16_to_cx<S>(v.y);
   }
   static __device__ __forceinline__ void store(void* base, size_t idx, Cx<float> a, Cx<float> b) {
-    ((uint2*)base)[idx] = make_uint2(cx_to_h2(a), cx_to_h2(b));
+    ((uint2*)base)[idx] = make_uint2(cx_to_w16<S>(a), cx_to_w16<S>(b));
   }
 };
+template <> struct Quad<Half16> : Quad16<Half16> {};
+template <> struct Quad<BF16> : Quad16<BF16> {};
 
 // Links: NP = NC / 2 pairs per link in [mu][pair][site] order, then, for
 // NC = 9, the ninth entry of every link in [mu][site] order.
@@ -542,17 +563,17 @@ template <typename R, int NC> struct Gauge {
   }
 };
 
-// Links stored in IEEE half precision for the inner Dslash of the solver
-// (entries of an SU(3) matrix lie in [-1, 1], so half keeps ~5e-4 relative
-// precision and needs no scale).  Same layout as Gauge<float, NC> with two
-// bytes per real: a pair of entries is 8 bytes, the NC = 9 tail 4 bytes.
-// Loads return FP32 matrices.
-template <int NC> struct Gauge<Half16, NC> {
+// Links stored in a 16-bit format (Half16 or BF16) for the inner Dslash of
+// the solver (entries of an SU(3) matrix lie in [-1, 1], so neither format
+// needs a scale).  Same layout as Gauge<float, NC> with two bytes per real:
+// a pair of entries is 8 bytes, the NC = 9 tail 4 bytes.  Loads return FP32
+// matrices.
+template <typename S, int NC> struct Gauge16 {
   static constexpr int NP = NC / 2;
   void* __restrict__ p;
   int V;
-  static __device__ __forceinline__ Cx<float> cx_of(unsigned int w) { return h2_to_cx(w); }
-  static __device__ __forceinline__ unsigned int word_of(const Cx<float>& c) { return cx_to_h2(c); }
+  static __device__ __forceinline__ Cx<float> cx_of(unsigned int w) { return w16_to_cx<S>(w); }
+  static __device__ __forceinline__ unsigned int word_of(const Cx<float>& c) { return cx_to_w16<S>(c); }
   __device__ __forceinline__ M3<float> load(int mu, int s) const {
     M3<float> m;
 #pragma unroll
@@ -580,6 +601,8 @@ template <int NC> struct Gauge<Half16, NC> {
     }
   }
 };
+template <int NC> struct Gauge<Half16, NC> : Gauge16<Half16, NC> {};
+template <int NC> struct Gauge<BF16, NC> : Gauge16<BF16, NC> {};
 
 // Momenta and forces: the 8 Gell-Mann coefficients of a link as two pairs of
 // (re, im)-like slots, [mu][pair][site].

@@ -48,9 +48,13 @@ cudaError_t launch_dslash(const GeomH& g, void* out, const void* in, const void*
                           const void* U, int out_par, int dag, int mode, double b, double* partial,
                           CgDev* cgd, cudaStream_t st);
 
-// Half-precision copy of FP32 links (NC entries per link) for the inner Dslash.
+// 16-bit formats of the inner solver's links and vectors (argument s16).
+enum { S16_HALF = 0, S16_BF16 = 1 };
+
+// 16-bit copy (format s16) of FP32 links (NC entries per link) for the inner
+// Dslash.
 template <int NC>
-cudaError_t launch_links_to_half(const GeomH& g, const void* U32, void* U16, cudaStream_t st);
+cudaError_t launch_links_to_half(int s16, const GeomH& g, const void* U32, void* U16, cudaStream_t st);
 
 // Pseudofermion force (8 Gell-Mann components per link) into FF (momentum
 // layout, precision RL); accumulate != 0 adds to FF.
@@ -81,24 +85,26 @@ cudaError_t launch_ru_residual_df(const void* bdf, const void* axdf, void* rs, d
                                   cudaStream_t st);
 cudaError_t launch_df_from_double(void* dst, const void* src, int n, cudaStream_t st);
 cudaError_t launch_df_to_double(void* dst, const void* src, int n, cudaStream_t st);
-// ---- half-precision inner vectors (r, p, Ap and the Dslash temporaries as
-// __half2, scaled by 1/sigma; the solution increment x_s stays FP32)
-// Dslash with half-precision spinors, FP32 arithmetic, links RL (float or Half16).
-template <typename RL, int NC>
-cudaError_t launch_dslash_h16(const GeomH& g, void* out, const void* in, const void* x, const void* pdot,
+// ---- 16-bit inner vectors (r, p, Ap and the Dslash temporaries as pairs of
+// IEEE half (s16 = S16_HALF) or bfloat16 (S16_BF16) reals, scaled by
+// 1/sigma; the solution increment x_s stays FP32)
+// Dslash with 16-bit links and spinors of format s16, FP32 arithmetic.
+template <int NC>
+cudaError_t launch_dslash_h16(int s16, const GeomH& g, void* out, const void* in, const void* x, const void* pdot,
                               const void* U, int out_par, int dag, int mode, double b, double* partial,
                               CgDev* cgd, cudaStream_t st);
-cudaError_t launch_cg_axpy_h16(void* xs, void* r, const void* p, const void* ap, CgDev* cgd, double* rr_part, int n,
-                               cudaStream_t st);
-cudaError_t launch_cg_xpay_h16(void* p, const void* r, CgDev* cgd, double* hist, int* iter_out, int maxiter, int n,
-                               cudaStream_t st);
+cudaError_t launch_cg_axpy_h16(int s16, void* xs, void* r, const void* p, const void* ap, CgDev* cgd,
+                               double* rr_part, int n, cudaStream_t st);
+cudaError_t launch_cg_xpay_h16(int s16, void* p, const void* r, CgDev* cgd, double* hist, int* iter_out,
+                               int maxiter, int n, cudaStream_t st);
 // Start of a solve: bb from the partials of |b|^2, sigma^2 = bb / n, rr = n, tol2bb, done.
 cudaError_t launch_cg_init_h16(const double* part, int nparts, CgDev* cgd, double tol2, double* bb_out, int n,
                                cudaStream_t st);
 // rs = b / sigma (b FP64).
-cudaError_t launch_scale_to_h16(void* rs, const void* b64, const CgDev* cgd, int n, cudaStream_t st);
-// dst (FP64) = sigma src (half-precision vector in scaled units).
-cudaError_t launch_h16_to_double_scaled(void* dst64, const void* src16, const CgDev* cgd, int n, cudaStream_t st);
+cudaError_t launch_scale_to_h16(int s16, void* rs, const void* b64, const CgDev* cgd, int n, cudaStream_t st);
+// dst (FP64) = sigma src (16-bit vector in scaled units).
+cudaError_t launch_h16_to_double_scaled(int s16, void* dst64, const void* src16, const CgDev* cgd, int n,
+                                        cudaStream_t st);
 // x (double-float) += sigma x_s; x_s = 0.
 cudaError_t launch_ru_accumulate_df_scaled(void* xdf, void* xs, const CgDev* cgd, int n, cudaStream_t st);
 // r = b - Ax written over Ax (double-float), partials of |r|^2.
@@ -106,13 +112,15 @@ cudaError_t launch_ru_residual_df_keep(const void* bdf, void* axdf, double* part
 // r = b - Ax written to r64 (FP64), partials of |r|^2.
 cudaError_t launch_ru_residual64_keep(const void* b64, const void* ax64, void* r64, double* part, int n,
                                       cudaStream_t st);
-// Publish a true residual for the half-precision solver: rr, restart, new
+// Publish a true residual for the 16-bit solver: rr, restart, new
 // sigma^2 and rho, rr[iter&1] in the new scaling, done.
 cudaError_t launch_ru_publish_h16(const double* part, int nparts, CgDev* cgd, double* true_rr, int n,
                                   cudaStream_t st);
 // rs = r / sigma (r double-float or FP64); p = restart ? rs : rho p.
-cudaError_t launch_ru_rescale_df_h16(const void* rdf, void* rs, void* p, const CgDev* cgd, int n, cudaStream_t st);
-cudaError_t launch_ru_rescale64_h16(const void* r64, void* rs, void* p, const CgDev* cgd, int n, cudaStream_t st);
+cudaError_t launch_ru_rescale_df_h16(int s16, const void* rdf, void* rs, void* p, const CgDev* cgd, int n,
+                                     cudaStream_t st);
+cudaError_t launch_ru_rescale64_h16(int s16, const void* r64, void* rs, void* p, const CgDev* cgd, int n,
+                                    cudaStream_t st);
 
 // Publish a reliable update's true residual: rr, restart (true residual more
 // than twice the iterated one), and with final != 0 done (rr <= tol2bb).

@@ -263,7 +263,7 @@ fg_status fg_lattice_create(const fg_params* p, fg_lattice** out) {
   const long long V = (long long)p->dims[0] * p->dims[1] * p->dims[2] * p->dims[3];
   if (V > (1LL << 28)) return FG_EINVAL;  // 32-bit element indices of links and momenta: 16 V - 1 < 2^32
   if (p->precision != FG_FP64 && p->precision != FG_FP32 && p->precision != FG_FP32_FP16CG &&
-      p->precision != FG_DF64 && p->precision != FG_FP32_AUTOCG)
+      p->precision != FG_DF64 && p->precision != FG_FP32_AUTOCG && p->precision != FG_FP32_BF16CG)
     return FG_EINVAL;
   if (p->precision == FG_DF64 && p->kappa != 0.0) return FG_EINVAL;  // double-float handles are pure gauge
   if (p->link_reals != 18 && p->link_reals != 12) return FG_EINVAL;
@@ -275,7 +275,10 @@ fg_status fg_lattice_create(const fg_params* p, fg_lattice** out) {
   h->prm = *p;
   if (h->prm.reunitarize < 0)
     h->prm.reunitarize =
-        (p->precision == FG_FP32 || p->precision == FG_FP32_FP16CG || p->precision == FG_FP32_AUTOCG) ? 1 : 0;
+        (p->precision == FG_FP32 || p->precision == FG_FP32_FP16CG || p->precision == FG_FP32_AUTOCG ||
+         p->precision == FG_FP32_BF16CG)
+            ? 1
+            : 0;
   if (!(h->prm.alpha > 0.0)) h->prm.alpha = 0.1932;
   fg_status s = lattice_init(h);
   if (s != FG_OK) {

@@ -24,7 +24,7 @@ STATUS_NAMES = {0: "FG_OK", 1: "FG_EINVAL", 2: "FG_ENOMEM", 3: "FG_ECUDA", 4: "F
                 5: "FG_ETIMEOUT", 6: "FG_ESTATE"}
 INTEGRATORS = {"leapfrog": 0, "omelyan": 1, "fg": 2, "force_gradient": 2, "campostrini": 3, "qpq": 4,
                "fg_analytic": 5}
-PRECISIONS = {"fp64": 0, "fp32": 1, "fp32_fp16cg": 2, "df64": 3, "fp32_autocg": 4}
+PRECISIONS = {"fp64": 0, "fp32": 1, "fp32_fp16cg": 2, "df64": 3, "fp32_autocg": 4, "fp32_bf16cg": 5}
 
 # Every function the header declares, with its ctypes signature.
 _vp, _dp, _i, _d = C.c_void_p, C.POINTER(C.c_double), C.c_int, C.c_double

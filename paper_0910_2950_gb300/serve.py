@@ -114,12 +114,12 @@ def footprint_bytes(spec: ChainSpec, precision: str = "fp32", link_reals: int = 
         n64 = 8 + (2 if precision != "fp64" else 0)
         dslash_blocks = (vh + 127) // 128
         vec_blocks = min((nvec + 255) // 256, 152 * 8)
-        half = precision == "fp32_fp16cg" or (
+        half = precision in ("fp32_fp16cg", "fp32_bf16cg") or (
             precision == "fp32_autocg" and v * (4 * (link_reals // 2) * 8 + 6 * 48) > l2_bytes)
         n_inner = 10 if half else 12
         total += n64 * nvec * 16 + n_inner * nvec * 2 * r + mom + 128 + 8 * (3 * dslash_blocks + 2 * vec_blocks + 3)
         if half:
-            total += 4 * v * link_reals * 2      # half-precision links of the inner solver
+            total += 4 * v * link_reals * 2      # 16-bit links of the inner solver
     return total + 4096
 
 

@@ -123,6 +123,28 @@ def test_inner_dslash_half_element_by_element(fgmod, dims, link_reals, dagger):
     assert 1e-5 < err < 5e-3, err    # half-precision rounding is visible, and bounded
 
 
+@pytest.mark.parametrize("dims", INNER_DIMS)
+@pytest.mark.parametrize("link_reals", [18, 12])
+@pytest.mark.parametrize("dagger", [0, 1])
+def test_inner_dslash_bf16_element_by_element(fgmod, dims, link_reals, dagger):
+    """The bfloat16 inner operator (FG_FP32_BF16CG: bfloat16 links and
+    spinors scaled to unit rms, FP32 arithmetic) against the oracle:
+    bfloat16 keeps 8 significant bits (unit roundoff 3.9e-3) in the links,
+    the input and the intermediate vector, bound 4e-2 of the largest entry
+    (the half-precision test's 10 units of roundoff); its error lies above
+    the half-precision operator's on the same input, as 3 fewer bits give."""
+    u, psi, ref, _ = _inner_case(dims)
+    out = {}
+    for prec in ("fp32_bf16cg", "fp32_fp16cg"):
+        with fgmod.Lattice(dims, BETA, kappa=KAPPA, precision=prec, link_reals=link_reals) as lat:
+            lat.set_gauge(u)
+            out[prec] = lat.apply_mhat_inner(psi, dagger=bool(dagger))
+    err = _rel(out["fp32_bf16cg"], ref[dagger])
+    err_half = _rel(out["fp32_fp16cg"], ref[dagger])
+    assert 1e-4 < err < 4e-2, err
+    assert err > 2 * err_half, (err, err_half)
+
+
 @pytest.mark.parametrize("dims,same_as", [((16, 16, 16, 32), "fp32"), ((24, 24, 24, 48), "fp32_fp16cg")])
 def test_autocg_follows_the_l2_size(fgmod, dims, same_as):
     """FG_FP32_AUTOCG runs the FP32 inner solver while its working set fits
@@ -149,7 +171,7 @@ def test_inner_dslash_fp64_is_apply_mhat(fgmod):
     assert _rel(out, ref[0]) < 1e-13
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_fp16cg"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_fp16cg", "fp32_bf16cg"])
 @pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 2, 6)])
 def test_cg_solve(fgmod, precision, dims):
     u = inputs.hot_start(dims, 5)
@@ -340,7 +362,7 @@ def test_fermion_fg_trajectory_dh_fp64(fgmod, fermion_traj_oracle, dt):
     assert r["cg_iters"] > 0
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp32_fp16cg"])
+@pytest.mark.parametrize("precision", ["fp32", "fp32_fp16cg", "fp32_bf16cg"])
 def test_fermion_fg_trajectory_fp32_mixed(fgmod, fermion_traj_oracle, precision):
     dims, u, p, chi, ref = fermion_traj_oracle
     with fgmod.Lattice(dims, BETA, kappa=KAPPA, precision=precision, cg_tol=1e-10,

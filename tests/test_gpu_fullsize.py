@@ -151,7 +151,7 @@ def test_mhat_16x16x16x32_fp32_links(fgmod, nf2_case):
     assert np.max(np.abs(outd - refd)) < 1e-13 * np.max(np.abs(refd))
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp32_fp16cg"])
+@pytest.mark.parametrize("precision", ["fp32", "fp32_fp16cg", "fp32_bf16cg"])
 def test_cg_and_force_16x16x16x32(fgmod, nf2_case, precision):
     dims, u, u32 = nf2_case
     kappa, tol = 0.158, 1e-10

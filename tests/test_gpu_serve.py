@@ -156,7 +156,7 @@ def test_served_results_match_the_oracle(fgmod):
 @pytest.mark.parametrize("spec", [serve.ChainSpec((8, 8, 8, 8), 6.0, 0.0, 1),
                                   serve.ChainSpec((8, 8, 8, 16), 5.6, 0.157, 2),
                                   serve.ChainSpec((6, 6, 6, 12), 5.6, 0.155, 3)])
-@pytest.mark.parametrize("precision", ["fp32", "fp32_fp16cg", "fp64"])
+@pytest.mark.parametrize("precision", ["fp32", "fp32_fp16cg", "fp32_bf16cg", "fp64"])
 def test_footprint_bounds_the_library_allocation(fgmod, spec, precision):
     """Admission by HBM footprint is only safe if the estimate is an upper
     bound of what a chain's handle holds after a trajectory (all lazy
