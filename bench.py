@@ -447,6 +447,10 @@ DSLASH_BYTES_FP32_18 = 8 * 96 + 8 * 72 + 96
 # counted above as its input (6 x 96): (4 * 768 + 96 + 288 + 576) / 4 =
 # 1008 B on average.
 DSLASH_BYTES_CG_AVG = (4 * (8 * 72 + 96 + 96) + 96 + 3 * 96 + 6 * 96) // 4
+# The same for the six-launch iteration (four Dslash launches, then axpy and
+# xpay): t_o = D p, t_e = p - k2 D t_o (+96, the p read), t_o = D^dag t_e,
+# Ap = t_e - k2 D^dag t_o with <p, Ap> (+2 x 96): (4 * 768 + 96 + 192) / 4.
+DSLASH_BYTES_CG_SIX = (4 * (8 * 72 + 96 + 96) + 96 + 2 * 96) // 4
 DSLASH_FLOP = 1320
 
 
@@ -489,6 +493,34 @@ def fermion_measurement(fg, stream, rank, hbm_peak, dims=(16, 16, 16, 32)):
     _, info = lat.cg_solve(bs[-1])
     cls = {c: lat.kernel_time(c) for c in ("dslash", "dslash_df", "dslash_fp64", "cg_blas", "reduce", "convert")}
     lat.timing(False)
+    # the library folds the vector updates into the Dslash launches on small
+    # lattices only; the six-launch form runs two vector kernels per iteration
+    folded = cls["cg_blas"][1] < info["iterations"]
+    # the same solves with the other iteration form forced
+    prev_fold = os.environ.get("FG_CG_FOLD")
+    os.environ["FG_CG_FOLD"] = "0" if folded else "1"
+    try:
+        with fg.Lattice(dims, 5.6, kappa=0.158, precision="fp32", cg_tol=1e-10, seed=400 + rank,
+                        stream=stream) as lalt:
+            lalt.set_gauge(u)
+            lalt.cg_solve(bs[0])
+            t0 = time.perf_counter()
+            its_alt = sum(lalt.cg_solve(bs[1 + k])[1]["iterations"] for k in range(solves))
+            wall_alt = time.perf_counter() - t0
+            lalt.timing(True)
+            lalt.timing_reset()
+            lalt.cg_solve(bs[-1])
+            cls_alt = {c: lalt.kernel_time(c)[0] for c in ("dslash", "dslash_df", "dslash_fp64", "cg_blas", "reduce",
+                                                           "convert")}
+            lalt.timing(False)
+    finally:
+        if prev_fold is None:
+            del os.environ["FG_CG_FOLD"]
+        else:
+            os.environ["FG_CG_FOLD"] = prev_fold
+    other_form = {"iteration": "six launches" if folded else "folded (four launches)",
+                  "ms_per_solve": 1000 * wall_alt / solves, "cg_iterations_per_solve": its_alt / solves,
+                  "cg_blas_ms_share": cls_alt["cg_blas"] / max(sum(cls_alt.values()), 1e-9)}
     # pseudofermion force kernel: compulsory bytes per link = U (72) + F^a out
     # (32) + a quarter of the site's Xt and Yt spinors (2 x 96 / 4).  Each
     # force() solves for X first, so the kernel reads links and spinors the
@@ -595,7 +627,8 @@ def fermion_measurement(fg, stream, rank, hbm_peak, dims=(16, 16, 16, 32)):
     inner16 = inner_precision_measurement(fg, stream, rank, u, dims)
     ds_ms, ds_n = cls["dslash"]
     avg = ds_ms / 1000.0 / max(ds_n, 1)
-    achieved = DSLASH_BYTES_CG_AVG * vh / avg / 1e9
+    dslash_bytes = DSLASH_BYTES_CG_AVG if folded else DSLASH_BYTES_CG_SIX
+    achieved = dslash_bytes * vh / avg / 1e9
     return {
         "workload": f"Nf=2 Wilson {dims[0]}^3x{dims[3]}, beta=5.6, kappa=0.158, even-odd CG on Mhat^dag Mhat "
                     "to 1e-10 (FP32 inner, FP64 reliable updates), gauge field: hot start + 50 FG trajectories",
@@ -608,11 +641,13 @@ def fermion_measurement(fg, stream, rank, hbm_peak, dims=(16, 16, 16, 32)):
         "launches_per_solve_by_class": {c: v[1] for c, v in cls.items()},
         "dslash_roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                             "frac": achieved / hbm_peak, "traffic": None,
-                            "bytes_per_site": DSLASH_BYTES_CG_AVG,
+                            "bytes_per_site": dslash_bytes,
                             "bytes_per_site_no_cache_reuse": DSLASH_BYTES_FP32_18,
                             "sites_per_launch": vh, "avg_launch_us": avg * 1e6, "launches": ds_n,
                             "gflops": DSLASH_FLOP * vh / avg / 1e9},
         "cg_blas_ms_share": cls["cg_blas"][0] / max(sum(v[0] for v in cls.values()), 1e-9),
+        "cg_iteration": "folded (four launches)" if folded else "six launches (four Dslash, axpy, xpay)",
+        "cg_other_iteration_form": other_form,
         "fermion_force_roofline": ff_roof,
         "trajectories": trajs,
         "half_precision_cg": half,

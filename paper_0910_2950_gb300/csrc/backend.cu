@@ -482,12 +482,22 @@ class Backend final : public IBackend {
   // rs_ and p_ always name the current ones
   void *rs2_ = nullptr, *p2_ = nullptr;
   // Folded CG iterations (four launches, vector updates inside the Dslash
-  // launches) for FP32 and FP64 inner vectors; the half-precision solver
-  // keeps its six launches.  FG_CG_FOLD=0 in the environment selects the six
-  // launches everywhere (tuning and comparison).
-  const bool fold_ = [] {
+  // launches) or six (four Dslash, axpy, xpay) for FP32 and FP64 inner
+  // vectors.  The folded form forms p' at each of a site's eight neighbours,
+  // reading r, Ap and p per hop, to save two streaming vector passes and two
+  // launches: that pays on small lattices, whose solves are bound by launch
+  // latency (the 8^3 x 16 and 12^3 x 24 Nf=2 chains of the served mix), and
+  // loses from 16^3 x 32 up (FP32: 8.1 against 7.5 ms per solve at
+  // 16^3 x 32, 25.7 against 17.9 at 20^3 x 40, 38.8 against 34.2 at
+  // 24^3 x 48; FP64 9-11% slower).  Default: folded up to kFoldMaxVh even
+  // sites; FG_CG_FOLD=1 or 0 in the environment forces either form.  The
+  // 16-bit solvers always take six launches.
+  static constexpr int kFoldMaxVh = 32768;
+  const bool fold_ = [this] {
     const char* e = std::getenv("FG_CG_FOLD");
-    return !(e && e[0] == '0');
+    if (e && e[0] == '1') return true;
+    if (e && e[0] == '0') return false;
+    return g_.Vh <= kFoldMaxVh;
   }() && !half_links_;
   void *Xe_ = nullptr, *Xo_ = nullptr, *Ye_ = nullptr, *Yo_ = nullptr, *FF_ = nullptr;
   CgDev* cgd_ = nullptr;
