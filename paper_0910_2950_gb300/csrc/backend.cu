@@ -477,6 +477,17 @@ class Backend final : public IBackend {
     const double bytes = (double)g_.V * (4.0 * NC * 8.0 + 6.0 * 48.0);
     return bytes > (double)l2;
   }
+  // The same working set in this handle's precision (links and six
+  // half-lattice vectors of R).
+  bool solver_exceeds_l2() const {
+    int dev = 0, l2 = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess) {
+      cudaGetLastError();
+      return true;
+    }
+    const double bytes = (double)g_.V * (4.0 * NC * 2.0 + 6.0 * 12.0) * (double)sizeof(R);
+    return bytes > (double)l2;
+  }
   void *xs_ = nullptr, *rs_ = nullptr, *p_ = nullptr, *ap_ = nullptr, *te_ = nullptr, *to_ = nullptr;
   // the folded iteration writes r' and p' to the other buffer of a pair;
   // rs_ and p_ always name the current ones
@@ -485,19 +496,20 @@ class Backend final : public IBackend {
   // launches) or six (four Dslash, axpy, xpay) for FP32 and FP64 inner
   // vectors.  The folded form forms p' at each of a site's eight neighbours,
   // reading r, Ap and p per hop, to save two streaming vector passes and two
-  // launches: that pays on small lattices, whose solves are bound by launch
-  // latency (the 8^3 x 16 and 12^3 x 24 Nf=2 chains of the served mix), and
-  // loses from 16^3 x 32 up (FP32: 8.1 against 7.5 ms per solve at
-  // 16^3 x 32, 25.7 against 17.9 at 20^3 x 40, 38.8 against 34.2 at
-  // 24^3 x 48; FP64 9-11% slower).  Default: folded up to kFoldMaxVh even
-  // sites; FG_CG_FOLD=1 or 0 in the environment forces either form.  The
-  // 16-bit solvers always take six launches.
-  static constexpr int kFoldMaxVh = 32768;
+  // launches.  While the solver's links and vectors fit in L2 the extra hop
+  // reads hit L2 and the saved launches count (served 8^3 x 16 and
+  // 12^3 x 24 chains; 16^3 x 32 FP32 within run-to-run spread: 8.9 against
+  // 9.0 and 8.1 against 7.5 ms per solve on two fields); beyond L2 they
+  // cost DRAM bandwidth (FP32 25.7 against 17.9 ms at 20^3 x 40, 38.8
+  // against 34.2 at 24^3 x 48; FP64 at 16^3 x 32 61.7 against 56.6).
+  // Default: folded when the fields fit in L2; FG_CG_FOLD=1 or 0 in the
+  // environment forces either form.  The 16-bit solvers always take six
+  // launches.
   const bool fold_ = [this] {
     const char* e = std::getenv("FG_CG_FOLD");
     if (e && e[0] == '1') return true;
     if (e && e[0] == '0') return false;
-    return g_.Vh <= kFoldMaxVh;
+    return !solver_exceeds_l2();
   }() && !half_links_;
   void *Xe_ = nullptr, *Xo_ = nullptr, *Ye_ = nullptr, *Yo_ = nullptr, *FF_ = nullptr;
   CgDev* cgd_ = nullptr;
