@@ -96,13 +96,14 @@ def footprint_bytes(spec: ChainSpec, precision: str = "fp32", link_reals: int = 
     result scalars, the FP64 host-layout staging buffer, and for fermions 8
     FP64 and 10 working half-lattice spinors (plus 2 double-float ones for the
     FP32 solver's reliable updates, and the second r and p buffers of the
-    folded CG iteration unless the inner vectors are half precision), the
+    folded CG iteration, which the library runs while the solver's links
+    and six vectors fit in L2 and never with 16-bit inner vectors), the
     pseudofermion force, the CG scalars and the Dslash (three values) and
     vector block partials (two arrays of the latter).  4 KiB are added for allocator
     rounding of the small buffers.  (The closed-form force gradient's
     buffers are not included: the server does not offer that integrator.)
     `l2_bytes` is the GPU's L2 size, which decides FG_FP32_AUTOCG's inner
-    precision."""
+    precision and the CG iteration form."""
     v = int(np.prod(spec.dims))
     r = 8 if precision in ("fp64", "df64") else 4     # bytes per real (double-float: two floats)
     gauge = 4 * v * link_reals * r
@@ -116,7 +117,10 @@ def footprint_bytes(spec: ChainSpec, precision: str = "fp32", link_reals: int = 
         vec_blocks = min((nvec + 255) // 256, 152 * 8)
         half = precision in ("fp32_fp16cg", "fp32_bf16cg") or (
             precision == "fp32_autocg" and v * (4 * (link_reals // 2) * 8 + 6 * 48) > l2_bytes)
-        n_inner = 10 if half else 12
+        # the fold buffers are left out only well beyond L2, so that the
+        # estimate stays an upper bound whatever L2 size the library sees
+        folded = not half and v * (4 * (link_reals // 2) * 2 + 6 * 12) * r <= 1.25 * l2_bytes
+        n_inner = 12 if folded else 10
         total += n64 * nvec * 16 + n_inner * nvec * 2 * r + mom + 128 + 8 * (3 * dslash_blocks + 2 * vec_blocks + 3)
         if half:
             total += 4 * v * link_reals * 2      # 16-bit links of the inner solver
