@@ -45,6 +45,35 @@ def test_binding_covers_the_header():
     assert names <= set(fg.SIGNATURES), sorted(names - set(fg.SIGNATURES))
 
 
+def _header_enums():
+    """{enum type name: {enumerator: value}} of the C header's typedef enums."""
+    text = open(os.path.join(ROOT, "include", "fg_lattice.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    out = {}
+    for body, name in re.findall(r"typedef\s+enum\s*\{(.*?)\}\s*(\w+)\s*;", text, flags=re.S):
+        out[name] = {k: int(v) for k, v in re.findall(r"\b(FG_[A-Z0-9_]+)\s*=\s*(-?\d+)", body)}
+    return out
+
+
+def test_binding_constants_match_the_header_enums():
+    """The Python names of statuses, integrators and precisions carry the
+    values the C header gives them."""
+    enums = _header_enums()
+    status = enums["fg_status"]
+    for name in ("FG_OK", "FG_EINVAL", "FG_ENOMEM", "FG_ECUDA", "FG_ENOCONV", "FG_ETIMEOUT", "FG_ESTATE"):
+        assert getattr(fg, name) == status[name], name
+    assert fg.STATUS_NAMES == {v: k for k, v in status.items()}
+    prec = enums["fg_precision"]
+    assert sorted(fg.PRECISIONS.values()) == sorted(prec.values())
+    for key, value in fg.PRECISIONS.items():
+        assert prec["FG_" + key.upper()] == value, key
+    integ = enums["fg_integrator"]
+    assert set(fg.INTEGRATORS.values()) == set(integ.values())
+    for key, value in fg.INTEGRATORS.items():
+        if "FG_" + key.upper() in integ:
+            assert integ["FG_" + key.upper()] == value, key
+
+
 def test_params_default(lib):
     p = fg.FgParams()
     assert lib.fg_params_default(C.byref(p)) == fg.FG_OK
@@ -56,7 +85,8 @@ def test_params_default(lib):
 
 @pytest.mark.parametrize("field,value", [("dims", (3, 4, 4, 4)), ("dims", (4, 4, 0, 4)),
                                          ("dims", (130, 128, 128, 128)),   # over 2^28 sites
-                                         ("link_reals", 10), ("precision", 7), ("cg_maxiter", 0),
+                                         ("link_reals", 10), ("precision", 6), ("precision", -1),
+                                         ("cg_maxiter", 0),
                                          ("cg_tol", 0.0), ("cg_delta", 1.5)])
 def test_create_rejects_bad_parameters_before_touching_the_device(lib, field, value):
     p = fg.FgParams()

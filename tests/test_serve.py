@@ -154,3 +154,22 @@ def test_served_mix_matches_the_workload():
     assert all(0.155 <= c.kappa <= 0.159 and c.dims in [(8, 8, 8, 16), (12, 12, 12, 24)] for c in nf2)
     pg = [c for c in chains.values() if c.kappa == 0]
     assert all(5.7 <= c.beta <= 6.2 and c.dims[0] in (8, 12, 16, 24) for c in pg)
+
+
+def test_footprint_follows_the_cg_iteration_form():
+    """The folded CG iteration's second r and p buffers are counted while
+    the solver's links and six half-lattice vectors fit in L2 (with a margin,
+    so the estimate stays an upper bound), and never for 16-bit inner
+    vectors: beyond L2 the estimate drops exactly those two vectors."""
+    spec = serve.ChainSpec((24, 24, 24, 48), 5.6, 0.158, 1)
+    nvec = 12 * int(np.prod(spec.dims)) // 2           # complex entries of one even-site vector
+    for precision, r in (("fp32", 4), ("fp64", 8)):
+        in_l2 = serve.footprint_bytes(spec, precision, l2_bytes=1 << 40)
+        beyond = serve.footprint_bytes(spec, precision, l2_bytes=1 << 20)
+        assert in_l2 - beyond == 2 * nvec * 2 * r
+    for precision in ("fp32_fp16cg", "fp32_bf16cg"):
+        assert serve.footprint_bytes(spec, precision, l2_bytes=1 << 40) == \
+            serve.footprint_bytes(spec, precision, l2_bytes=1 << 20)
+    # pure gauge chains have no solver
+    pg = serve.ChainSpec((16, 16, 16, 16), 6.0, 0.0, 2)
+    assert serve.footprint_bytes(pg, "fp32", l2_bytes=1 << 40) == serve.footprint_bytes(pg, "fp32", l2_bytes=1 << 20)
