@@ -1136,6 +1136,14 @@ def run_ours(args):
             "launches": force_n, "avg_launch_us": avg_launch_s * 1e6,
             "algorithmic_gbs": bytes_per_launch / avg_launch_s / 1e9,
             "share_of_step": force_ms / elapsed_ms}
+    # cross-check of the derived peak: the FP32 FMA rate independent FMA
+    # chains reach on this GPU now (after the timed region)
+    try:
+        fma = fg.fp32_fma_rate()
+    except fg.FgError:
+        fma = None
+    roof["measured_fp32_fma_tflops"] = fma
+    roof["frac_of_measured_fma"] = (achieved / fma if fma and args.precision == "fp32" else None)
 
     # ---------------------------------------------------------------- dH error of the headline precision
     headline_dh = headline_precision_check(fg, lat, stream.cuda_stream, args) if not args.no_compare else None

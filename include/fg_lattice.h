@@ -175,6 +175,15 @@ typedef struct {
 /* Fill *p with defaults (dims 4^4, beta 6.0, pure gauge, FP64, 18 reals). */
 fg_status fg_params_default(fg_params *p);
 
+/* Measure the current device's FP32 FMA throughput: 8 blocks of 256 threads
+ * per SM, each thread running 8 independent FMA chains (65,536 FMAs), timed
+ * with CUDA events on a stream of its own; *tflops_out is the best of five
+ * launches in TFLOP/s (2 flop per FMA).  The ceiling of an FP32 kernel bound
+ * by FMA issue, measured at the clocks the GPU holds at the time.  Allocates
+ * and frees 1 KiB per block of device memory.  FG_EINVAL for a NULL pointer,
+ * FG_ECUDA on a CUDA error. */
+fg_status fg_fp32_fma_rate(double *tflops_out);
+
 /* Create a handle: validates *p, allocates the device fields (cold start links,
  * zero momenta).  *out is NULL on failure. */
 fg_status fg_lattice_create(const fg_params *p, fg_lattice **out);

@@ -61,6 +61,9 @@ cudaError_t launch_drift(const GeomH& g, const void* Uin, const void* P, void* U
 // Every link = identity (cold start).
 template <typename R, int NC>
 cudaError_t launch_unit_links(const GeomH& g, void* U, cudaStream_t st);
+// FP32 FMA throughput probe: `blocks` blocks of 256 threads, each running
+// 8 chains x 16 x iters FMAs; out holds blocks x 256 floats.
+cudaError_t launch_fma_rate(float* out, int blocks, int iters, cudaStream_t st);
 
 // Haar-random SU(3) links (device hot start).
 template <typename R, int NC>

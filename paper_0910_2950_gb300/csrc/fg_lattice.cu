@@ -254,6 +254,48 @@ fg_status fg_params_default(fg_params* p) {
   return FG_OK;
 }
 
+fg_status fg_fp32_fma_rate(double* tflops_out) {
+  if (!tflops_out) return FG_EINVAL;
+  *tflops_out = 0.0;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+    cudaGetLastError();
+    return FG_ECUDA;
+  }
+  const int blocks = 8 * sms, iters = 512;
+  float* out = nullptr;
+  cudaStream_t st = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  fg_status rc = FG_ECUDA;
+  float best = 0.0f;
+  if (cudaMalloc(&out, (size_t)blocks * 256 * sizeof(float)) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    goto done;
+  if (fg::launch_fma_rate(out, blocks, iters, st) != cudaSuccess) goto done;  // warm-up
+  for (int k = 0; k < 5; ++k) {
+    float ms = 0.0f;
+    if (cudaEventRecord(e0, st) != cudaSuccess || fg::launch_fma_rate(out, blocks, iters, st) != cudaSuccess ||
+        cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+      goto done;
+    if (ms > 0.0f && (best == 0.0f || ms < best)) best = ms;
+  }
+  if (best > 0.0f) {
+    const double flop = 2.0 * 8.0 * 16.0 * (double)iters * (double)blocks * 256.0;
+    *tflops_out = flop / ((double)best * 1e-3) / 1e12;
+    rc = FG_OK;
+  }
+done:
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (st) cudaStreamDestroy(st);
+  if (out) cudaFree(out);
+  if (rc != FG_OK) cudaGetLastError();
+  return rc;
+}
+
 fg_status fg_lattice_create(const fg_params* p, fg_lattice** out) {
   if (!out) return FG_EINVAL;
   *out = nullptr;

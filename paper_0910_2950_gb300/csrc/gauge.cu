@@ -453,4 +453,29 @@ template cudaError_t launch_mom_to_canon<double>(const GeomH&, const void*, doub
 template cudaError_t launch_mom_to_canon<float>(const GeomH&, const void*, double*, cudaStream_t);
 template cudaError_t launch_mom_to_canon<DF>(const GeomH&, const void*, double*, cudaStream_t);
 
+// FP32 FMA throughput probe: eight independent FMA chains per thread, 16
+// FMAs of each per loop trip, one store per thread so nothing is dropped.
+// a <- a b + c with b = 1 - 1e-4 and c = 1e-4 stays near 1 (no overflow or
+// subnormals).
+__global__ void __launch_bounds__(256) fma_rate_kernel(float* __restrict__ out, int iters, float b, float c) {
+  float a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = 0.5f + 0.01f * float(k) + 1e-6f * float(threadIdx.x);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < 16; ++u)
+#pragma unroll
+      for (int k = 0; k < 8; ++k) a[k] = fmaf(a[k], b, c);
+  }
+  float s = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += a[k];
+  out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+cudaError_t launch_fma_rate(float* out, int blocks, int iters, cudaStream_t st) {
+  fma_rate_kernel<<<blocks, 256, 0, st>>>(out, iters, 1.0f - 1e-4f, 1e-4f);
+  return cudaGetLastError();
+}
+
 }  // namespace fg

@@ -61,6 +61,7 @@ class FgBatchParams(C.Structure):
 
 SIGNATURES = {
     "fg_params_default": (_i, [C.POINTER(FgParams)]),
+    "fg_fp32_fma_rate": (_i, [C.POINTER(C.c_double)]),
     "fg_lattice_create": (_i, [C.POINTER(FgParams), C.POINTER(_vp)]),
     "fg_lattice_destroy": (None, [_vp]),
     "fg_last_error": (C.c_char_p, [_vp]),
@@ -133,6 +134,17 @@ class FgError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
         self.status = status
+
+
+def fp32_fma_rate() -> float:
+    """The current device's measured FP32 FMA throughput in TFLOP/s
+    (fg_fp32_fma_rate: independent FMA chains filling every SM)."""
+    lib = load()
+    v = C.c_double()
+    st = lib.fg_fp32_fma_rate(C.byref(v))
+    if st != FG_OK:
+        raise FgError(st, "fg_fp32_fma_rate failed")
+    return v.value
 
 
 def _ptr(a: np.ndarray):

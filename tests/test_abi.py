@@ -173,6 +173,7 @@ def test_null_handle_calls_fail_cleanly(lib):
     lib.fg_lattice_destroy(None)
     assert lib.fg_trajectories_host_momenta(None, 2, 0.25, 1.0, 0, None, None, None) == fg.FG_EINVAL
     assert lib.fg_trajectories_host_momenta_f32(None, 2, 0.25, 1.0, 0, None, None, None) == fg.FG_EINVAL
+    assert lib.fg_fp32_fma_rate(None) == fg.FG_EINVAL
 
 
 @pytest.mark.parametrize("case", ["odd", "too_large", "tile", "link_reals", "df64_tile64", "df64_12real"])

@@ -256,6 +256,17 @@ def test_wait_limit_reports_timeout(fgmod):
             lat2.close()
 
 
+def test_fp32_fma_rate(fgmod):
+    """The FMA probe fills the FP32 pipes: between half and all of the
+    unit-count rate (SMs x 128 lanes x 2 flop) at 2.2 GHz, above any GB300
+    SM clock (2070 MHz at most)."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    ceiling = sms * 128 * 2 * 2.2e9 / 1e12
+    rate = fgmod.fp32_fma_rate()
+    assert 0.5 * ceiling < rate < ceiling, (rate, ceiling)
+
+
 def test_timing_and_launch_count(fgmod):
     dims = (4, 4, 4, 4)
     with fgmod.Lattice(dims, BETA) as lat:
