@@ -152,3 +152,22 @@ def test_chronological_guess_trajectory(fgmod, monkeypatch, precision):
     assert rg["cg_iters"] < 0.85 * r0["cg_iters"], (rg["cg_iters"], r0["cg_iters"])
     assert abs(rg["dH"] - r0["dH"]) <= (1e-8 if precision == "fp64" else 1e-3), (rg["dH"], r0["dH"])
     assert _rel(ug, u0) < (1e-11 if precision == "fp64" else 1e-4)
+
+
+@pytest.mark.parametrize("dims,precision,folded", [((16, 16, 16, 32), "fp32", True), ((24, 24, 24, 48), "fp32", False),
+                                                   ((16, 16, 16, 32), "fp64", False), ((8, 8, 8, 16), "fp64", True)])
+def test_default_form_follows_the_l2_working_set(fgmod, monkeypatch, dims, precision, folded):
+    """Without FG_CG_FOLD the library folds the iterations while the
+    solver's links and six vectors fit in L2 (FP32 16^3 x 32: 76 MB; FP64
+    8^3 x 16: 9 MB) and runs six launches beyond (FP32 24^3 x 48: 382 MB;
+    FP64 16^3 x 32: 151 MB): the six-launch form runs two vector kernels per
+    iteration, the folded one only in the setup and the reliable updates."""
+    monkeypatch.delenv("FG_CG_FOLD", raising=False)
+    b = _rand_even(dims, 18)
+    with fgmod.Lattice(dims, BETA, kappa=KAPPA, precision=precision, cg_tol=1e-8) as lat:
+        lat.random_gauge()
+        lat.timing(True)
+        _, info = lat.cg_solve(b)
+        n_blas = lat.kernel_time("cg_blas")[1]
+    assert info["true_residual"] <= 1e-8
+    assert (n_blas < info["iterations"]) == folded, (n_blas, info["iterations"])
